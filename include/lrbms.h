@@ -1,0 +1,204 @@
+/*
+ * lrbms.h - C ABI of the GB300 library for the online time step of the
+ * Localized Reduced Basis Multiscale (LRBMS) method for incompressible
+ * two-phase flow (Kaulmann, Flemisch, Haasdonk, Lie, Ohlberger,
+ * arXiv 1405.2810).
+ *
+ * One online step (Algorithm 3, step 5) advances the wetting saturation s^n
+ * of every listed simulation to s^{n+1}:
+ *   (a) least-squares fit of the mobility coefficients theta(s^n)
+ *       (Eq. leastSquaresFit) and assembly of the reduced system
+ *       (c + sum_q theta_q b_q) x = e + sum_q theta_q d_q   (Eq. reducedSystem);
+ *   (b) solve of that symmetric positive definite block-sparse system;
+ *   (c) reconstruction of the fine P1 pressure p = sum_i x_i phi_i
+ *       (Algorithm 3, step 5(b)) and of the conservative face fluxes of
+ *       Definition 2 (Eq. velocityDG) with the mobility lambda(s^n);
+ *   (d) explicit upwind finite-volume saturation update (Definition 3 with
+ *       piecewise-constant saturation, Eq. upwind) with a CFL time step.
+ * All arithmetic runs in CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Fine grid: nx x ny rectangles on [0,Lx] x [0,Ly]; cell (i,j) -> j*nx + i.
+ * Faces: x-faces (normal +x) (i,j), i=0..nx, j=0..ny-1 -> j*(nx+1)+i, then
+ * y-faces (normal +y) (i,j), i=0..nx-1, j=0..ny -> (nx+1)*ny + j*nx + i.
+ * Every face flux is the integral of u.n over the face with n = +x or +y.
+ * Boundary faces, 2*nx + 2*ny of them: left side (j = 0..ny-1), right side
+ * (j), bottom side (i = 0..nx-1), top side (i).
+ * Local P1 basis on a cell with centre (xc,yc): psi0 = 1,
+ * psi1 = 2(x-xc)/hx, psi2 = 2(y-yc)/hy; a pressure field is three arrays
+ * p0[n_cells], p1[n_cells], p2[n_cells] (structure of arrays).
+ * Coarse grid (Section 4.2): Sx x Sy subdomains of (nx/Sx) x (ny/Sy) cells,
+ * subdomain (I,J) -> J*Sx + I; local cell (li,lj) -> lj*(nx/Sx) + li.
+ * Coarse faces: x-interfaces between (I,J) and (I+1,J), index J*(Sx-1)+I,
+ * then y-interfaces between (I,J) and (I,J+1), index Sy*(Sx-1) + J*Sx + I.
+ *
+ * Ownership: every pointer passed in is owned by the caller, may be host or
+ * device memory (the library copies with unified addressing) and may be
+ * freed when the call returns. The library owns all device memory it uses;
+ * it is taken from one arena allocated at lrbms_create.
+ *
+ * Errors: every call returns LRBMS_OK (0) or a negative lrbms_status; the
+ * message of the last error is available from lrbms_last_error. No call
+ * aborts, traps or prints. A simulation whose step fails (non-SPD reduced
+ * matrix, non-finite state) is frozen with its status word set; the other
+ * simulations continue.
+ *
+ * Threads: a context is used by one host thread at a time.
+ */
+#ifndef LRBMS_H
+#define LRBMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrbms_ctx lrbms_ctx;
+
+typedef enum {
+  LRBMS_OK = 0,
+  LRBMS_E_ARG = -1,       /* invalid argument or shape                       */
+  LRBMS_E_BUDGET = -2,    /* device-memory budget or slot table exhausted    */
+  LRBMS_E_CUDA = -3,      /* a CUDA runtime call failed                       */
+  LRBMS_E_NOT_SPD = -4,   /* reduced matrix not positive definite (Cholesky) */
+  LRBMS_E_NONFINITE = -5, /* NaN or Inf in the saturation or time step       */
+  LRBMS_E_TIMEOUT = -6,   /* a bounded device-side wait gave up              */
+  LRBMS_E_FORMAT = -7,    /* offline data inconsistent with the problem      */
+  LRBMS_E_STATE = -9      /* unknown or released simulation id               */
+} lrbms_status;
+
+enum { LRBMS_FP64 = 0, LRBMS_MIXED = 1 };
+enum { LRBMS_COREY = 0, LRBMS_LINEAR = 1 };
+enum { LRBMS_DT_CFL = 0, LRBMS_DT_FIXED = 1 };
+
+typedef struct {
+  int precision;     /* LRBMS_FP64: every phase in FP64. LRBMS_MIXED: basis
+                        and component streams in FP32 with FP32 accumulation;
+                        fit, solve, fluxes and saturation in FP64.          */
+  int max_slots;     /* maximum number of resident simulations (>= 1)       */
+  size_t hbm_budget; /* bytes of device memory for simulation data; the
+                        arena is allocated once, at lrbms_create           */
+  void* stream;      /* cudaStream_t for all work, or NULL for a stream
+                        owned by the context                                */
+  int device;        /* CUDA device ordinal                                 */
+} lrbms_config;
+
+/* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with
+ * gravity and sources set to zero, on the grids described above. */
+typedef struct {
+  int nx, ny, Sx, Sy;
+  double Lx, Ly;
+  const double* perm;    /* [nx*ny] permeability kappa (P0)                  */
+  const double* poro;    /* [nx*ny] porosity phi (P0)                        */
+  double eta_w, eta_o;   /* viscosities                                      */
+  int relperm;           /* LRBMS_COREY (k_rw=s^2, k_ro=(1-s)^2) or LRBMS_LINEAR */
+  const int8_t* bc_type; /* [2nx+2ny] 1: Dirichlet pressure p_D; 0: Neumann,
+                            outward flux density v_N (0 = no flow)          */
+  const double* p_D;     /* [2nx+2ny]                                        */
+  const double* v_N;     /* [2nx+2ny]                                        */
+  const double* s_D;     /* [2nx+2ny] saturation entering through an inflow face */
+  const double* s0;      /* [nx*ny] initial saturation                       */
+  double cfl;            /* CFL number of the time step (dt_mode = CFL)      */
+  int dt_mode;           /* LRBMS_DT_CFL or LRBMS_DT_FIXED                   */
+  double dt_fixed;       /* time step for LRBMS_DT_FIXED                     */
+  double dt_max;         /* upper bound on the CFL step; <= 0: none          */
+  int mean_weights;      /* face mean weights: 0 tau_l = a_l/(a1+a2) (as
+                            printed, Section 3.1); 1 the swapped weights     */
+} lrbms_problem;
+
+/* Offline data of the offline/online decomposition (Section 4.4) for M
+ * mobility profiles and local bases of sizes N_E. Component index q = 0
+ * holds the parameter-independent part (c for the matrix, e for the right
+ * hand side); q = 1..M hold b_q and d_q. */
+typedef struct {
+  int M;
+  const int* N_E;          /* [Sx*Sy] local basis sizes (>= 1)               */
+  const uint8_t* prof_idx; /* [nx*ny] first profile index q (2..M) whose value
+                              is lambda(1) (profiles of Algorithm 2, step 1(c)),
+                              or NULL                                       */
+  const double* prof;      /* [M][nx*ny] total-mobility profiles, or NULL;
+                              exactly one of prof_idx and prof is given     */
+  const double* Gpinv;     /* [M*M] pseudo-inverse of the profile Gram matrix
+                              (normal equations of Eq. leastSquaresFit)     */
+  const double* Phi;       /* per subdomain E, concatenated: [N_E][3*cells_E],
+                              row k*cells_E + c = coefficient of psi_k on
+                              local cell c                                  */
+  const double* Dblk;      /* per subdomain E: [M+1][N_E][N_E]               */
+  const double* Fblk;      /* per coarse face (E-, E+): [M+1][N_E-][N_E+]    */
+  const double* rhs;       /* per subdomain E: [M+1][N_E]                    */
+  double c_pen;            /* penalty scale c_f / max(eta_w, eta_o), Remark 1:
+                              sigma_f = c_pen * 2 k1 k2/(k1+k2) inside,
+                              c_pen * k_e on a boundary face                */
+  double Lf;               /* max over [0,1] of f_w'(s) for the CFL step     */
+} lrbms_offline;
+
+/* Create a context on cfg->device with an arena of cfg->hbm_budget bytes. */
+int lrbms_create(lrbms_ctx** ctx, const lrbms_config* cfg);
+/* Free every device buffer and the context. */
+int lrbms_destroy(lrbms_ctx* ctx);
+
+/* Admit one simulation: validate shapes, charge the arena, copy the problem
+ * and offline data to the device and set s = s0, t = 0. On success *sim_id
+ * receives the slot. LRBMS_E_BUDGET if the arena or slot table is full. */
+int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* prob,
+                       const lrbms_offline* off, int* sim_id);
+/* Release a simulation's slot and arena memory. */
+int lrbms_release(lrbms_ctx* ctx, int sim_id);
+
+/* Enqueue n_steps online steps (Algorithm 3, step 5) for the n_sims listed
+ * simulations on the context stream, all simulations in each launch. With
+ * status == NULL the call returns once the work is enqueued; otherwise it
+ * waits for the stream and writes one lrbms_status per simulation. */
+int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int n_steps,
+               int* status);
+
+/* Run n_steps steps of one simulation, wait, and copy the saturation
+ * [n_cells], pressure [3][n_cells] and face fluxes [n_faces] of the last step
+ * into the caller's buffers (NULL buffers are skipped). */
+int lrbms_run(lrbms_ctx* ctx, int sim_id, int n_steps, double* s_out,
+              double* p_out, double* flux_out);
+
+/* Wait and copy the saturation [n_cells], simulated time and the cumulative
+ * water volume that left through the boundary (NULL skipped). */
+int lrbms_get_state(lrbms_ctx* ctx, int sim_id, double* s, double* t,
+                    double* mass_out);
+/* Overwrite a simulation's saturation (host or device pointer). */
+int lrbms_set_saturation(lrbms_ctx* ctx, int sim_id, const double* s);
+
+/* Intermediate fields of the last step, for inspection and parity tests. */
+enum {
+  LRBMS_FIELD_THETA = 0, /* [M] fit coefficients                              */
+  LRBMS_FIELD_A = 1,     /* assembled blocks: per E [N_E][N_E], then per coarse
+                            face [N_E-][N_E+]                                   */
+  LRBMS_FIELD_RHS = 2,   /* [N] assembled right-hand side                       */
+  LRBMS_FIELD_X = 3,     /* [N] reduced solution, subdomain-major               */
+  LRBMS_FIELD_P = 4,     /* [3][n_cells] reconstructed pressure                 */
+  LRBMS_FIELD_FLUX = 5,  /* [n_faces] face fluxes                               */
+  LRBMS_FIELD_S = 6,     /* [n_cells] saturation                                */
+  LRBMS_FIELD_DT = 7,    /* [1] last time step                                  */
+  LRBMS_FIELD_STATUS = 8 /* [1] int status word                                 */
+};
+/* Wait and copy a field (bytes must equal the field's size). */
+int lrbms_get_field(lrbms_ctx* ctx, int sim_id, int field, void* dst, size_t bytes);
+
+/* Size in bytes of a field for a resident simulation (0 if unknown). */
+size_t lrbms_field_bytes(lrbms_ctx* ctx, int sim_id, int field);
+
+/* Wait for all enqueued work. */
+int lrbms_sync(lrbms_ctx* ctx);
+
+/* Device bytes in use by resident simulations, and the arena size. */
+int lrbms_memory(lrbms_ctx* ctx, size_t* used, size_t* capacity);
+
+/* Number of kernel launches enqueued by this context so far. */
+long long lrbms_launch_count(const lrbms_ctx* ctx);
+
+const char* lrbms_last_error(const lrbms_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRBMS_H */

@@ -1,0 +1,427 @@
+// Per-cell and per-face kernels of the LRBMS online step:
+//   fit        partial sums of the normal equations of Eq. leastSquaresFit
+//   reconstruct p_E = Phi_E x_E (Algorithm 3, step 5(b))
+//   flux       face fluxes of Definition 2 (Eq. velocityDG), mobility lambda(s^n)
+//   cfl        per-tile minimum of the CFL bound phi|e| / (L_f * outflow_e)
+//   transport  explicit upwind update of Definition 3 with P0 saturation
+//   finalize   time, cumulative boundary outflow and step counter
+// Every reduction uses a fixed tile partition and a fixed order, so a
+// simulation's results do not depend on which other simulations share the
+// launch.
+#include "lrbms_internal.cuh"
+
+#include <cfloat>
+
+namespace lrbms {
+
+namespace {
+
+__device__ __forceinline__ const double* cur_s(const SimDev& S) {
+  return S.s + (size_t)(S.steps[0] & 1) * S.n_cells;
+}
+__device__ __forceinline__ double* next_s(const SimDev& S) {
+  return S.s + (size_t)((S.steps[0] + 1) & 1) * S.n_cells;
+}
+
+// Eq. brooksCorey: lambda_w = k_rw/eta_w, lambda_o = k_ro/eta_o.
+__device__ __forceinline__ void phase_mob(const SimDev& S, double s, double& lw, double& lo) {
+  if (S.relperm == 0) {
+    lw = s * s * S.inv_eta_w;
+    lo = (1.0 - s) * (1.0 - s) * S.inv_eta_o;
+  } else {
+    lw = s * S.inv_eta_w;
+    lo = (1.0 - s) * S.inv_eta_o;
+  }
+}
+__device__ __forceinline__ double total_mob(const SimDev& S, double s) {
+  double lw, lo;
+  phase_mob(S, s, lw, lo);
+  return lw + lo;
+}
+// Eq. frationalFlow.
+__device__ __forceinline__ double frac_flow(const SimDev& S, double s) {
+  double lw, lo;
+  phase_mob(S, s, lw, lo);
+  return lw / (lw + lo);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Fixed-order block sum of one value per thread; result valid in thread 0.
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) r += red[i];
+  return r;
+}
+__device__ double block_min(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_min(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = DBL_MAX;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; ++i) r = fmin(r, red[i]);
+  return r;
+}
+
+// ------------------------------------------------------------------ fit
+// r_q = sum_e Lambda^q_e lambda(s_e) per tile. With the threshold profiles of
+// Algorithm 2 (Lambda^q_e = lambda(1) if q >= k_e else lambda(0)) the cells are
+// binned by k_e and r follows from the bin sums.
+__global__ void k_fit(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
+  const double* s = cur_s(S);
+  const int M = S.M;
+  double acc[kMaxM];
+#pragma unroll
+  for (int q = 0; q < kMaxM; ++q) acc[q] = 0.0;
+  const int e0 = tile * kCellTile;
+  const int e1 = min(e0 + kCellTile, S.n_cells);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const double lam = total_mob(S, s[e]);
+    if (S.prof_mode == 0) {
+      const int k = S.prof_idx[e];  // 1-based profile index in 2..M
+#pragma unroll
+      for (int q = 0; q < kMaxM; ++q) acc[q] += (q == k - 1) ? lam : 0.0;
+    } else {
+#pragma unroll
+      for (int q = 0; q < kMaxM; ++q)
+        if (q < M) acc[q] += S.prof[(size_t)q * S.n_cells + e] * lam;
+    }
+  }
+  __shared__ double red[32];
+  __shared__ double tot[kMaxM];
+  for (int q = 0; q < M; ++q) {
+    const double v = block_sum(acc[q], red);
+    if (threadIdx.x == 0) tot[q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    const int q = threadIdx.x;  // 0-based profile q+1
+    double r;
+    if (S.prof_mode == 0) {
+      // bins tot[k-1] hold sum of lambda over cells with index k
+      r = 0.0;
+      for (int k = 1; k <= M; ++k) r += tot[k - 1] * ((q + 1 >= k) ? S.lam1 : S.lam0);
+    } else {
+      r = tot[q];
+    }
+    S.fit_part[(size_t)tile * kMaxM + q] = r;
+  }
+}
+
+// ------------------------------------------------------------------ reconstruct
+__global__ void k_reconstruct(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int E = blockIdx.x;
+  if (E >= S.n_sub || S.status[0] != kStOk) return;
+  extern __shared__ double xs[];
+  const int NE = S.NE[E];
+  const int x0 = S.xoff[E];
+  for (int i = threadIdx.x; i < NE; i += blockDim.x) xs[i] = S.x[x0 + i];
+  __syncthreads();
+  const int cells = S.cx * S.cy;
+  const int rows = 3 * cells;
+  const double* Phi = S.Phi + S.phi_off[E];
+  const int I = E % S.Sx, J = E / S.Sx;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < NE; ++i) acc = fma(Phi[(size_t)i * rows + r], xs[i], acc);
+    const int k = r / cells, c = r - k * cells;
+    const int li = c % S.cx, lj = c / S.cx;
+    const int ge = (J * S.cy + lj) * S.nx + I * S.cx + li;
+    S.p[(size_t)k * S.n_cells + ge] = acc;
+  }
+}
+
+__global__ void k_reconstruct32(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int E = blockIdx.x;
+  if (E >= S.n_sub || S.status[0] != kStOk) return;
+  extern __shared__ double xsd[];
+  float* xs = reinterpret_cast<float*>(xsd);
+  const int NE = S.NE[E];
+  const int x0 = S.xoff[E];
+  for (int i = threadIdx.x; i < NE; i += blockDim.x) xs[i] = (float)S.x[x0 + i];
+  __syncthreads();
+  const int cells = S.cx * S.cy;
+  const int rows = 3 * cells;
+  const float* Phi = S.Phi32 + S.phi_off[E];
+  const int I = E % S.Sx, J = E / S.Sx;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    float acc = 0.0f;
+    for (int i = 0; i < NE; ++i) acc = fmaf(Phi[(size_t)i * rows + r], xs[i], acc);
+    const int k = r / cells, c = r - k * cells;
+    const int li = c % S.cx, lj = c / S.cx;
+    const int ge = (J * S.cy + lj) * S.nx + I * S.cx + li;
+    S.p[(size_t)k * S.n_cells + ge] = (double)acc;
+  }
+}
+
+// ------------------------------------------------------------------ flux
+// Definition 2 for P1 pressure and P0 coefficients: the normal gradient is
+// constant per cell and the jump is linear along the face, so
+//   F = |f| ( -(tau1 l1 k1 dn p1 + tau2 l2 k2 dn p2) ) + sigma_f [p](midpoint)
+// with sigma_f/h_f * |f| = sigma_f in 2D (h_f = |f|).
+__global__ void k_flux(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= S.n_faces || S.status[0] != kStOk) return;
+  const double* s = cur_s(S);
+  const double* p0 = S.p;
+  const double* p1 = S.p + S.n_cells;
+  const double* p2 = S.p + 2 * (size_t)S.n_cells;
+  const int nx = S.nx, ny = S.ny;
+  int e1 = -1, e2 = -1, bidx = -1;
+  bool xface;
+  double flen, dscale;
+  if (f < S.nxf) {
+    xface = true;
+    const int j = f / (nx + 1), i = f - j * (nx + 1);
+    if (i > 0) e1 = j * nx + i - 1;
+    if (i < nx) e2 = j * nx + i;
+    if (i == 0) bidx = j;
+    if (i == nx) bidx = ny + j;
+    flen = S.hy;
+    dscale = 2.0 / S.hx;
+  } else {
+    xface = false;
+    const int g = f - S.nxf;
+    const int j = g / nx, i = g - j * nx;
+    if (j > 0) e1 = (j - 1) * nx + i;
+    if (j < ny) e2 = j * nx + i;
+    if (j == 0) bidx = 2 * ny + i;
+    if (j == ny) bidx = 2 * ny + nx + i;
+    flen = S.hx;
+    dscale = 2.0 / S.hy;
+  }
+  const double* pt = xface ? p1 : p2;  // tangential-free coefficient along the normal
+  double F;
+  if (e1 >= 0 && e2 >= 0) {
+    const double k1 = S.perm[e1], k2 = S.perm[e2];
+    const double ks = k1 + k2;
+    const double t1 = (S.swapped ? k2 : k1) / ks;
+    const double t2 = (S.swapped ? k1 : k2) / ks;
+    const double l1 = total_mob(S, s[e1]), l2 = total_mob(S, s[e2]);
+    const double g1 = dscale * pt[e1], g2 = dscale * pt[e2];
+    const double mean = t1 * l1 * k1 * g1 + t2 * l2 * k2 * g2;
+    const double jump = (p0[e1] + pt[e1]) - (p0[e2] - pt[e2]);
+    const double sig = S.c_pen * 2.0 * k1 * k2 / ks;
+    F = -flen * mean + sig * jump;
+  } else {
+    const int e = (e1 >= 0) ? e1 : e2;
+    const double sgn = (e1 >= 0) ? 1.0 : -1.0;  // outward normal along +axis?
+    double Fout;
+    if (S.bc_type[bidx] == 1) {
+      const double ke = S.perm[e];
+      const double le = total_mob(S, s[e]);
+      const double gn = sgn * dscale * pt[e];
+      const double pmid = p0[e] + sgn * pt[e];
+      Fout = -flen * le * ke * gn + S.c_pen * ke * (pmid - S.p_D[bidx]);
+    } else {
+      Fout = flen * S.v_N[bidx];
+    }
+    F = sgn * Fout;
+  }
+  S.F[f] = F;
+}
+
+// Outward fluxes of cell (i,j): left face -F, right +F, bottom -F, top +F.
+__device__ __forceinline__ void cell_faces(const SimDev& S, int e, int& fl, int& fr, int& fb,
+                                           int& ft) {
+  const int nx = S.nx;
+  const int j = e / nx, i = e - j * nx;
+  fl = j * (nx + 1) + i;
+  fr = fl + 1;
+  fb = S.nxf + j * nx + i;
+  ft = fb + nx;
+}
+
+// ------------------------------------------------------------------ cfl
+__global__ void k_cfl(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
+  const int e0 = tile * kCellTile;
+  const int e1 = min(e0 + kCellTile, S.n_cells);
+  double m = DBL_MAX;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    int fl, fr, fb, ft;
+    cell_faces(S, e, fl, fr, fb, ft);
+    const double out = fmax(-S.F[fl], 0.0) + fmax(S.F[fr], 0.0) + fmax(-S.F[fb], 0.0) +
+                       fmax(S.F[ft], 0.0);
+    if (out > 0.0) m = fmin(m, S.poro[e] * S.vol / (S.Lf * out));
+  }
+  __shared__ double red[32];
+  const double r = block_min(m, red);
+  if (threadIdx.x == 0) S.cfl_part[tile] = r;
+}
+
+__device__ __forceinline__ double step_dt(const SimDev& S) {
+  if (S.dt_mode == 1) return S.dt_fixed;
+  double m = DBL_MAX;
+  for (int t = 0; t < S.n_tiles; ++t) m = fmin(m, S.cfl_part[t]);
+  double dt = (m == DBL_MAX) ? DBL_MAX : S.cfl * m;
+  if (S.dt_max > 0.0) dt = fmin(dt, S.dt_max);
+  return dt;
+}
+
+// ------------------------------------------------------------------ transport
+// Face term G_f = F_f f_w(s_up) with s_up from the face's own upwind rule
+// (s|e1 if F >= 0, else s|e2; s_D on boundary inflow). Both cells of an
+// interior face evaluate G_f from identical operands, so it cancels exactly
+// in the total water volume.
+__device__ __forceinline__ double face_term_interior(const SimDev& S, const double* s, double F,
+                                                     int e1, int e2) {
+  const double su = (F >= 0.0) ? s[e1] : s[e2];
+  return F * frac_flow(S, su);
+}
+
+__global__ void k_transport(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
+  __shared__ double dt_sh;
+  if (threadIdx.x == 0) dt_sh = step_dt(S);
+  __syncthreads();
+  const double dt = dt_sh;
+  const double* s = cur_s(S);
+  double* sn = next_s(S);
+  const int nx = S.nx, ny = S.ny;
+  const int e0 = tile * kCellTile;
+  const int e1 = min(e0 + kCellTile, S.n_cells);
+  double bout = 0.0;
+  bool bad = !(dt > 0.0 && dt < DBL_MAX);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int j = e / nx, i = e - j * nx;
+    int fl, fr, fb, ft;
+    cell_faces(S, e, fl, fr, fb, ft);
+    double net = 0.0;
+    // left face: this cell is e2; outward flux -F
+    if (i > 0) {
+      net -= face_term_interior(S, s, S.F[fl], e - 1, e);
+    } else {
+      const double Fo = -S.F[fl];
+      const double su = (Fo >= 0.0) ? s[e] : S.s_D[j];
+      const double g = Fo * frac_flow(S, su);
+      net += g;
+      bout += g;
+    }
+    if (i < nx - 1) {
+      net += face_term_interior(S, s, S.F[fr], e, e + 1);
+    } else {
+      const double Fo = S.F[fr];
+      const double su = (Fo >= 0.0) ? s[e] : S.s_D[ny + j];
+      const double g = Fo * frac_flow(S, su);
+      net += g;
+      bout += g;
+    }
+    if (j > 0) {
+      net -= face_term_interior(S, s, S.F[fb], e - nx, e);
+    } else {
+      const double Fo = -S.F[fb];
+      const double su = (Fo >= 0.0) ? s[e] : S.s_D[2 * ny + i];
+      const double g = Fo * frac_flow(S, su);
+      net += g;
+      bout += g;
+    }
+    if (j < ny - 1) {
+      net += face_term_interior(S, s, S.F[ft], e, e + nx);
+    } else {
+      const double Fo = S.F[ft];
+      const double su = (Fo >= 0.0) ? s[e] : S.s_D[2 * ny + nx + i];
+      const double g = Fo * frac_flow(S, su);
+      net += g;
+      bout += g;
+    }
+    const double v = s[e] - dt / (S.poro[e] * S.vol) * net;
+    if (!isfinite(v)) bad = true;
+    sn[e] = v;
+  }
+  __shared__ double red[32];
+  const double tot = block_sum(bout, red);
+  const int anybad = __syncthreads_or(bad ? 1 : 0);
+  if (threadIdx.x == 0) {
+    S.mass_part[tile] = tot;
+    if (anybad) S.status[0] = kStNonFinite;
+  }
+}
+
+// ------------------------------------------------------------------ finalize
+__global__ void k_finalize(const SimDev* __restrict__ sims, const int* __restrict__ active,
+                           int n_active) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_active) return;
+  const SimDev& S = sims[active[a]];
+  if (S.status[0] != kStOk) return;
+  const double dt = step_dt(S);
+  double out = 0.0;
+  for (int t = 0; t < S.n_tiles; ++t) out += S.mass_part[t];
+  S.scal[0] += dt;
+  S.scal[1] = dt;
+  S.scal[2] += dt * out;
+  S.scal[3] = out;
+  S.steps[0] += 1;
+}
+
+__global__ void k_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+}  // namespace
+
+void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_to_float<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
+}
+
+void launch_fit(const SimDev* sims, const int* active, int n_active, int max_tiles,
+                cudaStream_t st) {
+  k_fit<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
+}
+void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
+                        int mixed, cudaStream_t st) {
+  const size_t smem = 64 * sizeof(double);  // max_NE <= 64 (checked at load)
+  if (mixed)
+    k_reconstruct32<<<dim3(max_sub, n_active), 256, smem, st>>>(sims, active);
+  else
+    k_reconstruct<<<dim3(max_sub, n_active), 256, smem, st>>>(sims, active);
+}
+void launch_flux(const SimDev* sims, const int* active, int n_active, int max_faces,
+                 cudaStream_t st) {
+  k_flux<<<dim3((max_faces + kFaceThreads - 1) / kFaceThreads, n_active), kFaceThreads, 0, st>>>(
+      sims, active);
+}
+void launch_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles,
+                cudaStream_t st) {
+  k_cfl<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
+}
+void launch_transport(const SimDev* sims, const int* active, int n_active, int max_tiles,
+                      cudaStream_t st) {
+  k_transport<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
+}
+void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st) {
+  k_finalize<<<(n_active + 127) / 128, 128, 0, st>>>(sims, active, n_active);
+}
+
+}  // namespace lrbms

@@ -1,0 +1,360 @@
+// Reduced system of Eq. reducedSystem: assembly and solve.
+//
+// assemble: theta = G^+ r (normal equations of Eq. leastSquaresFit from the
+//   fixed-order sum of the fit partials), then every block
+//   A_b = c_b + sum_q theta_q (b_q)_b and every subdomain right-hand side
+//   b_E = e_E + sum_q theta_q (d_q)_E, streamed from the component arrays.
+// chol_solve: one CTA per simulation. The matrix is symmetric positive
+//   definite with a 5-point block pattern over the Sx x Sy subdomains; in
+//   lexicographic subdomain order its Cholesky factor lives in the envelope
+//   j in [k - Sx, k] of every block row k. Block row k of L is kept as a dense
+//   N_k x W_k panel (left-looking: L_kj = (A_kj - sum_i L_ki L_ji^T) L_jj^-T,
+//   L_kk = chol(A_kk - sum_i L_ki L_ki^T)); the inverse of every diagonal block
+//   is kept to turn the triangular solves into small products. Forward and
+//   backward substitution follow, then `refine` steps of iterative refinement
+//   with an FP64 residual r = b - A x.
+#include "lrbms_internal.cuh"
+
+namespace lrbms {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// theta = G^+ (sum over tiles of the fit partials), by warp 0; w[0] = 1.
+__device__ void compute_weights(const SimDev& S, double* w, double* rsh, bool store) {
+  const int M = S.M;
+  if (threadIdx.x < 32) {
+    const int q = threadIdx.x;
+    if (q < M) {
+      double r = 0.0;
+      for (int t = 0; t < S.n_tiles; ++t) r += S.fit_part[(size_t)t * kMaxM + q];
+      rsh[q] = r;
+    }
+    __syncwarp();
+    if (q < M) {
+      double th = 0.0;
+      for (int j = 0; j < M; ++j) th = fma(S.Gpinv[q * M + j], rsh[j], th);
+      w[1 + q] = th;
+      if (store) S.theta[q] = th;
+    }
+    if (q == 0) w[0] = 1.0;
+  }
+  __syncthreads();
+}
+
+__global__ void k_assemble(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int bidx = blockIdx.x;
+  if (bidx >= S.n_blocks + S.n_sub || S.status[0] != kStOk) return;
+  __shared__ double w[kMaxM + 1];
+  __shared__ double rsh[kMaxM];
+  compute_weights(S, w, rsh, bidx == 0);
+  const int Q = S.M + 1;
+  if (bidx < S.n_blocks) {
+    const long long o = S.aoff[bidx];
+    const int size = (int)(S.aoff[bidx + 1] - o);
+    const double* c = S.comp + (size_t)Q * o;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc = fma(w[q], c[(size_t)q * size + i], acc);
+      S.A[o + i] = acc;
+    }
+  } else {
+    const int E = bidx - S.n_blocks;
+    const int NE = S.NE[E], x0 = S.xoff[E];
+    const double* c = S.rhs + (size_t)Q * x0;
+    for (int i = threadIdx.x; i < NE; i += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc = fma(w[q], c[(size_t)q * NE + i], acc);
+      S.b[x0 + i] = acc;
+    }
+  }
+}
+
+// Mixed precision: FP32 components, FP32 products accumulated in FP32.
+__global__ void k_assemble32(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int bidx = blockIdx.x;
+  if (bidx >= S.n_blocks + S.n_sub || S.status[0] != kStOk) return;
+  __shared__ double w[kMaxM + 1];
+  __shared__ double rsh[kMaxM];
+  compute_weights(S, w, rsh, bidx == 0);
+  float wf[kMaxM + 1];
+  const int Q = S.M + 1;
+#pragma unroll
+  for (int q = 0; q < kMaxM + 1; ++q) wf[q] = q < Q ? (float)w[q] : 0.0f;
+  if (bidx < S.n_blocks) {
+    const long long o = S.aoff[bidx];
+    const int size = (int)(S.aoff[bidx + 1] - o);
+    const float* c = S.comp32 + (size_t)Q * o;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+      float acc = 0.0f;
+      for (int q = 0; q < Q; ++q) acc = fmaf(wf[q], c[(size_t)q * size + i], acc);
+      S.A[o + i] = (double)acc;
+    }
+  } else {
+    const int E = bidx - S.n_blocks;
+    const int NE = S.NE[E], x0 = S.xoff[E];
+    const double* c = S.rhs + (size_t)Q * x0;
+    for (int i = threadIdx.x; i < NE; i += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc = fma(w[q], c[(size_t)q * NE + i], acc);
+      S.b[x0 + i] = acc;
+    }
+  }
+}
+
+// Index of the assembled coupling block between subdomain k and its left
+// (dir 0) or lower (dir 1) neighbour; -1 if none.
+__device__ __forceinline__ int coupling_block(const SimDev& S, int k, int dir) {
+  const int I = k % S.Sx, J = k / S.Sx;
+  if (dir == 0) return I > 0 ? S.n_sub + J * (S.Sx - 1) + (I - 1) : -1;
+  return J > 0 ? S.n_sub + S.Sy * (S.Sx - 1) + (J - 1) * S.Sx + I : -1;
+}
+// ... and with its right (dir 2) or upper (dir 3) neighbour.
+__device__ __forceinline__ int coupling_block_up(const SimDev& S, int k, int dir) {
+  const int I = k % S.Sx, J = k / S.Sx;
+  if (dir == 2) return I < S.Sx - 1 ? S.n_sub + J * (S.Sx - 1) + I : -1;
+  return J < S.Sy - 1 ? S.n_sub + S.Sy * (S.Sx - 1) + J * S.Sx + I : -1;
+}
+
+// Returns false if a pivot is not positive.
+__device__ bool factor(const SimDev& S, double* sm) {
+  const int nsub = S.n_sub, Sx = S.Sx;
+  __shared__ int bad;
+  __shared__ double dsh;
+  if (threadIdx.x == 0) bad = 0;
+  double* tmp = sm;  // max_NE * max_NE
+  for (int k = 0; k < nsub; ++k) {
+    const int jl = jlo_of(k, Sx);
+    const int base = S.xoff[jl];
+    const int W = S.xoff[k + 1] - base;
+    const int Nk = S.NE[k];
+    double* R = S.L + S.loff[k];
+    for (int i = threadIdx.x; i < Nk * W; i += blockDim.x) R[i] = 0.0;
+    __syncthreads();
+    {
+      const double* Akk = S.A + S.aoff[k];
+      const int cd = S.xoff[k] - base;
+      for (int i = threadIdx.x; i < Nk * Nk; i += blockDim.x) {
+        const int r = i / Nk, c = i - r * Nk;
+        R[r * W + cd + c] = Akk[i];
+      }
+      for (int dir = 0; dir < 2; ++dir) {
+        const int bblk = coupling_block(S, k, dir);
+        if (bblk < 0) continue;
+        const int j = dir == 0 ? k - 1 : k - Sx;
+        const int Nj = S.NE[j];
+        const double* Ab = S.A + S.aoff[bblk];  // [N_j][N_k] = A_{j,k}
+        const int cj = S.xoff[j] - base;
+        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
+          const int r = i / Nj, c = i - r * Nj;  // A_{k,j}[r][c] = A_{j,k}[c][r]
+          R[r * W + cj + c] = Ab[c * Nk + r];
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = jl; j <= k; ++j) {
+      const int Nj = S.NE[j];
+      const int c0 = S.xoff[j] - base;
+      const int jlj = jlo_of(j, Sx);
+      const int Wj = S.xoff[j + 1] - S.xoff[jlj];
+      const double* Lj = S.L + S.loff[j];
+      const int offj = base - S.xoff[jlj];
+      const int len = c0;
+      if (len > 0) {
+        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
+          const int r = i / Nj, c = i - r * Nj;
+          if (j == k && c > r) continue;
+          const double* a = R + (size_t)r * W;
+          const double* bb = Lj + (size_t)c * Wj + offj;
+          double acc = 0.0;
+          for (int t = 0; t < len; ++t) acc = fma(a[t], bb[t], acc);
+          R[r * W + c0 + c] -= acc;
+        }
+        __syncthreads();
+      }
+      if (j < k) {
+        const double* Li = S.Linv + S.ioff[j];
+        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
+          const int r = i / Nj, c = i - r * Nj;
+          double acc = 0.0;
+          for (int t = 0; t <= c; ++t) acc = fma(R[r * W + c0 + t], Li[c * Nj + t], acc);
+          tmp[i] = acc;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
+          const int r = i / Nj, c = i - r * Nj;
+          R[r * W + c0 + c] = tmp[i];
+        }
+        __syncthreads();
+      } else {
+        for (int c = 0; c < Nk; ++c) {
+          if (threadIdx.x == 0) {
+            const double d = R[c * W + c0 + c];
+            if (!(d > 0.0) || !isfinite(d)) bad = 1;
+            dsh = sqrt(d);
+            R[c * W + c0 + c] = dsh;
+          }
+          __syncthreads();
+          if (bad) return false;
+          for (int r = c + 1 + threadIdx.x; r < Nk; r += blockDim.x) R[r * W + c0 + c] /= dsh;
+          __syncthreads();
+          const int m = Nk - c - 1;
+          for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+            const int r = c + 1 + i / m, t = c + 1 + i % m;
+            if (t <= r) R[r * W + c0 + t] -= R[r * W + c0 + c] * R[t * W + c0 + c];
+          }
+          __syncthreads();
+        }
+        // zero the strict upper triangle and invert the diagonal block
+        for (int i = threadIdx.x; i < Nk * Nk; i += blockDim.x) {
+          const int r = i / Nk, c = i - r * Nk;
+          if (c > r) R[r * W + c0 + c] = 0.0;
+        }
+        __syncthreads();
+        double* Li = S.Linv + S.ioff[k];
+        for (int col = threadIdx.x; col < Nk; col += blockDim.x) {
+          for (int r = 0; r < Nk; ++r) {
+            if (r < col) {
+              Li[r * Nk + col] = 0.0;
+              continue;
+            }
+            double sum = (r == col) ? 1.0 : 0.0;
+            for (int t = col; t < r; ++t) sum -= R[r * W + c0 + t] * Li[t * Nk + col];
+            Li[r * Nk + col] = sum / R[r * W + c0 + r];
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  return true;
+}
+
+// Solve L L^T out = in, using y as work. in and out may alias.
+__device__ void substitute(const SimDev& S, const double* in, double* out, double* sm) {
+  const int nsub = S.n_sub, Sx = S.Sx;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* t = sm;
+  double* y = S.y;
+  for (int k = 0; k < nsub; ++k) {
+    const int jl = jlo_of(k, Sx);
+    const int base = S.xoff[jl];
+    const int W = S.xoff[k + 1] - base;
+    const int Nk = S.NE[k];
+    const int off = W - Nk;
+    const double* R = S.L + S.loff[k];
+    for (int r = warp; r < Nk; r += nw) {
+      double acc = 0.0;
+      for (int g = lane; g < off; g += 32) acc = fma(R[(size_t)r * W + g], y[base + g], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) t[r] = in[S.xoff[k] + r] - acc;
+    }
+    __syncthreads();
+    const double* Li = S.Linv + S.ioff[k];
+    for (int r = threadIdx.x; r < Nk; r += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c <= r; ++c) acc = fma(Li[r * Nk + c], t[c], acc);
+      y[S.xoff[k] + r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int k = nsub - 1; k >= 0; --k) {
+    const int Nk = S.NE[k];
+    const int kmax = min(k + Sx, nsub - 1);
+    for (int c = warp; c < Nk; c += nw) {
+      double acc = 0.0;
+      for (int kk = k + 1; kk <= kmax; ++kk) {
+        const int jl2 = jlo_of(kk, Sx);
+        const int W2 = S.xoff[kk + 1] - S.xoff[jl2];
+        const int col = S.xoff[k] - S.xoff[jl2] + c;
+        const double* R2 = S.L + S.loff[kk];
+        const int N2 = S.NE[kk];
+        for (int r = lane; r < N2; r += 32) acc = fma(R2[(size_t)r * W2 + col], out[S.xoff[kk] + r], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) t[c] = y[S.xoff[k] + c] - acc;
+    }
+    __syncthreads();
+    const double* Li = S.Linv + S.ioff[k];
+    for (int c = threadIdx.x; c < Nk; c += blockDim.x) {
+      double acc = 0.0;
+      for (int r = c; r < Nk; ++r) acc = fma(Li[r * Nk + c], t[r], acc);
+      out[S.xoff[k] + c] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// r = b - A x with the block-sparse assembled A.
+__device__ void residual(const SimDev& S, const double* x, const double* b, double* r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int E = 0; E < S.n_sub; ++E) {
+    const int NE = S.NE[E], x0 = S.xoff[E];
+    for (int i = warp; i < NE; i += nw) {
+      double acc = 0.0;
+      const double* Ad = S.A + S.aoff[E];
+      for (int c = lane; c < NE; c += 32) acc = fma(Ad[i * NE + c], x[x0 + c], acc);
+      for (int dir = 0; dir < 2; ++dir) {  // neighbours below in the order: A_{E,j} = blk^T
+        const int bb = coupling_block(S, E, dir);
+        if (bb < 0) continue;
+        const int j = dir == 0 ? E - 1 : E - S.Sx;
+        const int Nj = S.NE[j];
+        const double* Ab = S.A + S.aoff[bb];  // [N_j][N_E]
+        for (int c = lane; c < Nj; c += 32) acc = fma(Ab[c * NE + i], x[S.xoff[j] + c], acc);
+      }
+      for (int dir = 2; dir < 4; ++dir) {  // neighbours above: A_{E,j} = blk
+        const int bb = coupling_block_up(S, E, dir);
+        if (bb < 0) continue;
+        const int j = dir == 2 ? E + 1 : E + S.Sx;
+        const int Nj = S.NE[j];
+        const double* Ab = S.A + S.aoff[bb];  // [N_E][N_j]
+        for (int c = lane; c < Nj; c += 32) acc = fma(Ab[i * Nj + c], x[S.xoff[j] + c], acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) r[x0 + i] = b[x0 + i] - acc;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void k_chol_solve(const SimDev* __restrict__ sims, const int* __restrict__ active,
+                             int refine) {
+  const SimDev& S = sims[active[blockIdx.x]];
+  if (S.status[0] != kStOk) return;
+  extern __shared__ double sm[];
+  if (!factor(S, sm)) {
+    if (threadIdx.x == 0) S.status[0] = kStNotSpd;
+    return;
+  }
+  substitute(S, S.b, S.x, sm);
+  for (int it = 0; it < refine; ++it) {
+    residual(S, S.x, S.b, S.rv);
+    substitute(S, S.rv, S.dv, sm);
+    for (int i = threadIdx.x; i < S.N; i += blockDim.x) S.x[i] += S.dv[i];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
+                     int mixed, cudaStream_t st) {
+  if (mixed)
+    k_assemble32<<<dim3(max_blocks, n_active), 128, 0, st>>>(sims, active);
+  else
+    k_assemble<<<dim3(max_blocks, n_active), 128, 0, st>>>(sims, active);
+}
+
+void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int refine,
+                       cudaStream_t st) {
+  const size_t smem = 64 * 64 * sizeof(double);  // max_NE <= 64 (checked at load)
+  k_chol_solve<<<n_active, 256, smem, st>>>(sims, active, refine);
+}
+
+}  // namespace lrbms

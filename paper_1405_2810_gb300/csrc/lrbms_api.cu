@@ -1,0 +1,533 @@
+// Host side of the C ABI declared in include/lrbms.h: context, device-memory
+// arena, slot table of resident simulations, offline-data loader and the
+// driver that enqueues the kernels of one online step (Algorithm 3, step 5)
+// for a batch of simulations.
+#include "lrbms.h"
+#include "lrbms_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <iterator>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using lrbms::SimDev;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over one cudaMalloc'd arena; free blocks are merged.
+class Arena {
+ public:
+  cudaError_t init(size_t cap) {
+    cap_ = align_up(cap);
+    cudaError_t e = cudaMalloc(&base_, cap_);
+    if (e != cudaSuccess) {
+      base_ = nullptr;
+      return e;
+    }
+    free_[0] = cap_;
+    return cudaSuccess;
+  }
+  void release() {
+    if (base_) cudaFree(base_);
+    base_ = nullptr;
+  }
+  // Returns offset or SIZE_MAX.
+  size_t alloc(size_t n) {
+    n = align_up(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        size_t off = it->first, rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        used_ += n;
+        return off;
+      }
+    }
+    return SIZE_MAX;
+  }
+  void free(size_t off, size_t n) {
+    n = align_up(n);
+    used_ -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  char* base() const { return base_; }
+  size_t used() const { return used_; }
+  size_t cap() const { return cap_; }
+
+ private:
+  char* base_ = nullptr;
+  size_t cap_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+struct Slot {
+  bool used = false;
+  size_t off = 0, bytes = 0;
+  SimDev d{};
+};
+
+}  // namespace
+
+struct lrbms_ctx {
+  int device = 0;
+  int precision = LRBMS_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Arena arena;
+  std::vector<Slot> slots;
+  SimDev* d_sims = nullptr;
+  int* d_active = nullptr;
+  std::vector<int> last_active;
+  std::string err;
+  long long launches = 0;
+};
+
+namespace {
+
+int fail(lrbms_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+int cuda_fail(lrbms_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LRBMS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+struct Layout {
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    size_t o = total;
+    total = align_up(total + bytes);
+    return o;
+  }
+};
+
+bool valid_sim(lrbms_ctx* ctx, int id) {
+  return ctx && id >= 0 && id < (int)ctx->slots.size() && ctx->slots[id].used;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
+  if (!out || !cfg) return LRBMS_E_ARG;
+  *out = nullptr;
+  if (cfg->max_slots < 1 || cfg->hbm_budget == 0 ||
+      (cfg->precision != LRBMS_FP64 && cfg->precision != LRBMS_MIXED))
+    return LRBMS_E_ARG;
+  lrbms_ctx* ctx = new lrbms_ctx();
+  ctx->device = cfg->device;
+  ctx->precision = cfg->precision;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return LRBMS_E_CUDA;
+  }
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return LRBMS_E_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (ctx->arena.init(cfg->hbm_budget) != cudaSuccess ||
+      cudaMalloc(&ctx->d_sims, sizeof(SimDev) * cfg->max_slots) != cudaSuccess ||
+      cudaMalloc(&ctx->d_active, sizeof(int) * cfg->max_slots) != cudaSuccess) {
+    ctx->arena.release();
+    if (ctx->d_sims) cudaFree(ctx->d_sims);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LRBMS_E_CUDA;
+  }
+  ctx->slots.resize(cfg->max_slots);
+  *out = ctx;
+  return LRBMS_OK;
+}
+
+int lrbms_destroy(lrbms_ctx* ctx) {
+  if (!ctx) return LRBMS_E_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->arena.release();
+  cudaFree(ctx->d_sims);
+  cudaFree(ctx->d_active);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return LRBMS_OK;
+}
+
+const char* lrbms_last_error(const lrbms_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+long long lrbms_launch_count(const lrbms_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int lrbms_memory(lrbms_ctx* ctx, size_t* used, size_t* capacity) {
+  if (!ctx) return LRBMS_E_ARG;
+  if (used) *used = ctx->arena.used();
+  if (capacity) *capacity = ctx->arena.cap();
+  return LRBMS_OK;
+}
+
+int lrbms_sync(lrbms_ctx* ctx) {
+  if (!ctx) return LRBMS_E_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LRBMS_OK;
+}
+
+int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offline* off,
+                       int* sim_id) {
+  if (!ctx || !pr || !off || !sim_id) return fail(ctx, LRBMS_E_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  const int nx = pr->nx, ny = pr->ny, Sx = pr->Sx, Sy = pr->Sy, M = off->M;
+  if (nx < 1 || ny < 1 || Sx < 1 || Sy < 1 || nx % Sx || ny % Sy)
+    return fail(ctx, LRBMS_E_ARG, "grid sizes must be positive and nx%Sx == ny%Sy == 0");
+  if (!(pr->Lx > 0) || !(pr->Ly > 0) || !(pr->eta_w > 0) || !(pr->eta_o > 0))
+    return fail(ctx, LRBMS_E_ARG, "domain lengths and viscosities must be positive");
+  if (M < 1 || M > lrbms::kMaxM) return fail(ctx, LRBMS_E_ARG, "M must be in 1..16");
+  if (!pr->perm || !pr->poro || !pr->bc_type || !pr->p_D || !pr->v_N || !pr->s_D || !pr->s0)
+    return fail(ctx, LRBMS_E_ARG, "missing problem array");
+  if (!off->N_E || !off->Gpinv || !off->Phi || !off->Dblk || !off->rhs || (!off->Fblk && Sx * Sy > 1))
+    return fail(ctx, LRBMS_E_ARG, "missing offline array");
+  if ((off->prof_idx == nullptr) == (off->prof == nullptr))
+    return fail(ctx, LRBMS_E_ARG, "exactly one of prof_idx and prof must be given");
+  if (pr->dt_mode == LRBMS_DT_CFL && !(pr->cfl > 0 && off->Lf > 0))
+    return fail(ctx, LRBMS_E_ARG, "CFL step needs cfl > 0 and Lf > 0");
+  if (pr->dt_mode == LRBMS_DT_FIXED && !(pr->dt_fixed > 0))
+    return fail(ctx, LRBMS_E_ARG, "fixed step needs dt_fixed > 0");
+  int slot = -1;
+  for (int i = 0; i < (int)ctx->slots.size(); ++i)
+    if (!ctx->slots[i].used) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return fail(ctx, LRBMS_E_BUDGET, "slot table full");
+
+  const int n_cells = nx * ny, n_sub = Sx * Sy, cx = nx / Sx, cy = ny / Sy, cells = cx * cy;
+  const int n_cf = Sy * (Sx - 1) + (Sy - 1) * Sx, nb = 2 * nx + 2 * ny;
+  const int nxf = (nx + 1) * ny, n_faces = nxf + nx * (ny + 1);
+  const int n_blocks = n_sub + n_cf;
+  // host copies of the basis sizes (may be a device pointer)
+  std::vector<int> NE(n_sub);
+  CK(cudaMemcpy(NE.data(), off->N_E, sizeof(int) * n_sub, cudaMemcpyDefault));
+  int max_NE = 0;
+  for (int E = 0; E < n_sub; ++E) {
+    if (NE[E] < 1 || NE[E] > 64 || NE[E] > 3 * cells)
+      return fail(ctx, LRBMS_E_FORMAT, "local basis sizes must be in 1..min(64, 3*cells_E)");
+    max_NE = NE[E] > max_NE ? NE[E] : max_NE;
+  }
+  std::vector<int> xoff(n_sub + 1, 0);
+  for (int E = 0; E < n_sub; ++E) xoff[E + 1] = xoff[E] + NE[E];
+  const int N = xoff[n_sub];
+  std::vector<long long> phi_off(n_sub);
+  long long phi_tot = 0;
+  for (int E = 0; E < n_sub; ++E) {
+    phi_off[E] = phi_tot;
+    phi_tot += (long long)NE[E] * 3 * cells;
+  }
+  std::vector<int> cf_m(n_cf), cf_p(n_cf);
+  {
+    int f = 0;
+    for (int J = 0; J < Sy; ++J)
+      for (int I = 0; I + 1 < Sx; ++I, ++f) cf_m[f] = J * Sx + I, cf_p[f] = J * Sx + I + 1;
+    for (int J = 0; J + 1 < Sy; ++J)
+      for (int I = 0; I < Sx; ++I, ++f) cf_m[f] = J * Sx + I, cf_p[f] = (J + 1) * Sx + I;
+  }
+  std::vector<long long> aoff(n_blocks + 1, 0);
+  for (int E = 0; E < n_sub; ++E) aoff[E + 1] = aoff[E] + (long long)NE[E] * NE[E];
+  for (int f = 0; f < n_cf; ++f)
+    aoff[n_sub + f + 1] = aoff[n_sub + f] + (long long)NE[cf_m[f]] * NE[cf_p[f]];
+  const long long a_tot = aoff[n_blocks];
+  const long long d_tot = aoff[n_sub];  // diagonal blocks
+  std::vector<long long> loff(n_sub + 1, 0), ioff(n_sub + 1, 0);
+  for (int k = 0; k < n_sub; ++k) {
+    const int jl = lrbms::jlo_of(k, Sx);
+    loff[k + 1] = loff[k] + (long long)NE[k] * (xoff[k + 1] - xoff[jl]);
+    ioff[k + 1] = ioff[k] + (long long)NE[k] * NE[k];
+  }
+  const int n_tiles = (n_cells + lrbms::kCellTile - 1) / lrbms::kCellTile;
+  const bool mixed = ctx->precision == LRBMS_MIXED;
+  const size_t Q = (size_t)M + 1;
+
+  Layout L;
+  const size_t o_perm = L.add(8 * (size_t)n_cells), o_poro = L.add(8 * (size_t)n_cells);
+  const size_t o_pidx = off->prof_idx ? L.add(n_cells) : 0;
+  const size_t o_prof = off->prof ? L.add(8 * (size_t)M * n_cells) : 0;
+  const size_t o_gp = L.add(8 * (size_t)M * M);
+  const size_t o_bct = L.add(nb), o_pD = L.add(8 * (size_t)nb), o_vN = L.add(8 * (size_t)nb),
+               o_sD = L.add(8 * (size_t)nb);
+  const size_t o_NE = L.add(4 * (size_t)n_sub), o_xoff = L.add(4 * (size_t)(n_sub + 1));
+  const size_t o_phioff = L.add(8 * (size_t)n_sub), o_aoff = L.add(8 * (size_t)(n_blocks + 1));
+  const size_t o_loff = L.add(8 * (size_t)(n_sub + 1)), o_ioff = L.add(8 * (size_t)(n_sub + 1));
+  const size_t o_phi = L.add(8 * (size_t)phi_tot);
+  const size_t o_comp = L.add(8 * Q * (size_t)a_tot);
+  const size_t o_rhs = L.add(8 * Q * (size_t)N);
+  const size_t o_phi32 = mixed ? L.add(4 * (size_t)phi_tot) : 0;
+  const size_t o_comp32 = mixed ? L.add(4 * Q * (size_t)a_tot) : 0;
+  const size_t o_s = L.add(16 * (size_t)n_cells), o_p = L.add(24 * (size_t)n_cells);
+  const size_t o_F = L.add(8 * (size_t)n_faces);
+  const size_t o_x = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N), o_y = L.add(8 * (size_t)N),
+               o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N);
+  const size_t o_A = L.add(8 * (size_t)a_tot);
+  const size_t o_L = L.add(8 * (size_t)loff[n_sub]), o_Li = L.add(8 * (size_t)ioff[n_sub]);
+  const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
+  const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
+  const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
+  const size_t o_status = L.add(4), o_steps = L.add(4);
+  (void)d_tot;
+
+  const size_t aoffset = ctx->arena.alloc(L.total);
+  if (aoffset == SIZE_MAX) return fail(ctx, LRBMS_E_BUDGET, "device-memory budget exhausted");
+  char* base = ctx->arena.base() + aoffset;
+  auto P = [&](size_t o) { return (void*)(base + o); };
+
+  SimDev d{};
+  d.nx = nx; d.ny = ny; d.Sx = Sx; d.Sy = Sy; d.cx = cx; d.cy = cy;
+  d.n_cells = n_cells; d.n_sub = n_sub; d.n_cf = n_cf; d.nb = nb; d.nxf = nxf; d.n_faces = n_faces;
+  d.M = M; d.N = N; d.max_NE = max_NE; d.n_tiles = n_tiles; d.n_blocks = n_blocks;
+  d.relperm = pr->relperm; d.swapped = pr->mean_weights; d.prof_mode = off->prof_idx ? 0 : 1;
+  d.dt_mode = pr->dt_mode;
+  d.hx = pr->Lx / nx; d.hy = pr->Ly / ny; d.vol = d.hx * d.hy; d.c_pen = off->c_pen; d.Lf = off->Lf;
+  d.inv_eta_w = 1.0 / pr->eta_w; d.inv_eta_o = 1.0 / pr->eta_o; d.cfl = pr->cfl;
+  d.dt_fixed = pr->dt_fixed; d.dt_max = pr->dt_max;
+  // lambda(0) and lambda(1) for both relative permeability laws (k_rw(0)=0,
+  // k_rw(1)=1, k_ro(0)=1, k_ro(1)=0)
+  d.lam0 = d.inv_eta_o;
+  d.lam1 = d.inv_eta_w;
+  d.perm = (const double*)P(o_perm); d.poro = (const double*)P(o_poro);
+  d.prof_idx = off->prof_idx ? (const uint8_t*)P(o_pidx) : nullptr;
+  d.prof = off->prof ? (const double*)P(o_prof) : nullptr;
+  d.Gpinv = (const double*)P(o_gp);
+  d.bc_type = (const int8_t*)P(o_bct); d.p_D = (const double*)P(o_pD);
+  d.v_N = (const double*)P(o_vN); d.s_D = (const double*)P(o_sD);
+  d.NE = (const int*)P(o_NE); d.xoff = (const int*)P(o_xoff);
+  d.phi_off = (const long long*)P(o_phioff); d.aoff = (const long long*)P(o_aoff);
+  d.loff = (const long long*)P(o_loff); d.ioff = (const long long*)P(o_ioff);
+  d.Phi = (const double*)P(o_phi); d.comp = (const double*)P(o_comp); d.rhs = (const double*)P(o_rhs);
+  d.Phi32 = mixed ? (const float*)P(o_phi32) : nullptr;
+  d.comp32 = mixed ? (const float*)P(o_comp32) : nullptr;
+  d.s = (double*)P(o_s); d.p = (double*)P(o_p); d.F = (double*)P(o_F);
+  d.x = (double*)P(o_x); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
+  d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv);
+  d.A = (double*)P(o_A); d.L = (double*)P(o_L); d.Linv = (double*)P(o_Li);
+  d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
+  d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);
+  d.status = (int*)P(o_status); d.steps = (int*)P(o_steps);
+
+  cudaStream_t st = ctx->stream;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+  };
+  const size_t nc8 = 8 * (size_t)n_cells;
+  CK(cp(P(o_perm), pr->perm, nc8));
+  CK(cp(P(o_poro), pr->poro, nc8));
+  if (off->prof_idx) CK(cp(P(o_pidx), off->prof_idx, n_cells));
+  if (off->prof) CK(cp(P(o_prof), off->prof, nc8 * M));
+  CK(cp(P(o_gp), off->Gpinv, 8 * (size_t)M * M));
+  CK(cp(P(o_bct), pr->bc_type, nb));
+  CK(cp(P(o_pD), pr->p_D, 8 * (size_t)nb));
+  CK(cp(P(o_vN), pr->v_N, 8 * (size_t)nb));
+  CK(cp(P(o_sD), pr->s_D, 8 * (size_t)nb));
+  CK(cp(P(o_phi), off->Phi, 8 * (size_t)phi_tot));
+  CK(cp(P(o_comp), off->Dblk, 8 * Q * (size_t)aoff[n_sub]));
+  if (n_cf) CK(cp((char*)P(o_comp) + 8 * Q * aoff[n_sub], off->Fblk, 8 * Q * (size_t)(a_tot - aoff[n_sub])));
+  CK(cp(P(o_rhs), off->rhs, 8 * Q * (size_t)N));
+  CK(cp(P(o_s), pr->s0, nc8));
+  // metadata from host vectors (pageable: staged before the call returns)
+  CK(cp(P(o_NE), NE.data(), 4 * (size_t)n_sub));
+  CK(cp(P(o_xoff), xoff.data(), 4 * (size_t)(n_sub + 1)));
+  CK(cp(P(o_phioff), phi_off.data(), 8 * (size_t)n_sub));
+  CK(cp(P(o_aoff), aoff.data(), 8 * (size_t)(n_blocks + 1)));
+  CK(cp(P(o_loff), loff.data(), 8 * (size_t)(n_sub + 1)));
+  CK(cp(P(o_ioff), ioff.data(), 8 * (size_t)(n_sub + 1)));
+  CK(cudaMemsetAsync(P(o_scal), 0, 8 * 4, st));
+  CK(cudaMemsetAsync(P(o_theta), 0, 8 * lrbms::kMaxM, st));
+  CK(cudaMemsetAsync(P(o_status), 0, 4, st));
+  CK(cudaMemsetAsync(P(o_steps), 0, 4, st));
+  CK(cudaMemsetAsync(P(o_p), 0, 24 * (size_t)n_cells, st));
+  CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
+  CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
+  if (mixed) {
+    lrbms::launch_to_float((const double*)P(o_phi), (float*)P(o_phi32), phi_tot, st);
+    lrbms::launch_to_float((const double*)P(o_comp), (float*)P(o_comp32), Q * a_tot, st);
+    ctx->launches += 2;
+  }
+  CK(cp(ctx->d_sims + slot, &d, sizeof(SimDev)));
+  CK(cudaStreamSynchronize(st));  // caller buffers may be freed on return
+  CK(cudaGetLastError());
+  Slot& s = ctx->slots[slot];
+  s.used = true;
+  s.off = aoffset;
+  s.bytes = L.total;
+  s.d = d;
+  ctx->last_active.clear();
+  *sim_id = slot;
+  return LRBMS_OK;
+}
+
+int lrbms_release(lrbms_ctx* ctx, int id) {
+  if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  CK(cudaStreamSynchronize(ctx->stream));
+  Slot& s = ctx->slots[id];
+  ctx->arena.free(s.off, s.bytes);
+  s = Slot();
+  ctx->last_active.clear();
+  return LRBMS_OK;
+}
+
+int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* status) {
+  if (!ctx || n_sims < 1 || !ids || n_steps < 0) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  if (n_sims > (int)ctx->slots.size()) return fail(ctx, LRBMS_E_ARG, "too many simulations");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<int> act(ids, ids + n_sims);
+  int max_tiles = 0, max_blocks = 0, max_sub = 0, max_faces = 0;
+  for (int id : act) {
+    if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+    const SimDev& d = ctx->slots[id].d;
+    max_tiles = std::max(max_tiles, d.n_tiles);
+    max_blocks = std::max(max_blocks, d.n_blocks + d.n_sub);
+    max_sub = std::max(max_sub, d.n_sub);
+    max_faces = std::max(max_faces, d.n_faces);
+  }
+  cudaStream_t st = ctx->stream;
+  if (act != ctx->last_active) {
+    CK(cudaMemcpyAsync(ctx->d_active, act.data(), sizeof(int) * n_sims, cudaMemcpyHostToDevice, st));
+    ctx->last_active = act;
+  }
+  const int mixed = ctx->precision == LRBMS_MIXED;
+  const int refine = 1;
+  for (int k = 0; k < n_steps; ++k) {
+    lrbms::launch_fit(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st);
+    lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, refine, st);
+    lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st);
+    lrbms::launch_flux(ctx->d_sims, ctx->d_active, n_sims, max_faces, st);
+    lrbms::launch_cfl(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    lrbms::launch_transport(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
+    ctx->launches += 8;
+  }
+  CK(cudaGetLastError());
+  if (status) {
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_sims; ++i)
+      CK(cudaMemcpy(&status[i], ctx->slots[act[i]].d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  return LRBMS_OK;
+}
+
+size_t lrbms_field_bytes(lrbms_ctx* ctx, int id, int field) {
+  if (!valid_sim(ctx, id)) return 0;
+  const SimDev& d = ctx->slots[id].d;
+  switch (field) {
+    case LRBMS_FIELD_THETA: return 8 * (size_t)d.M;
+    case LRBMS_FIELD_A: {
+      // sum of block sizes: computed from the host copy of the layout
+      size_t n = 0;
+      std::vector<long long> a(d.n_blocks + 1);
+      if (cudaMemcpy(a.data(), d.aoff, 8 * a.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+      n = (size_t)a[d.n_blocks];
+      return 8 * n;
+    }
+    case LRBMS_FIELD_RHS:
+    case LRBMS_FIELD_X: return 8 * (size_t)d.N;
+    case LRBMS_FIELD_P: return 24 * (size_t)d.n_cells;
+    case LRBMS_FIELD_FLUX: return 8 * (size_t)d.n_faces;
+    case LRBMS_FIELD_S: return 8 * (size_t)d.n_cells;
+    case LRBMS_FIELD_DT: return 8;
+    case LRBMS_FIELD_STATUS: return 4;
+    default: return 0;
+  }
+}
+
+int lrbms_get_field(lrbms_ctx* ctx, int id, int field, void* dst, size_t bytes) {
+  if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  if (!dst || bytes != lrbms_field_bytes(ctx, id, field))
+    return fail(ctx, LRBMS_E_ARG, "destination size does not match the field");
+  CK(cudaStreamSynchronize(ctx->stream));
+  const SimDev& d = ctx->slots[id].d;
+  const void* src = nullptr;
+  int steps = 0;
+  switch (field) {
+    case LRBMS_FIELD_THETA: src = d.theta; break;
+    case LRBMS_FIELD_A: src = d.A; break;
+    case LRBMS_FIELD_RHS: src = d.b; break;
+    case LRBMS_FIELD_X: src = d.x; break;
+    case LRBMS_FIELD_P: src = d.p; break;
+    case LRBMS_FIELD_FLUX: src = d.F; break;
+    case LRBMS_FIELD_S:
+      CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
+      src = d.s + (size_t)(steps & 1) * d.n_cells;
+      break;
+    case LRBMS_FIELD_DT: src = d.scal + 1; break;
+    case LRBMS_FIELD_STATUS: src = d.status; break;
+    default: return fail(ctx, LRBMS_E_ARG, "unknown field");
+  }
+  CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
+  return LRBMS_OK;
+}
+
+int lrbms_get_state(lrbms_ctx* ctx, int id, double* s, double* t, double* mass_out) {
+  if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  const SimDev& d = ctx->slots[id].d;
+  if (s) {
+    int rc = lrbms_get_field(ctx, id, LRBMS_FIELD_S, s, 8 * (size_t)d.n_cells);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  double sc[4];
+  CK(cudaMemcpy(sc, d.scal, sizeof(sc), cudaMemcpyDeviceToHost));
+  if (t) *t = sc[0];
+  if (mass_out) *mass_out = sc[2];
+  return LRBMS_OK;
+}
+
+int lrbms_set_saturation(lrbms_ctx* ctx, int id, const double* s) {
+  if (!valid_sim(ctx, id) || !s) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  const SimDev& d = ctx->slots[id].d;
+  CK(cudaStreamSynchronize(ctx->stream));
+  int steps = 0;
+  CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(d.s + (size_t)(steps & 1) * d.n_cells, s, 8 * (size_t)d.n_cells, cudaMemcpyDefault));
+  return LRBMS_OK;
+}
+
+int lrbms_run(lrbms_ctx* ctx, int id, int n_steps, double* s_out, double* p_out, double* flux_out) {
+  if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  int st = 0;
+  int rc = lrbms_step(ctx, 1, &id, n_steps, &st);
+  if (rc) return rc;
+  const SimDev& d = ctx->slots[id].d;
+  if (s_out && (rc = lrbms_get_field(ctx, id, LRBMS_FIELD_S, s_out, 8 * (size_t)d.n_cells))) return rc;
+  if (p_out && (rc = lrbms_get_field(ctx, id, LRBMS_FIELD_P, p_out, 24 * (size_t)d.n_cells))) return rc;
+  if (flux_out && (rc = lrbms_get_field(ctx, id, LRBMS_FIELD_FLUX, flux_out, 8 * (size_t)d.n_faces)))
+    return rc;
+  if (st != LRBMS_OK) return fail(ctx, st, "simulation stopped with a non-zero status");
+  return LRBMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+"""ctypes binding of the C ABI in include/lrbms.h.
+
+Argument marshalling only: every step of the online scheme runs in the CUDA
+kernels of liblrbms.so. Arrays may be NumPy arrays (host) or objects with a
+``data_ptr()`` method such as CUDA torch tensors (device); they must be
+C-contiguous with the dtype the header states. If the shared library is
+missing, every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrbms.so")
+
+LRBMS_OK = 0
+LRBMS_E_ARG = -1
+LRBMS_E_BUDGET = -2
+LRBMS_E_CUDA = -3
+LRBMS_E_NOT_SPD = -4
+LRBMS_E_NONFINITE = -5
+LRBMS_E_TIMEOUT = -6
+LRBMS_E_FORMAT = -7
+LRBMS_E_STATE = -9
+LRBMS_FP64 = 0
+LRBMS_MIXED = 1
+LRBMS_COREY = 0
+LRBMS_LINEAR = 1
+LRBMS_DT_CFL = 0
+LRBMS_DT_FIXED = 1
+FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS = range(9)
+
+EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_release", "lrbms_step",
+            "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
+            "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count",
+            "lrbms_last_error"]
+
+
+class LrbmsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lrbms error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_slots", C.c_int), ("hbm_budget", C.c_size_t),
+                ("stream", C.c_void_p), ("device", C.c_int)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("Sx", C.c_int), ("Sy", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double),
+                ("perm", C.c_void_p), ("poro", C.c_void_p),
+                ("eta_w", C.c_double), ("eta_o", C.c_double), ("relperm", C.c_int),
+                ("bc_type", C.c_void_p), ("p_D", C.c_void_p), ("v_N", C.c_void_p),
+                ("s_D", C.c_void_p), ("s0", C.c_void_p),
+                ("cfl", C.c_double), ("dt_mode", C.c_int), ("dt_fixed", C.c_double),
+                ("dt_max", C.c_double), ("mean_weights", C.c_int)]
+
+
+class Offline(C.Structure):
+    _fields_ = [("M", C.c_int), ("N_E", C.c_void_p), ("prof_idx", C.c_void_p), ("prof", C.c_void_p),
+                ("Gpinv", C.c_void_p), ("Phi", C.c_void_p), ("Dblk", C.c_void_p),
+                ("Fblk", C.c_void_p), ("rhs", C.c_void_p), ("c_pen", C.c_double), ("Lf", C.c_double)]
+
+
+_lib = None
+
+
+def library() -> C.CDLL:
+    """Load liblrbms.so (built in-tree by paper_1405_2810_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1405_2810_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        vp, i, sz, dp = C.c_void_p, C.c_int, C.c_size_t, C.POINTER(C.c_double)
+        lib.lrbms_create.argtypes = [C.POINTER(vp), C.POINTER(Config)]
+        lib.lrbms_destroy.argtypes = [vp]
+        lib.lrbms_offline_load.argtypes = [vp, C.POINTER(Problem), C.POINTER(Offline), C.POINTER(i)]
+        lib.lrbms_release.argtypes = [vp, i]
+        lib.lrbms_step.argtypes = [vp, i, vp, i, vp]
+        lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
+        lib.lrbms_get_state.argtypes = [vp, i, vp, dp, dp]
+        lib.lrbms_set_saturation.argtypes = [vp, i, vp]
+        lib.lrbms_get_field.argtypes = [vp, i, i, vp, sz]
+        lib.lrbms_field_bytes.argtypes = [vp, i, i]
+        lib.lrbms_field_bytes.restype = sz
+        lib.lrbms_sync.argtypes = [vp]
+        lib.lrbms_memory.argtypes = [vp, C.POINTER(sz), C.POINTER(sz)]
+        lib.lrbms_launch_count.argtypes = [vp]
+        lib.lrbms_launch_count.restype = C.c_longlong
+        lib.lrbms_last_error.argtypes = [vp]
+        lib.lrbms_last_error.restype = C.c_char_p
+        _lib = lib
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays passed to lrbms must be C-contiguous")
+    return a.ctypes.data
+
+
+def _check(ctx, rc):
+    if rc != LRBMS_OK:
+        msg = library().lrbms_last_error(ctx).decode() if ctx else ""
+        raise LrbmsError(rc, msg)
+
+
+def _as(a, dtype):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ------------------------------------------------------------------ C-ABI names
+def lrbms_create(precision=LRBMS_FP64, max_slots=64, hbm_budget=8 << 30, stream=None, device=0):
+    cfg = Config(precision, max_slots, hbm_budget, stream, device)
+    h = C.c_void_p()
+    _check(None, library().lrbms_create(C.byref(h), C.byref(cfg)))
+    return h
+
+
+def lrbms_destroy(ctx):
+    _check(ctx, library().lrbms_destroy(ctx))
+
+
+def lrbms_offline_load(ctx, problem: dict, offline: dict) -> int:
+    """problem/offline: dicts with the fields of lrbms_problem / lrbms_offline
+    (arrays as NumPy arrays or device tensors)."""
+    keep = {}
+    pa = {k: _as(problem[k], dt) for k, dt in (("perm", np.float64), ("poro", np.float64),
+                                             ("bc_type", np.int8), ("p_D", np.float64),
+                                             ("v_N", np.float64), ("s_D", np.float64),
+                                             ("s0", np.float64))}
+    keep.update(pa)
+    pr = Problem(problem["nx"], problem["ny"], problem["Sx"], problem["Sy"], problem["Lx"], problem["Ly"],
+                 _ptr(pa["perm"]), _ptr(pa["poro"]), problem["eta_w"], problem["eta_o"],
+                 problem.get("relperm", LRBMS_COREY), _ptr(pa["bc_type"]), _ptr(pa["p_D"]),
+                 _ptr(pa["v_N"]), _ptr(pa["s_D"]), _ptr(pa["s0"]), problem.get("cfl", 0.5),
+                 problem.get("dt_mode", LRBMS_DT_CFL), problem.get("dt_fixed", 0.0),
+                 problem.get("dt_max", 0.0), problem.get("mean_weights", 0))
+    oa = {k: _as(offline.get(k), dt) for k, dt in (("N_E", np.int32), ("prof_idx", np.uint8),
+                                                 ("prof", np.float64), ("Gpinv", np.float64),
+                                                 ("Phi", np.float64), ("Dblk", np.float64),
+                                                 ("Fblk", np.float64), ("rhs", np.float64))}
+    keep.update(oa)
+    off = Offline(offline["M"], _ptr(oa["N_E"]), _ptr(oa["prof_idx"]), _ptr(oa["prof"]), _ptr(oa["Gpinv"]),
+                  _ptr(oa["Phi"]), _ptr(oa["Dblk"]), _ptr(oa["Fblk"]), _ptr(oa["rhs"]),
+                  offline["c_pen"], offline["Lf"])
+    sid = C.c_int()
+    _check(ctx, library().lrbms_offline_load(ctx, C.byref(pr), C.byref(off), C.byref(sid)))
+    del keep
+    return sid.value
+
+
+def lrbms_release(ctx, sim_id: int):
+    _check(ctx, library().lrbms_release(ctx, sim_id))
+
+
+def lrbms_step(ctx, sim_ids, n_steps: int = 1, wait: bool = True):
+    ids = np.ascontiguousarray(sim_ids, dtype=np.int32)
+    status = np.zeros(len(ids), dtype=np.int32) if wait else None
+    _check(ctx, library().lrbms_step(ctx, len(ids), _ptr(ids), n_steps, _ptr(status)))
+    return status
+
+
+def lrbms_run(ctx, sim_id: int, n_steps: int, s_out=None, p_out=None, flux_out=None):
+    _check(ctx, library().lrbms_run(ctx, sim_id, n_steps, _ptr(s_out), _ptr(p_out), _ptr(flux_out)))
+
+
+def lrbms_get_state(ctx, sim_id: int, s_out=None):
+    t, m = C.c_double(), C.c_double()
+    _check(ctx, library().lrbms_get_state(ctx, sim_id, _ptr(s_out), C.byref(t), C.byref(m)))
+    return t.value, m.value
+
+
+def lrbms_set_saturation(ctx, sim_id: int, s):
+    s = _as(s, np.float64)
+    _check(ctx, library().lrbms_set_saturation(ctx, sim_id, _ptr(s)))
+
+
+def lrbms_field_bytes(ctx, sim_id: int, field: int) -> int:
+    return int(library().lrbms_field_bytes(ctx, sim_id, field))
+
+
+def lrbms_get_field(ctx, sim_id: int, field: int, dtype=np.float64):
+    nb = lrbms_field_bytes(ctx, sim_id, field)
+    if nb == 0:
+        raise LrbmsError(LRBMS_E_ARG, "unknown field or simulation")
+    out = np.empty(nb // np.dtype(dtype).itemsize, dtype=dtype)
+    _check(ctx, library().lrbms_get_field(ctx, sim_id, field, _ptr(out), nb))
+    return out
+
+
+def lrbms_sync(ctx):
+    _check(ctx, library().lrbms_sync(ctx))
+
+
+def lrbms_memory(ctx):
+    u, c = C.c_size_t(), C.c_size_t()
+    _check(ctx, library().lrbms_memory(ctx, C.byref(u), C.byref(c)))
+    return u.value, c.value
+
+
+def lrbms_launch_count(ctx) -> int:
+    return int(library().lrbms_launch_count(ctx))
+
+
+def lrbms_last_error(ctx) -> str:
+    return library().lrbms_last_error(ctx).decode()

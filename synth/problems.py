@@ -21,8 +21,10 @@ Workloads (seeded stand-ins; the paper's fields exist only as figures):
            U[2, 20] per simulation, basis sizes U{5..30} per subdomain
   served   grid n in {64,128,256,512}, subdomains S in {4,8,16,32}, n/S >= 4
   paper_bc the paper's benchmark boundary conditions (Section 6): Dirichlet
-           inflow on the left, Neumann outflow v_N on the right, no-flow
-           top/bottom
+           inflow on the left (p = p_inflow, 10 in the paper), Neumann outflow
+           v_N = 3e-4 on the right, no-flow top/bottom
+  rect     nx x ny fine grid with Sx x Sy subdomains given as n=(nx, ny),
+           S=(Sx, Sy) (sizes that leave ragged tiles)
   strip    n x 1 strip with Dirichlet pressure at both ends (1D transport)
 All fields use porosity 0.2, eta_w = 1, eta_o = viscosity ratio, s0 = 0.
 Default boundary conditions: left Dirichlet p = 1 with s_D = 1 (injection),
@@ -101,7 +103,8 @@ def default_bcs(nx: int, ny: int, p_left: float = 1.0, p_right: float = 0.0,
 
 
 def make_problem(name: str, seed: int | None = None, sim_index: int = 0,
-                 n: int | None = None, S: int | None = None, **overrides) -> Problem:
+                 n: int | None = None, S: int | None = None, p_inflow: float = 10.0,
+                 **overrides) -> Problem:
     """Build one seeded workload by name (see module docstring)."""
     if name == "small":
         nx = ny = 32
@@ -141,6 +144,13 @@ def make_problem(name: str, seed: int | None = None, sim_index: int = 0,
         perm = lognormal_field(nx, ny, 300.0, 60.0, 1.0, (30.0, 6.0), sd)
         ratio = 0.008 / 0.00130581
         steps, nmax = 50, 10
+    elif name == "rect":
+        nx, ny = (48, 40) if n is None else n
+        Sx, Sy = (4, 5) if S is None else S
+        sd = 4242 if seed is None else seed
+        perm = lognormal_field(nx, ny, 1.0, 1.0, 1.0, (0.1, 0.1), sd)
+        ratio = 4.0
+        steps, nmax = 20, 8
     elif name == "strip":
         nx = 64 if n is None else n
         ny = 1
@@ -154,7 +164,7 @@ def make_problem(name: str, seed: int | None = None, sim_index: int = 0,
 
     if name == "paper_bc":
         Lx, Ly = 300.0, 60.0
-        bcs = default_bcs(nx, ny, p_left=10.0, right="neumann", v_out=3e-4)
+        bcs = default_bcs(nx, ny, p_left=p_inflow, right="neumann", v_out=3e-4)
         eta_w, eta_o = 0.00130581, 0.008
         relperm = "linear"
     else:
