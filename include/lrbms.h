@@ -187,6 +187,35 @@ int lrbms_get_field(lrbms_ctx* ctx, int sim_id, int field, void* dst, size_t byt
 /* Size in bytes of a field for a resident simulation (0 if unknown). */
 size_t lrbms_field_bytes(lrbms_ctx* ctx, int sim_id, int field);
 
+/* Offline phase on the GPU (Algorithm 2 with a given list of snapshot
+ * parameters instead of the greedy selection, then Section 4.4): initial
+ * pressure and velocity with lambda(s0), time-of-flight, threshold profiles,
+ * pseudo-inverse of the profile Gram matrix, fine snapshots at the parameters
+ * mu, local bases (unit function first, FP64 Gram-Schmidt in L2(E)) and the
+ * projected components. Fine systems are solved with the same block
+ * Cholesky as the reduced ones. */
+typedef struct {
+  int M;             /* number of mobility profiles, 3..16                     */
+  int n_steps_T;     /* profile thresholds use T = n_steps_T * dt0, dt0 the CFL
+                        step of the initial velocity                          */
+  const int* N_E;    /* [Sx*Sy] local basis sizes to build                     */
+  int n_snap;        /* number of snapshot parameters                          */
+  const double* mu;  /* [n_snap][M] snapshot parameters (drawn by the caller)  */
+  double c_pen;      /* penalty scale c_f / max(eta_w, eta_o)                  */
+} lrbms_build_opts;
+
+/* Build the offline data of n_prob problems (same grids, one options entry
+ * each) and admit n_copies simulations per problem. Copy r of problem p uses
+ * local bases rotated by the orthogonal matrices rot[p*n_copies + r]
+ * (concatenated row-major N_E x N_E per subdomain; NULL entry or NULL rot: no
+ * rotation), which changes the stored bytes but not the online results.
+ * sim_ids receives n_prob*n_copies slots. Scratch device memory is taken with
+ * cudaMalloc and released before return. LRBMS_E_FORMAT if the snapshots do
+ * not span the requested local basis sizes. */
+int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
+                        const lrbms_build_opts* opts, int n_copies,
+                        const double* const* rot, int* sim_ids);
+
 /* Wait for all enqueued work. */
 int lrbms_sync(lrbms_ctx* ctx);
 

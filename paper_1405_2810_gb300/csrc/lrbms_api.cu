@@ -184,6 +184,9 @@ int lrbms_destroy(lrbms_ctx* ctx) {
 
 const char* lrbms_last_error(const lrbms_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
+cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx) { return ctx->stream; }
+int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+
 long long lrbms_launch_count(const lrbms_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 int lrbms_memory(lrbms_ctx* ctx, size_t* used, size_t* capacity) {

@@ -1,0 +1,1066 @@
+// Offline phase on the GPU: Algorithm 2 (initial pressure and velocity,
+// time-of-flight, mobility profiles, snapshots and local Gram-Schmidt; the
+// greedy selection is replaced by a caller-given list of snapshot parameters)
+// followed by the offline/online decomposition of Section 4.4.
+//
+// The fine SWIP-DG system (Section 3.2) of a P1 pressure on one-cell blocks
+// has exactly the 5-point block pattern the online solver factorises, so every
+// fine solve here runs through the same envelope block Cholesky
+// (launch_chol_solve) on a "fine" system with Sx = nx, Sy = ny and three
+// unknowns per block.
+//
+// Local SWIP matrices use closed forms for rectangles: on a face with
+// tangential coordinate t in [-1,1], the P1 traces are alpha + beta t, so
+// int_f (alpha_a + beta_a t)(alpha_b + beta_b t) = |f| (alpha_a alpha_b +
+// beta_a beta_b / 3) and int_f t = 0; volume terms are
+// gamma kappa |e| diag(0, 4/hx^2, 4/hy^2).
+#include "lrbms.h"
+#include "lrbms_internal.cuh"
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace lrbms {
+
+// Fine-grid data of one problem being built.
+struct FineDev {
+  int nx, ny, Sx, Sy, cx, cy, n_cells, nxf, n_faces, nb, M, relperm, swapped;
+  double hx, hy, vol, c_pen, inv_eta_w, inv_eta_o, lam0, lam1;
+  const double* perm;
+  const double* poro;
+  const int8_t* bc_type;
+  const double* p_D;
+  const double* v_N;
+  const double* s_D;
+  const double* s0;
+  uint8_t* prof_idx;
+};
+
+// One fine system to assemble: mobility gamma per cell given by
+//   mode 0: lambda(s0), mode 1: sum_q mu_q Lambda^q, mode 2: Lambda^q (q = prof)
+// and the terms selected by `parts` (bit 0 penalty + Dirichlet-penalty and
+// Neumann right-hand side, bit 1 volume + consistency + Dirichlet-consistency
+// right-hand side).
+struct SysJob {
+  int prob, mode, parts, q;
+  const double* mu;  // [M]
+  double* D;         // [n_cells][9] diagonal blocks
+  double* O;         // blocks per interior face in coarse-face order [9] (row e1, col e2)
+  double* r;         // [n_cells][3]
+};
+
+namespace {
+
+__device__ __forceinline__ double mob_total(const FineDev& f, double s) {
+  if (f.relperm == 0) return s * s * f.inv_eta_w + (1.0 - s) * (1.0 - s) * f.inv_eta_o;
+  return s * f.inv_eta_w + (1.0 - s) * f.inv_eta_o;
+}
+
+__device__ __forceinline__ double job_gamma(const FineDev& f, const SysJob& J, int e) {
+  if (J.mode == 0) return mob_total(f, f.s0[e]);
+  const int k = f.prof_idx[e];
+  if (J.mode == 2) return (J.q + 1 >= k) ? f.lam1 : f.lam0;
+  double g = 0.0;
+  for (int q = 0; q < f.M; ++q) g += J.mu[q] * ((q + 1 >= k) ? f.lam1 : f.lam0);
+  return g;
+}
+
+// Trace coefficients on a face of a cell: value = alpha + beta t.
+// side = +1: the face at the cell's + end along `axis`, -1: at its - end.
+__device__ __forceinline__ void traces(int axis, int side, double* al, double* be) {
+  al[0] = 1.0; be[0] = 0.0;
+  if (axis == 0) {
+    al[1] = side; be[1] = 0.0;
+    al[2] = 0.0; be[2] = 1.0;
+  } else {
+    al[1] = 0.0; be[1] = 1.0;
+    al[2] = side; be[2] = 0.0;
+  }
+}
+
+// Normal derivative (along +axis) of each local basis function.
+__device__ __forceinline__ void dnormal(const FineDev& f, int axis, double* g) {
+  g[0] = 0.0;
+  g[1] = axis == 0 ? 2.0 / f.hx : 0.0;
+  g[2] = axis == 1 ? 2.0 / f.hy : 0.0;
+}
+
+// 6x6 local matrix of an interior face (rows/cols 0..2: e1, 3..5: e2), normal
+// +axis from e1 to e2: penalty sigma/h int [.][.], consistency and symmetry
+// -int {gamma kappa grad . n}[.] (reading R1 sign), weights tau (reading R3).
+__device__ void interior_face_matrix(const FineDev& f, int axis, double k1, double g1, double k2,
+                                     double g2, int parts, double* Mx) {
+  const double flen = axis == 0 ? f.hy : f.hx;
+  double a1[3], b1[3], a2[3], b2[3], dn[3];
+  traces(axis, +1, a1, b1);
+  traces(axis, -1, a2, b2);
+  dnormal(f, axis, dn);
+  double al[6], be[6], mn[6];
+  const double t1 = (f.swapped ? k2 : k1) / (k1 + k2), t2 = (f.swapped ? k1 : k2) / (k1 + k2);
+  for (int k = 0; k < 3; ++k) {
+    al[k] = a1[k]; be[k] = b1[k]; mn[k] = t1 * g1 * k1 * dn[k];
+    al[3 + k] = -a2[k]; be[3 + k] = -b2[k]; mn[3 + k] = t2 * g2 * k2 * dn[k];
+  }
+  const double sig = f.c_pen * 2.0 * k1 * k2 / (k1 + k2);  // sigma/h_f * |f| = sigma (h_f = |f|)
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) {
+      double v = 0.0;
+      if (parts & 1) v += sig * (al[a] * al[b] + be[a] * be[b] / 3.0);
+      if (parts & 2) v -= flen * (al[a] * mn[b] + mn[a] * al[b]);
+      Mx[a * 6 + b] = v;
+    }
+}
+
+// Boundary face of cell e on side `side` along `axis` (outward normal
+// side * e_axis): 3x3 matrix and right-hand side.
+__device__ void boundary_face(const FineDev& f, int axis, int side, int b, double ke, double ge,
+                              int parts, double* Mx, double* rv) {
+  const double flen = axis == 0 ? f.hy : f.hx;
+  double al[3], be[3], dn[3], mn[3];
+  traces(axis, side, al, be);
+  dnormal(f, axis, dn);
+  for (int k = 0; k < 3; ++k) mn[k] = ge * ke * side * dn[k];
+  for (int k = 0; k < 9; ++k) Mx[k] = 0.0;
+  for (int k = 0; k < 3; ++k) rv[k] = 0.0;
+  if (f.bc_type[b] == 1) {
+    const double sig = f.c_pen * ke;
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+        if (parts & 1) v += sig * (al[a] * al[c] + be[a] * be[c] / 3.0);
+        if (parts & 2) v -= flen * (al[a] * mn[c] + mn[a] * al[c]);
+        Mx[a * 3 + c] = v;
+      }
+    for (int a = 0; a < 3; ++a) {
+      if (parts & 1) rv[a] += sig * al[a] * f.p_D[b];
+      if (parts & 2) rv[a] -= flen * mn[a] * f.p_D[b];
+    }
+  } else if (parts & 1) {
+    for (int a = 0; a < 3; ++a) rv[a] -= flen * al[a] * f.v_N[b];
+  }
+}
+
+__device__ __forceinline__ int coarse_face_of_fine(const FineDev& f, int face) {
+  // interior fine face -> index among interior faces in "coarse-face" order of
+  // the one-cell-block system (x-interfaces J*(nx-1)+I, then y-interfaces)
+  if (face < f.nxf) {
+    const int j = face / (f.nx + 1), i = face - j * (f.nx + 1);
+    return j * (f.nx - 1) + (i - 1);
+  }
+  const int g = face - f.nxf;
+  const int j = g / f.nx, i = g - j * f.nx;
+  return f.ny * (f.nx - 1) + (j - 1) * f.nx + i;
+}
+
+__global__ void k_fine_system(const FineDev* __restrict__ fds, const SysJob* __restrict__ jobs) {
+  const SysJob J = jobs[blockIdx.y];
+  const FineDev& f = fds[J.prob];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double Mx[36], rv[3];
+  if (t < f.n_cells) {
+    const int e = t, j = e / f.nx, i = e - j * f.nx;
+    const double ke = f.perm[e], ge = job_gamma(f, J, e);
+    double D[9], r[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 9; ++k) D[k] = 0.0;
+    if (J.parts & 2) {
+      D[4] = ge * ke * f.vol * 4.0 / (f.hx * f.hx);
+      D[8] = ge * ke * f.vol * 4.0 / (f.hy * f.hy);
+    }
+    // four faces: (axis, side, neighbour or boundary index)
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const int axis = s4 >> 1, side = (s4 & 1) ? +1 : -1;
+      int nb = -1, bidx = -1;
+      if (axis == 0) {
+        if (side < 0) { if (i > 0) nb = e - 1; else bidx = j; }
+        else { if (i < f.nx - 1) nb = e + 1; else bidx = f.ny + j; }
+      } else {
+        if (side < 0) { if (j > 0) nb = e - f.nx; else bidx = 2 * f.ny + i; }
+        else { if (j < f.ny - 1) nb = e + f.nx; else bidx = 2 * f.ny + f.nx + i; }
+      }
+      if (nb >= 0) {
+        const double kn = f.perm[nb], gn = job_gamma(f, J, nb);
+        if (side > 0) {  // this cell is e1
+          interior_face_matrix(f, axis, ke, ge, kn, gn, J.parts, Mx);
+          for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) D[a * 3 + c] += Mx[a * 6 + c];
+        } else {         // this cell is e2
+          interior_face_matrix(f, axis, kn, gn, ke, ge, J.parts, Mx);
+          for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) D[a * 3 + c] += Mx[(3 + a) * 6 + 3 + c];
+        }
+      } else {
+        boundary_face(f, axis, side, bidx, ke, ge, J.parts, Mx, rv);
+        for (int k = 0; k < 9; ++k) D[k] += Mx[k];
+        for (int k = 0; k < 3; ++k) r[k] += rv[k];
+      }
+    }
+    for (int k = 0; k < 9; ++k) J.D[(size_t)e * 9 + k] = D[k];
+    for (int k = 0; k < 3; ++k) J.r[(size_t)e * 3 + k] = r[k];
+  }
+  if (t < f.n_faces) {
+    const int face = t;
+    int e1 = -1, e2 = -1, axis;
+    if (face < f.nxf) {
+      axis = 0;
+      const int j = face / (f.nx + 1), i = face - j * (f.nx + 1);
+      if (i > 0 && i < f.nx) { e1 = j * f.nx + i - 1; e2 = e1 + 1; }
+    } else {
+      axis = 1;
+      const int g = face - f.nxf;
+      const int j = g / f.nx, i = g - j * f.nx;
+      if (j > 0 && j < f.ny) { e1 = (j - 1) * f.nx + i; e2 = e1 + f.nx; }
+    }
+    if (e1 >= 0) {
+      interior_face_matrix(f, axis, f.perm[e1], job_gamma(f, J, e1), f.perm[e2],
+                           job_gamma(f, J, e2), J.parts, Mx);
+      double* O = J.O + (size_t)coarse_face_of_fine(f, face) * 9;
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) O[a * 3 + c] = Mx[a * 6 + 3 + c];
+    }
+  }
+}
+
+// Face fluxes of Definition 2 from a cell-major P1 pressure x[e*3+k], with
+// the mobility lambda(s0) (Algorithm 2, step 1(a)).
+__global__ void k_fine_flux(const FineDev* __restrict__ fds, const double* const* __restrict__ xs,
+                            double* const* __restrict__ Fs) {
+  const FineDev& f = fds[blockIdx.y];
+  const double* x = xs[blockIdx.y];
+  double* F = Fs[blockIdx.y];
+  const int face = blockIdx.x * blockDim.x + threadIdx.x;
+  if (face >= f.n_faces) return;
+  int e1 = -1, e2 = -1, bidx = -1, axis;
+  if (face < f.nxf) {
+    axis = 0;
+    const int j = face / (f.nx + 1), i = face - j * (f.nx + 1);
+    if (i > 0) e1 = j * f.nx + i - 1;
+    if (i < f.nx) e2 = j * f.nx + i;
+    if (i == 0) bidx = j;
+    if (i == f.nx) bidx = f.ny + j;
+  } else {
+    axis = 1;
+    const int g = face - f.nxf;
+    const int j = g / f.nx, i = g - j * f.nx;
+    if (j > 0) e1 = (j - 1) * f.nx + i;
+    if (j < f.ny) e2 = j * f.nx + i;
+    if (j == 0) bidx = 2 * f.ny + i;
+    if (j == f.ny) bidx = 2 * f.ny + f.nx + i;
+  }
+  const double flen = axis == 0 ? f.hy : f.hx;
+  const double dsc = axis == 0 ? 2.0 / f.hx : 2.0 / f.hy;
+  const int kt = 1 + axis;  // basis function varying along the normal
+  double val;
+  if (e1 >= 0 && e2 >= 0) {
+    const double k1 = f.perm[e1], k2 = f.perm[e2];
+    const double t1 = (f.swapped ? k2 : k1) / (k1 + k2), t2 = (f.swapped ? k1 : k2) / (k1 + k2);
+    const double g1 = mob_total(f, f.s0[e1]), g2 = mob_total(f, f.s0[e2]);
+    const double mean = t1 * g1 * k1 * dsc * x[e1 * 3 + kt] + t2 * g2 * k2 * dsc * x[e2 * 3 + kt];
+    const double jump = (x[e1 * 3] + x[e1 * 3 + kt]) - (x[e2 * 3] - x[e2 * 3 + kt]);
+    val = -flen * mean + f.c_pen * 2.0 * k1 * k2 / (k1 + k2) * jump;
+  } else {
+    const int e = e1 >= 0 ? e1 : e2;
+    const double sg = e1 >= 0 ? 1.0 : -1.0;
+    double out;
+    if (f.bc_type[bidx] == 1) {
+      const double ke = f.perm[e], ge = mob_total(f, f.s0[e]);
+      out = -flen * ge * ke * sg * dsc * x[e * 3 + kt] +
+            f.c_pen * ke * (x[e * 3] + sg * x[e * 3 + kt] - f.p_D[bidx]);
+    } else {
+      out = flen * f.v_N[bidx];
+    }
+    val = sg * out;
+  }
+  F[face] = val;
+}
+
+// CFL bound of the initial velocity: min_e phi|e| / outflow_e (as a positive
+// double, so the bit pattern orders like the value).
+__global__ void k_fine_cfl(const FineDev* __restrict__ fds, double* const* __restrict__ Fs,
+                           unsigned long long* out) {
+  const FineDev& f = fds[blockIdx.y];
+  const double* F = Fs[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= f.n_cells) return;
+  const int j = e / f.nx, i = e - j * f.nx;
+  const int fl = j * (f.nx + 1) + i, fb = f.nxf + j * f.nx + i;
+  const double o = fmax(-F[fl], 0.0) + fmax(F[fl + 1], 0.0) + fmax(-F[fb], 0.0) + fmax(F[fb + f.nx], 0.0);
+  if (o > 0.0) atomicMin(out + blockIdx.y, __double_as_longlong(f.poro[e] * f.vol / o));
+}
+
+// One Jacobi sweep of the upwind time-of-flight equations (Eq. timeOfFlight
+// with constant test functions): tau_e = (phi|e| + sum_in |F| tau_up) / sum_out F.
+__global__ void k_tof_sweep(const FineDev* __restrict__ fds, double* const* __restrict__ Fs,
+                            double* const* __restrict__ tin, double* const* __restrict__ tout,
+                            int* changed) {
+  const FineDev& f = fds[blockIdx.y];
+  const double* F = Fs[blockIdx.y];
+  const double* a = tin[blockIdx.y];
+  double* b = tout[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= f.n_cells) return;
+  const int j = e / f.nx, i = e - j * f.nx;
+  const int fl = j * (f.nx + 1) + i, fb = f.nxf + j * f.nx + i;
+  const double fo[4] = {-F[fl], F[fl + 1], -F[fb], F[fb + f.nx]};
+  const int nbr[4] = {i > 0 ? e - 1 : -1, i < f.nx - 1 ? e + 1 : -1, j > 0 ? e - f.nx : -1,
+                      j < f.ny - 1 ? e + f.nx : -1};
+  double out = 0.0, src = f.poro[e] * f.vol;
+  for (int k = 0; k < 4; ++k) {
+    if (fo[k] >= 0.0) out += fo[k];
+    else if (nbr[k] >= 0) src += -fo[k] * a[nbr[k]];
+  }
+  const double v = out > 0.0 ? src / out : DBL_MAX;
+  if (v != a[e]) *changed = 1;
+  b[e] = v;
+}
+
+// Profile index (Algorithm 2, step 1(c)): first q in 2..M-1 with
+// tau <= (q-1) T/(M-2), else M; and a histogram of the indices.
+__global__ void k_profiles(FineDev* fds, double* const* __restrict__ taus, const double* T,
+                           unsigned int* hist) {
+  FineDev& f = fds[blockIdx.y];
+  const double* tau = taus[blockIdx.y];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= f.n_cells) return;
+  int k = f.M;
+  for (int q = 2; q <= f.M - 1; ++q)
+    if (tau[e] <= (q - 1) * T[blockIdx.y] / (f.M - 2)) {
+      k = q;
+      break;
+    }
+  f.prof_idx[e] = (uint8_t)k;
+  atomicAdd(hist + blockIdx.y * (kMaxM + 1) + k, 1u);
+}
+
+__device__ double block_reduce_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+// Local bases (Algorithm 2, step 2(e)): for subdomain E, the normalised unit
+// function, then each snapshot restricted to E, orthonormalised by two passes
+// of modified Gram-Schmidt in L2(E) (weights |e| (1, 1/3, 1/3)) and rejected
+// when its remaining norm is below 1e-10 of its original norm; stops at N_E.
+// Output layout: [N_E][3 cells_E], row k*cells_E + c.
+struct GsJob {
+  int prob, E, NE, n_snap;
+  const double* const* snaps;  // cell-major fine pressures
+  double* Phi;                 // output for this subdomain
+  int* got;                    // number of functions produced
+};
+
+__global__ void k_gram_schmidt(const FineDev* __restrict__ fds, const GsJob* __restrict__ jobs) {
+  const GsJob J = jobs[blockIdx.x];
+  const FineDev& f = fds[J.prob];
+  const int cells = f.cx * f.cy, rows = 3 * cells;
+  const int I = J.E % f.Sx, Jy = J.E / f.Sx;
+  extern __shared__ double v[];  // rows
+  __shared__ double red[32];
+  const double w3[3] = {f.vol, f.vol / 3.0, f.vol / 3.0};
+  int have = 0;
+  for (int cand = -1; cand < J.n_snap && have < J.NE; ++cand) {
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      const int k = r / cells, c = r - k * cells;
+      if (cand < 0) {
+        v[r] = (k == 0) ? 1.0 : 0.0;
+      } else {
+        const int li = c % f.cx, lj = c / f.cx;
+        const int ge = (Jy * f.cy + lj) * f.nx + I * f.cx + li;
+        v[r] = J.snaps[cand][ge * 3 + k];
+      }
+    }
+    __syncthreads();
+    double n0 = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) n0 += w3[r / cells] * v[r] * v[r];
+    n0 = sqrt(block_reduce_sum(n0, red));
+    if (!(n0 > 0.0)) continue;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int b = 0; b < have; ++b) {
+        const double* ph = J.Phi + (size_t)b * rows;
+        double d = 0.0;
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) d += w3[r / cells] * ph[r] * v[r];
+        d = block_reduce_sum(d, red);
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) v[r] -= d * ph[r];
+        __syncthreads();
+      }
+    double nw = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) nw += w3[r / cells] * v[r] * v[r];
+    nw = sqrt(block_reduce_sum(nw, red));
+    if (!(nw >= 1e-10 * n0)) continue;
+    double* out = J.Phi + (size_t)have * rows;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) out[r] = v[r] / nw;
+    __syncthreads();
+    ++have;
+  }
+  if (threadIdx.x == 0) *J.got = have;
+}
+
+// Projection (Section 4.4) of the fine component q (0: penalty terms, q >= 1:
+// volume + consistency with Lambda^q) onto the local bases, for one
+// assembled block (diagonal block of E, or coarse face (E-, E+)) or one
+// subdomain right-hand side. Fine blocks: D [n_cells][9], O per interior fine
+// face [9] (row e1, col e2), r [n_cells][3].
+struct ProjJob {
+  int prob, kind, E, Ep, q;  // kind 0: diagonal block E, 1: coarse face (E, Ep), 2: rhs of E
+  int NE, NEp;
+  const double* D;
+  const double* O;
+  const double* r;
+  const double* PhiE;   // [NE][rows]
+  const double* PhiEp;  // [NEp][rows]
+  double* out;          // block [NE][NEp] or vector [NE]
+};
+
+__device__ __forceinline__ int gcell(const FineDev& f, int E, int c) {
+  const int I = E % f.Sx, J = E / f.Sx, li = c % f.cx, lj = c / f.cx;
+  return (J * f.cy + lj) * f.nx + I * f.cx + li;
+}
+
+__global__ void k_project(const FineDev* __restrict__ fds, const ProjJob* __restrict__ jobs) {
+  const ProjJob P = jobs[blockIdx.x];
+  const FineDev& f = fds[P.prob];
+  const int cells = f.cx * f.cy, rows = 3 * cells;
+  if (P.kind == 2) {
+    for (int i = threadIdx.x; i < P.NE; i += blockDim.x) {
+      double acc = 0.0;
+      const double* ph = P.PhiE + (size_t)i * rows;
+      for (int c = 0; c < cells; ++c) {
+        const double* rr = P.r + (size_t)gcell(f, P.E, c) * 3;
+        for (int k = 0; k < 3; ++k) acc += ph[k * cells + c] * rr[k];
+      }
+      P.out[i] = acc;
+    }
+    return;
+  }
+  const int NJ = P.kind == 0 ? P.NE : P.NEp;
+  for (int idx = threadIdx.x; idx < P.NE * NJ; idx += blockDim.x) {
+    const int i = idx / NJ, jj = idx - i * NJ;
+    const double* pi = P.PhiE + (size_t)i * rows;
+    double acc = 0.0;
+    if (P.kind == 0) {
+      const double* pj = P.PhiE + (size_t)jj * rows;
+      for (int c = 0; c < cells; ++c) {
+        const double* D = P.D + (size_t)gcell(f, P.E, c) * 9;
+        for (int k = 0; k < 3; ++k) {
+          const double t = D[k * 3] * pj[c] + D[k * 3 + 1] * pj[cells + c] + D[k * 3 + 2] * pj[2 * cells + c];
+          acc += pi[k * cells + c] * t;
+        }
+      }
+      // interior fine faces inside E: both orientations of the coupling block
+      for (int c = 0; c < cells; ++c) {
+        const int li = c % f.cx, lj = c / f.cx;
+        const int e = gcell(f, P.E, c);
+        for (int dir = 0; dir < 2; ++dir) {
+          if (dir == 0 && li + 1 >= f.cx) continue;
+          if (dir == 1 && lj + 1 >= f.cy) continue;
+          const int c2 = dir == 0 ? c + 1 : c + f.cx;
+          const int ei = e % f.nx, ej = e / f.nx;
+          const int cf = dir == 0 ? ej * (f.nx - 1) + ei : f.ny * (f.nx - 1) + ej * f.nx + ei;
+          const double* O = P.O + (size_t)cf * 9;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+              const double o = O[k * 3 + l];
+              acc += o * (pi[k * cells + c] * pj[l * cells + c2] + pi[l * cells + c2] * pj[k * cells + c]);
+            }
+        }
+      }
+    } else {
+      const double* pj = P.PhiEp + (size_t)jj * rows;
+      const bool xdir = (P.Ep == P.E + 1);
+      const int n = xdir ? f.cy : f.cx;
+      for (int t = 0; t < n; ++t) {
+        // cell c1 in E on the interface, c2 its neighbour in Ep
+        const int c1 = xdir ? t * f.cx + (f.cx - 1) : (f.cy - 1) * f.cx + t;
+        const int c2 = xdir ? t * f.cx : t;
+        const int e = gcell(f, P.E, c1);
+        const int ei = e % f.nx, ej = e / f.nx;
+        const int cf = xdir ? ej * (f.nx - 1) + ei : f.ny * (f.nx - 1) + ej * f.nx + ei;
+        const double* O = P.O + (size_t)cf * 9;
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) acc += pi[k * cells + c1] * O[k * 3 + l] * pj[l * cells + c2];
+      }
+    }
+    P.out[(size_t)i * NJ + jj] = acc;
+  }
+}
+
+// Rotated copy: Phi_E Q_E, Q_E^T B Q_E' per component, Q_E^T r_E.
+struct RotJob {
+  int kind, NE, NEp, rows, Q1;  // kind 0: basis of E, 1: block (E, E'), 2: rhs of E
+  const double* QE;
+  const double* QEp;
+  const double* src;
+  double* dst;
+};
+
+__global__ void k_rotate(const RotJob* __restrict__ jobs) {
+  const RotJob R = jobs[blockIdx.x];
+  if (R.kind == 0) {
+    for (int idx = threadIdx.x; idx < R.NE * R.rows; idx += blockDim.x) {
+      const int j = idx / R.rows, r = idx - j * R.rows;
+      double acc = 0.0;
+      for (int i = 0; i < R.NE; ++i) acc += R.src[(size_t)i * R.rows + r] * R.QE[i * R.NE + j];
+      R.dst[idx] = acc;
+    }
+  } else if (R.kind == 1) {
+    const int sz = R.NE * R.NEp;
+    for (int q = 0; q < R.Q1; ++q) {
+      const double* B = R.src + (size_t)q * sz;
+      double* out = R.dst + (size_t)q * sz;
+      for (int idx = threadIdx.x; idx < sz; idx += blockDim.x) {
+        const int a = idx / R.NEp, b = idx - a * R.NEp;
+        double acc = 0.0;
+        for (int i = 0; i < R.NE; ++i) {
+          double t = 0.0;
+          for (int j = 0; j < R.NEp; ++j) t += B[i * R.NEp + j] * R.QEp[j * R.NEp + b];
+          acc += R.QE[i * R.NE + a] * t;
+        }
+        out[idx] = acc;
+      }
+    }
+  } else {
+    for (int q = 0; q < R.Q1; ++q)
+      for (int a = threadIdx.x; a < R.NE; a += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < R.NE; ++i) acc += R.QE[i * R.NE + a] * R.src[(size_t)q * R.NE + i];
+        R.dst[(size_t)q * R.NE + a] = acc;
+      }
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- host side
+namespace {
+
+struct DevBuf {
+  std::vector<void*> ptrs;
+  ~DevBuf() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+};
+
+// Max over [0,1] of f_w'(s) by dense sampling of a central difference and a
+// local golden-section refinement.
+double max_fw_slope(double ew, double eo, int law) {
+  auto fw = [&](double s) {
+    const double lw = (law == 0 ? s * s : s) / ew;
+    const double lo = (law == 0 ? (1 - s) * (1 - s) : (1 - s)) / eo;
+    return lw / (lw + lo);
+  };
+  auto d = [&](double s) {
+    const double h = 1e-7, a = std::max(0.0, s - h), b = std::min(1.0, s + h);
+    return (fw(b) - fw(a)) / (b - a);
+  };
+  const int n = 200000;
+  int best = 0;
+  double bv = -1;
+  for (int i = 0; i <= n; ++i) {
+    const double v = d((double)i / n);
+    if (v > bv) bv = v, best = i;
+  }
+  double lo = std::max(0, best - 1) / (double)n, hi = std::min(n, best + 1) / (double)n;
+  const double gr = (std::sqrt(5.0) - 1) / 2;
+  for (int it = 0; it < 80; ++it) {
+    const double c = hi - gr * (hi - lo), e = lo + gr * (hi - lo);
+    if (d(c) > d(e)) hi = e; else lo = c;
+  }
+  return std::max(bv, d(0.5 * (lo + hi)));
+}
+
+// Minimum-norm pseudo-inverse of a symmetric M x M matrix (cyclic Jacobi
+// eigen-decomposition; eigenvalues below 1e-12 of the largest dropped).
+void sym_pinv(int M, const std::vector<double>& G, std::vector<double>& out) {
+  std::vector<double> A = G, V(M * M, 0.0);
+  for (int i = 0; i < M; ++i) V[i * M + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < M; ++p)
+      for (int q = p + 1; q < M; ++q) off += A[p * M + q] * A[p * M + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < M; ++p)
+      for (int q = p + 1; q < M; ++q) {
+        const double apq = A[p * M + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double th = (A[q * M + q] - A[p * M + p]) / (2 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1));
+        const double c = 1 / std::sqrt(t * t + 1), s = t * c;
+        for (int k = 0; k < M; ++k) {
+          const double akp = A[k * M + p], akq = A[k * M + q];
+          A[k * M + p] = c * akp - s * akq;
+          A[k * M + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < M; ++k) {
+          const double apk = A[p * M + k], aqk = A[q * M + k];
+          A[p * M + k] = c * apk - s * aqk;
+          A[q * M + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < M; ++k) {
+          const double vkp = V[k * M + p], vkq = V[k * M + q];
+          V[k * M + p] = c * vkp - s * vkq;
+          V[k * M + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  double wmax = 0;
+  for (int i = 0; i < M; ++i) wmax = std::max(wmax, A[i * M + i]);
+  out.assign(M * M, 0.0);
+  for (int k = 0; k < M; ++k) {
+    const double w = A[k * M + k];
+    if (!(w > 1e-12 * wmax)) continue;
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) out[i * M + j] += V[i * M + k] * V[j * M + k] / w;
+  }
+}
+
+}  // namespace
+
+// Fine-system solves through the online solver: one "simulation" per system
+// with one-cell blocks.
+struct FineSolver {
+  int nx, ny;
+  int n_cells, n_int;
+  std::vector<SimDev> sims;
+  SimDev* d_sims = nullptr;
+  int* d_active = nullptr;
+  DevBuf* buf;
+  // shared metadata
+  int *NE = nullptr, *xoff = nullptr;
+  long long *aoff = nullptr, *loff = nullptr, *ioff = nullptr;
+
+  bool init(DevBuf& b, int nx_, int ny_, int count, cudaStream_t st) {
+    buf = &b;
+    nx = nx_; ny = ny_;
+    n_cells = nx * ny;
+    n_int = ny * (nx - 1) + (ny - 1) * nx;
+    const int n_blocks = n_cells + n_int;
+    std::vector<int> ne(n_cells, 3), xo(n_cells + 1);
+    for (int e = 0; e <= n_cells; ++e) xo[e] = 3 * e;
+    std::vector<long long> ao(n_blocks + 1), lo(n_cells + 1), io(n_cells + 1);
+    for (int k = 0; k <= n_blocks; ++k) ao[k] = 9LL * k;
+    lo[0] = 0; io[0] = 0;
+    for (int k = 0; k < n_cells; ++k) {
+      const int jl = jlo_of(k, nx);
+      lo[k + 1] = lo[k] + 3LL * (xo[k + 1] - xo[jl]);
+      io[k + 1] = io[k] + 9;
+    }
+    NE = b.get<int>(n_cells); xoff = b.get<int>(n_cells + 1);
+    aoff = b.get<long long>(n_blocks + 1); loff = b.get<long long>(n_cells + 1);
+    ioff = b.get<long long>(n_cells + 1);
+    if (!NE || !xoff || !aoff || !loff || !ioff) return false;
+    cudaMemcpyAsync(NE, ne.data(), 4 * ne.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(xoff, xo.data(), 4 * xo.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(aoff, ao.data(), 8 * ao.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(loff, lo.data(), 8 * lo.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ioff, io.data(), 8 * io.size(), cudaMemcpyHostToDevice, st);
+    sims.resize(count);
+    for (int s = 0; s < count; ++s) {
+      SimDev d{};
+      d.nx = nx; d.ny = ny; d.Sx = nx; d.Sy = ny; d.n_sub = n_cells; d.n_cf = n_int;
+      d.n_blocks = n_blocks; d.N = 3 * n_cells; d.max_NE = 3;
+      d.NE = NE; d.xoff = xoff; d.aoff = aoff; d.loff = loff; d.ioff = ioff;
+      d.A = b.get<double>(9 * (size_t)n_blocks);
+      d.b = b.get<double>(3 * (size_t)n_cells);
+      d.x = b.get<double>(3 * (size_t)n_cells);
+      d.y = b.get<double>(3 * (size_t)n_cells);
+      d.rv = b.get<double>(3 * (size_t)n_cells);
+      d.dv = b.get<double>(3 * (size_t)n_cells);
+      d.L = b.get<double>((size_t)lo[n_cells]);
+      d.Linv = b.get<double>(9 * (size_t)n_cells);
+      d.status = b.get<int>(1);
+      if (!d.A || !d.b || !d.x || !d.y || !d.rv || !d.dv || !d.L || !d.Linv || !d.status) return false;
+      cudaMemsetAsync(d.status, 0, 4, st);
+      sims[s] = d;
+    }
+    d_sims = b.get<SimDev>(count);
+    d_active = b.get<int>(count);
+    if (!d_sims || !d_active) return false;
+    std::vector<int> act(count);
+    for (int s = 0; s < count; ++s) act[s] = s;
+    cudaMemcpyAsync(d_sims, sims.data(), sizeof(SimDev) * count, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_active, act.data(), 4 * count, cudaMemcpyHostToDevice, st);
+    return cudaStreamSynchronize(st) == cudaSuccess;
+  }
+};
+
+}  // namespace lrbms
+
+using namespace lrbms;
+
+extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
+                                   const lrbms_build_opts* opts, int n_copies,
+                                   const double* const* rot, int* sim_ids);
+
+// Defined in lrbms_api.cu.
+extern "C" cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx);
+extern "C" int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg);
+
+#define BCK(call)                                                              \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return lrbms_internal_fail(ctx, LRBMS_E_CUDA, (std::string(#call) + ": " + \
+                                                     cudaGetErrorString(e_)).c_str()); \
+  } while (0)
+
+extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
+                                   const lrbms_build_opts* opts, int n_copies,
+                                   const double* const* rot, int* sim_ids) {
+  if (!ctx || n_prob < 1 || !probs || !opts || n_copies < 1 || !sim_ids)
+    return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad arguments");
+  cudaStream_t st = lrbms_internal_stream(ctx);
+  const lrbms_problem& p0 = probs[0];
+  const int nx = p0.nx, ny = p0.ny, Sx = p0.Sx, Sy = p0.Sy;
+  for (int p = 0; p < n_prob; ++p) {
+    const lrbms_problem& P = probs[p];
+    const lrbms_build_opts& O = opts[p];
+    if (P.nx != nx || P.ny != ny || P.Sx != Sx || P.Sy != Sy)
+      return lrbms_internal_fail(ctx, LRBMS_E_ARG, "all problems of one build must share the grids");
+    if (nx < 2 || ny < 2 || nx % Sx || ny % Sy)
+      return lrbms_internal_fail(ctx, LRBMS_E_ARG, "grid must be at least 2x2 and match the subdomains");
+    if (O.M < 3 || O.M > kMaxM || O.n_snap < 0 || (O.n_snap && !O.mu) || !O.N_E || O.n_steps_T < 1 ||
+        !(O.c_pen > 0))
+      return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad build options");
+  }
+  const int n_cells = nx * ny, cx = nx / Sx, cy = ny / Sy, cells = cx * cy, n_sub = Sx * Sy;
+  const int nxf = (nx + 1) * ny, n_faces = nxf + nx * (ny + 1), nb = 2 * nx + 2 * ny;
+  const int n_int = ny * (nx - 1) + (ny - 1) * nx;
+  const int n_cf = Sy * (Sx - 1) + (Sy - 1) * Sx;
+  DevBuf B;
+
+  // ---- problem data on the device
+  std::vector<FineDev> fd(n_prob);
+  for (int p = 0; p < n_prob; ++p) {
+    const lrbms_problem& P = probs[p];
+    FineDev& f = fd[p];
+    f.nx = nx; f.ny = ny; f.Sx = Sx; f.Sy = Sy; f.cx = cx; f.cy = cy; f.n_cells = n_cells;
+    f.nxf = nxf; f.n_faces = n_faces; f.nb = nb; f.M = opts[p].M; f.relperm = P.relperm;
+    f.swapped = P.mean_weights; f.hx = P.Lx / nx; f.hy = P.Ly / ny; f.vol = f.hx * f.hy;
+    f.c_pen = opts[p].c_pen; f.inv_eta_w = 1.0 / P.eta_w; f.inv_eta_o = 1.0 / P.eta_o;
+    f.lam0 = f.inv_eta_o; f.lam1 = f.inv_eta_w;
+    double* perm = B.get<double>(n_cells); double* poro = B.get<double>(n_cells);
+    double* s0 = B.get<double>(n_cells);
+    int8_t* bct = B.get<int8_t>(nb);
+    double* pD = B.get<double>(nb); double* vN = B.get<double>(nb); double* sD = B.get<double>(nb);
+    uint8_t* pidx = B.get<uint8_t>(n_cells);
+    if (!perm || !poro || !s0 || !bct || !pD || !vN || !sD || !pidx)
+      return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the offline build");
+    BCK(cudaMemcpyAsync(perm, P.perm, 8 * (size_t)n_cells, cudaMemcpyDefault, st));
+    BCK(cudaMemcpyAsync(poro, P.poro, 8 * (size_t)n_cells, cudaMemcpyDefault, st));
+    BCK(cudaMemcpyAsync(s0, P.s0, 8 * (size_t)n_cells, cudaMemcpyDefault, st));
+    BCK(cudaMemcpyAsync(bct, P.bc_type, nb, cudaMemcpyDefault, st));
+    BCK(cudaMemcpyAsync(pD, P.p_D, 8 * (size_t)nb, cudaMemcpyDefault, st));
+    BCK(cudaMemcpyAsync(vN, P.v_N, 8 * (size_t)nb, cudaMemcpyDefault, st));
+    BCK(cudaMemcpyAsync(sD, P.s_D, 8 * (size_t)nb, cudaMemcpyDefault, st));
+    f.perm = perm; f.poro = poro; f.s0 = s0; f.bc_type = bct; f.p_D = pD; f.v_N = vN; f.s_D = sD;
+    f.prof_idx = pidx;
+  }
+  FineDev* d_fd = B.get<FineDev>(n_prob);
+  if (!d_fd) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the offline build");
+  BCK(cudaMemcpyAsync(d_fd, fd.data(), sizeof(FineDev) * n_prob, cudaMemcpyHostToDevice, st));
+
+  auto run_systems = [&](std::vector<SysJob>& jobs) -> int {
+    SysJob* dj = B.get<SysJob>(jobs.size());
+    if (!dj) return LRBMS_E_BUDGET;
+    if (cudaMemcpyAsync(dj, jobs.data(), sizeof(SysJob) * jobs.size(), cudaMemcpyHostToDevice, st)) return LRBMS_E_CUDA;
+    const int n = std::max(n_cells, n_faces);
+    k_fine_system<<<dim3((n + 127) / 128, (unsigned)jobs.size()), 128, 0, st>>>(d_fd, dj);
+    return cudaGetLastError() == cudaSuccess ? 0 : LRBMS_E_CUDA;
+  };
+
+  // ---- step 1(a): initial pressure with lambda(s0)
+  FineSolver init;
+  if (!init.init(B, nx, ny, n_prob, st))
+    return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the initial fine solves");
+  {
+    std::vector<SysJob> jobs(n_prob);
+    for (int p = 0; p < n_prob; ++p)
+      jobs[p] = SysJob{p, 0, 3, 0, nullptr, init.sims[p].A, init.sims[p].A + 9 * (size_t)n_cells,
+                       init.sims[p].b};
+    if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "fine assembly");
+    launch_chol_solve(init.d_sims, init.d_active, n_prob, 1, st);
+  }
+  // ---- velocity, time-of-flight and profiles (steps 1(b), 1(c))
+  std::vector<double*> hF(n_prob), hta(n_prob), htb(n_prob);
+  std::vector<const double*> hx(n_prob);
+  for (int p = 0; p < n_prob; ++p) {
+    hF[p] = B.get<double>(n_faces); hta[p] = B.get<double>(n_cells); htb[p] = B.get<double>(n_cells);
+    if (!hF[p] || !hta[p] || !htb[p]) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "tof buffers");
+    hx[p] = init.sims[p].x;
+    BCK(cudaMemsetAsync(hta[p], 0, 8 * (size_t)n_cells, st));
+  }
+  double** dF = B.get<double*>(n_prob); double** dta = B.get<double*>(n_prob);
+  double** dtb = B.get<double*>(n_prob); const double** dx = (const double**)B.get<double*>(n_prob);
+  unsigned long long* dcfl = B.get<unsigned long long>(n_prob);
+  int* dchg = B.get<int>(1);
+  unsigned int* dhist = B.get<unsigned int>(n_prob * (kMaxM + 1));
+  double* dT = B.get<double>(n_prob);
+  if (!dF || !dta || !dtb || !dx || !dcfl || !dchg || !dhist || !dT)
+    return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "tof buffers");
+  BCK(cudaMemcpyAsync(dF, hF.data(), sizeof(double*) * n_prob, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(dta, hta.data(), sizeof(double*) * n_prob, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(dtb, htb.data(), sizeof(double*) * n_prob, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(dx, hx.data(), sizeof(double*) * n_prob, cudaMemcpyHostToDevice, st));
+  {
+    std::vector<unsigned long long> inf(n_prob);
+    const double big = DBL_MAX;
+    for (auto& v : inf) std::memcpy(&v, &big, 8);
+    BCK(cudaMemcpyAsync(dcfl, inf.data(), 8 * (size_t)n_prob, cudaMemcpyHostToDevice, st));
+  }
+  BCK(cudaMemsetAsync(dhist, 0, 4 * (size_t)n_prob * (kMaxM + 1), st));
+  k_fine_flux<<<dim3((n_faces + 255) / 256, n_prob), 256, 0, st>>>(d_fd, dx, dF);
+  k_fine_cfl<<<dim3((n_cells + 255) / 256, n_prob), 256, 0, st>>>(d_fd, dF, dcfl);
+  {
+    const int max_sweeps = 16 * (nx + ny) + 64;
+    int sweep = 0;
+    for (; sweep < max_sweeps; sweep += 2) {
+      BCK(cudaMemsetAsync(dchg, 0, 4, st));
+      k_tof_sweep<<<dim3((n_cells + 255) / 256, n_prob), 256, 0, st>>>(d_fd, dF, dta, dtb, dchg);
+      k_tof_sweep<<<dim3((n_cells + 255) / 256, n_prob), 256, 0, st>>>(d_fd, dF, dtb, dta, dchg);
+      if (sweep % 32 == 30 || sweep + 2 >= max_sweeps) {
+        int chg = 1;
+        BCK(cudaMemcpyAsync(&chg, dchg, 4, cudaMemcpyDeviceToHost, st));
+        BCK(cudaStreamSynchronize(st));
+        if (!chg) break;
+      }
+    }
+  }
+  std::vector<unsigned long long> cflbits(n_prob);
+  BCK(cudaMemcpyAsync(cflbits.data(), dcfl, 8 * (size_t)n_prob, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  std::vector<double> T(n_prob), Lf(n_prob);
+  for (int p = 0; p < n_prob; ++p) {
+    double m;
+    std::memcpy(&m, &cflbits[p], 8);
+    Lf[p] = max_fw_slope(probs[p].eta_w, probs[p].eta_o, probs[p].relperm);
+    const double dt0 = probs[p].cfl * m / Lf[p];
+    T[p] = opts[p].n_steps_T * dt0;
+  }
+  BCK(cudaMemcpyAsync(dT, T.data(), 8 * (size_t)n_prob, cudaMemcpyHostToDevice, st));
+  k_profiles<<<dim3((n_cells + 255) / 256, n_prob), 256, 0, st>>>(d_fd, dta, dT, dhist);
+  std::vector<unsigned int> hist(n_prob * (kMaxM + 1));
+  BCK(cudaMemcpyAsync(hist.data(), dhist, 4 * hist.size(), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  // G = P P^T from the histogram of profile indices, then its pseudo-inverse
+  std::vector<std::vector<double>> Gp(n_prob);
+  for (int p = 0; p < n_prob; ++p) {
+    const int M = opts[p].M;
+    std::vector<double> G(M * M, 0.0);
+    for (int k = 1; k <= M; ++k) {
+      const double n = hist[p * (kMaxM + 1) + k];
+      if (n == 0) continue;
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b)
+          G[a * M + b] += n * ((a + 1 >= k) ? fd[p].lam1 : fd[p].lam0) * ((b + 1 >= k) ? fd[p].lam1 : fd[p].lam0);
+    }
+    sym_pinv(M, G, Gp[p]);
+  }
+
+  // ---- snapshots (step 2(c)) for all problems at once
+  std::vector<int> snap_off(n_prob + 1, 0);
+  for (int p = 0; p < n_prob; ++p) snap_off[p + 1] = snap_off[p] + opts[p].n_snap;
+  const int n_snap_tot = snap_off[n_prob];
+  FineSolver snaps;
+  std::vector<double*> dmu(n_prob);
+  if (n_snap_tot) {
+    if (!snaps.init(B, nx, ny, n_snap_tot, st))
+      return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the snapshot solves");
+    std::vector<SysJob> jobs;
+    for (int p = 0; p < n_prob; ++p) {
+      dmu[p] = B.get<double>((size_t)opts[p].n_snap * opts[p].M);
+      BCK(cudaMemcpyAsync(dmu[p], opts[p].mu, 8 * (size_t)opts[p].n_snap * opts[p].M, cudaMemcpyDefault, st));
+      for (int k = 0; k < opts[p].n_snap; ++k) {
+        const SimDev& d = snaps.sims[snap_off[p] + k];
+        jobs.push_back(SysJob{p, 1, 3, 0, dmu[p] + (size_t)k * opts[p].M, d.A, d.A + 9 * (size_t)n_cells, d.b});
+      }
+    }
+    if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "snapshot assembly");
+    launch_chol_solve(snaps.d_sims, snaps.d_active, n_snap_tot, 1, st);
+  }
+
+  // ---- local bases (step 2(e))
+  std::vector<std::vector<int>> NE(n_prob, std::vector<int>(n_sub));
+  std::vector<std::vector<long long>> phioff(n_prob, std::vector<long long>(n_sub + 1, 0));
+  std::vector<double*> Phi(n_prob);
+  int* dgot = B.get<int>((size_t)n_prob * n_sub);
+  std::vector<GsJob> gjobs;
+  std::vector<const double*> snap_ptrs(std::max(n_snap_tot, 1));
+  for (int s = 0; s < n_snap_tot; ++s) snap_ptrs[s] = snaps.sims[s].x;
+  const double** dsnap = (const double**)B.get<double*>(std::max(n_snap_tot, 1));
+  BCK(cudaMemcpyAsync(dsnap, snap_ptrs.data(), sizeof(double*) * snap_ptrs.size(), cudaMemcpyHostToDevice, st));
+  for (int p = 0; p < n_prob; ++p) {
+    BCK(cudaMemcpy(NE[p].data(), opts[p].N_E, 4 * (size_t)n_sub, cudaMemcpyDefault));
+    for (int E = 0; E < n_sub; ++E) {
+      if (NE[p][E] < 1 || NE[p][E] > 64 || NE[p][E] > 3 * cells)
+        return lrbms_internal_fail(ctx, LRBMS_E_ARG, "local basis sizes must be in 1..min(64, 3 cells_E)");
+      phioff[p][E + 1] = phioff[p][E] + (long long)NE[p][E] * 3 * cells;
+    }
+    Phi[p] = B.get<double>((size_t)phioff[p][n_sub]);
+    if (!Phi[p]) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "basis buffers");
+    for (int E = 0; E < n_sub; ++E)
+      gjobs.push_back(GsJob{p, E, NE[p][E], opts[p].n_snap, dsnap + snap_off[p], Phi[p] + phioff[p][E],
+                            dgot + p * n_sub + E});
+  }
+  {
+    GsJob* dj = B.get<GsJob>(gjobs.size());
+    BCK(cudaMemcpyAsync(dj, gjobs.data(), sizeof(GsJob) * gjobs.size(), cudaMemcpyHostToDevice, st));
+    k_gram_schmidt<<<(unsigned)gjobs.size(), 256, 8 * (size_t)3 * cells, st>>>(d_fd, dj);
+    BCK(cudaGetLastError());
+    std::vector<int> got((size_t)n_prob * n_sub);
+    BCK(cudaMemcpyAsync(got.data(), dgot, 4 * got.size(), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    for (int p = 0; p < n_prob; ++p)
+      for (int E = 0; E < n_sub; ++E)
+        if (got[p * n_sub + E] != NE[p][E])
+          return lrbms_internal_fail(ctx, LRBMS_E_FORMAT,
+                                     "too few independent snapshots for the requested local basis size");
+  }
+
+  // ---- components (Section 4.4): fine blocks per component, then projection
+  std::vector<std::vector<int>> xoff(n_prob, std::vector<int>(n_sub + 1, 0));
+  std::vector<std::vector<long long>> aoff(n_prob, std::vector<long long>(n_sub + n_cf + 1, 0));
+  std::vector<int> cfm(n_cf), cfp(n_cf);
+  {
+    int fidx = 0;
+    for (int J = 0; J < Sy; ++J)
+      for (int I = 0; I + 1 < Sx; ++I, ++fidx) cfm[fidx] = J * Sx + I, cfp[fidx] = J * Sx + I + 1;
+    for (int J = 0; J + 1 < Sy; ++J)
+      for (int I = 0; I < Sx; ++I, ++fidx) cfm[fidx] = J * Sx + I, cfp[fidx] = (J + 1) * Sx + I;
+  }
+  std::vector<double*> comp(n_prob), rhs(n_prob);
+  for (int p = 0; p < n_prob; ++p) {
+    const int Q = opts[p].M + 1;
+    for (int E = 0; E < n_sub; ++E) xoff[p][E + 1] = xoff[p][E] + NE[p][E];
+    for (int E = 0; E < n_sub; ++E) aoff[p][E + 1] = aoff[p][E] + (long long)NE[p][E] * NE[p][E];
+    for (int c = 0; c < n_cf; ++c)
+      aoff[p][n_sub + c + 1] = aoff[p][n_sub + c] + (long long)NE[p][cfm[c]] * NE[p][cfp[c]];
+    comp[p] = B.get<double>((size_t)Q * aoff[p][n_sub + n_cf]);
+    rhs[p] = B.get<double>((size_t)Q * xoff[p][n_sub]);
+    if (!comp[p] || !rhs[p]) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "component buffers");
+  }
+  {
+    // fine blocks of every component of every problem (reused buffers per problem)
+    for (int p = 0; p < n_prob; ++p) {
+      const int Q = opts[p].M + 1;
+      std::vector<SysJob> jobs(Q);
+      std::vector<double*> D(Q), O(Q), R(Q);
+      for (int q = 0; q < Q; ++q) {
+        D[q] = B.get<double>(9 * (size_t)n_cells);
+        O[q] = B.get<double>(9 * (size_t)std::max(n_int, 1));
+        R[q] = B.get<double>(3 * (size_t)n_cells);
+        if (!D[q] || !O[q] || !R[q]) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "fine component blocks");
+        jobs[q] = q == 0 ? SysJob{p, 2, 1, 0, nullptr, D[q], O[q], R[q]}
+                         : SysJob{p, 2, 2, q - 1, nullptr, D[q], O[q], R[q]};
+      }
+      if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "component assembly");
+      std::vector<ProjJob> pj;
+      for (int q = 0; q < Q; ++q) {
+        for (int E = 0; E < n_sub; ++E) {
+          const double* PE = Phi[p] + phioff[p][E];
+          const size_t sz = (size_t)NE[p][E] * NE[p][E];
+          pj.push_back(ProjJob{p, 0, E, E, q, NE[p][E], NE[p][E], D[q], O[q], R[q], PE, PE,
+                               comp[p] + (size_t)Q * aoff[p][E] + q * sz});
+          pj.push_back(ProjJob{p, 2, E, E, q, NE[p][E], 0, D[q], O[q], R[q], PE, PE,
+                               rhs[p] + (size_t)Q * xoff[p][E] + (size_t)q * NE[p][E]});
+        }
+        for (int c = 0; c < n_cf; ++c) {
+          const int Em = cfm[c], Ep = cfp[c];
+          const size_t sz = (size_t)NE[p][Em] * NE[p][Ep];
+          pj.push_back(ProjJob{p, 1, Em, Ep, q, NE[p][Em], NE[p][Ep], D[q], O[q], R[q],
+                               Phi[p] + phioff[p][Em], Phi[p] + phioff[p][Ep],
+                               comp[p] + (size_t)Q * aoff[p][n_sub + c] + q * sz});
+        }
+      }
+      ProjJob* dj = B.get<ProjJob>(pj.size());
+      if (!dj) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "projection jobs");
+      BCK(cudaMemcpyAsync(dj, pj.data(), sizeof(ProjJob) * pj.size(), cudaMemcpyHostToDevice, st));
+      k_project<<<(unsigned)pj.size(), 256, 0, st>>>(d_fd, dj);
+      BCK(cudaGetLastError());
+      BCK(cudaStreamSynchronize(st));
+    }
+  }
+  for (int s = 0; s < n_snap_tot; ++s) {
+    int stv = 0;
+    BCK(cudaMemcpy(&stv, snaps.sims[s].status, 4, cudaMemcpyDeviceToHost));
+    if (stv) return lrbms_internal_fail(ctx, LRBMS_E_NOT_SPD, "a fine snapshot system was not positive definite");
+  }
+  for (int p = 0; p < n_prob; ++p) {
+    int stv = 0;
+    BCK(cudaMemcpy(&stv, init.sims[p].status, 4, cudaMemcpyDeviceToHost));
+    if (stv) return lrbms_internal_fail(ctx, LRBMS_E_NOT_SPD, "the initial fine system was not positive definite");
+  }
+
+  // ---- admit n_copies simulations per problem (optionally with rotated bases)
+  for (int p = 0; p < n_prob; ++p) {
+    const int Q = opts[p].M + 1;
+    std::vector<long long> qoff(n_sub + 1, 0);
+    for (int E = 0; E < n_sub; ++E) qoff[E + 1] = qoff[E] + (long long)NE[p][E] * NE[p][E];
+    double* rPhi = B.get<double>((size_t)phioff[p][n_sub]);
+    double* rcomp = B.get<double>((size_t)Q * aoff[p][n_sub + n_cf]);
+    double* rrhs = B.get<double>((size_t)Q * xoff[p][n_sub]);
+    double* dQ = B.get<double>((size_t)qoff[n_sub]);
+    int* dne = B.get<int>(n_sub);
+    if (!rPhi || !rcomp || !rrhs || !dQ || !dne) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "copy buffers");
+    BCK(cudaMemcpyAsync(dne, NE[p].data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, st));
+    double* dGp = B.get<double>(opts[p].M * opts[p].M);
+    BCK(cudaMemcpyAsync(dGp, Gp[p].data(), 8 * Gp[p].size(), cudaMemcpyHostToDevice, st));
+    for (int r = 0; r < n_copies; ++r) {
+      const double* Qh = rot ? rot[p * n_copies + r] : nullptr;
+      const double *uPhi = Phi[p], *ucomp = comp[p], *urhs = rhs[p];
+      if (Qh) {
+        BCK(cudaMemcpyAsync(dQ, Qh, 8 * (size_t)qoff[n_sub], cudaMemcpyDefault, st));
+        std::vector<RotJob> rj;
+        for (int E = 0; E < n_sub; ++E) {
+          rj.push_back(RotJob{0, NE[p][E], NE[p][E], 3 * cells, Q, dQ + qoff[E], dQ + qoff[E],
+                              Phi[p] + phioff[p][E], rPhi + phioff[p][E]});
+          rj.push_back(RotJob{1, NE[p][E], NE[p][E], 0, Q, dQ + qoff[E], dQ + qoff[E],
+                              comp[p] + (size_t)Q * aoff[p][E], rcomp + (size_t)Q * aoff[p][E]});
+          rj.push_back(RotJob{2, NE[p][E], NE[p][E], 0, Q, dQ + qoff[E], dQ + qoff[E],
+                              rhs[p] + (size_t)Q * xoff[p][E], rrhs + (size_t)Q * xoff[p][E]});
+        }
+        for (int c = 0; c < n_cf; ++c)
+          rj.push_back(RotJob{1, NE[p][cfm[c]], NE[p][cfp[c]], 0, Q, dQ + qoff[cfm[c]], dQ + qoff[cfp[c]],
+                              comp[p] + (size_t)Q * aoff[p][n_sub + c], rcomp + (size_t)Q * aoff[p][n_sub + c]});
+        RotJob* dj = B.get<RotJob>(rj.size());
+        if (!dj) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "rotation jobs");
+        BCK(cudaMemcpyAsync(dj, rj.data(), sizeof(RotJob) * rj.size(), cudaMemcpyHostToDevice, st));
+        k_rotate<<<(unsigned)rj.size(), 256, 0, st>>>(dj);
+        BCK(cudaGetLastError());
+        uPhi = rPhi; ucomp = rcomp; urhs = rrhs;
+      }
+      lrbms_offline off{};
+      off.M = opts[p].M;
+      off.N_E = dne;
+      off.prof_idx = fd[p].prof_idx;
+      off.prof = nullptr;
+      off.Gpinv = dGp;
+      off.Phi = uPhi;
+      off.Dblk = ucomp;
+      off.Fblk = n_cf ? ucomp + (size_t)Q * aoff[p][n_sub] : nullptr;
+      off.rhs = urhs;
+      off.c_pen = opts[p].c_pen;
+      off.Lf = Lf[p];
+      BCK(cudaStreamSynchronize(st));
+      const int rc = lrbms_offline_load(ctx, &probs[p], &off, &sim_ids[p * n_copies + r]);
+      if (rc) return rc;
+    }
+  }
+  BCK(cudaStreamSynchronize(st));
+  return LRBMS_OK;
+}

@@ -33,7 +33,8 @@ LRBMS_DT_CFL = 0
 LRBMS_DT_FIXED = 1
 FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS = range(9)
 
-EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_release", "lrbms_step",
+EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offline_build",
+            "lrbms_release", "lrbms_step",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
             "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count",
             "lrbms_last_error"]
@@ -67,6 +68,11 @@ class Offline(C.Structure):
                 ("Fblk", C.c_void_p), ("rhs", C.c_void_p), ("c_pen", C.c_double), ("Lf", C.c_double)]
 
 
+class BuildOpts(C.Structure):
+    _fields_ = [("M", C.c_int), ("n_steps_T", C.c_int), ("N_E", C.c_void_p), ("n_snap", C.c_int),
+                ("mu", C.c_void_p), ("c_pen", C.c_double)]
+
+
 _lib = None
 
 
@@ -81,6 +87,8 @@ def library() -> C.CDLL:
         lib.lrbms_create.argtypes = [C.POINTER(vp), C.POINTER(Config)]
         lib.lrbms_destroy.argtypes = [vp]
         lib.lrbms_offline_load.argtypes = [vp, C.POINTER(Problem), C.POINTER(Offline), C.POINTER(i)]
+        lib.lrbms_offline_build.argtypes = [vp, i, C.POINTER(Problem), C.POINTER(BuildOpts), i,
+                                            C.POINTER(vp), C.POINTER(i)]
         lib.lrbms_release.argtypes = [vp, i]
         lib.lrbms_step.argtypes = [vp, i, vp, i, vp]
         lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
@@ -131,6 +139,48 @@ def lrbms_create(precision=LRBMS_FP64, max_slots=64, hbm_budget=8 << 30, stream=
 
 def lrbms_destroy(ctx):
     _check(ctx, library().lrbms_destroy(ctx))
+
+
+def _problem_struct(problem: dict, keep: dict) -> Problem:
+    pa = {k: _as(problem[k], dt) for k, dt in (("perm", np.float64), ("poro", np.float64),
+                                             ("bc_type", np.int8), ("p_D", np.float64),
+                                             ("v_N", np.float64), ("s_D", np.float64),
+                                             ("s0", np.float64))}
+    keep[id(pa)] = pa
+    return Problem(problem["nx"], problem["ny"], problem["Sx"], problem["Sy"], problem["Lx"], problem["Ly"],
+                   _ptr(pa["perm"]), _ptr(pa["poro"]), problem["eta_w"], problem["eta_o"],
+                   problem.get("relperm", LRBMS_COREY), _ptr(pa["bc_type"]), _ptr(pa["p_D"]),
+                   _ptr(pa["v_N"]), _ptr(pa["s_D"]), _ptr(pa["s0"]), problem.get("cfl", 0.5),
+                   problem.get("dt_mode", LRBMS_DT_CFL), problem.get("dt_fixed", 0.0),
+                   problem.get("dt_max", 0.0), problem.get("mean_weights", 0))
+
+
+def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None):
+    """Build offline data on the GPU for each problem (dicts as for
+    lrbms_offline_load; opts: dicts with M, n_steps_T, N_E, mu, c_pen) and
+    admit n_copies simulations per problem. rot: optional list (len
+    n_prob*n_copies) of concatenated per-subdomain orthogonal matrices or
+    None entries. Returns the simulation ids."""
+    keep = {}
+    n = len(problems)
+    probs = (Problem * n)(*[_problem_struct(p, keep) for p in problems])
+    ol = []
+    for o in opts:
+        ne = np.ascontiguousarray(o["N_E"], dtype=np.int32)
+        mu = np.ascontiguousarray(o["mu"], dtype=np.float64)
+        keep[id(ne)] = ne
+        keep[id(mu)] = mu
+        ol.append(BuildOpts(o["M"], o["n_steps_T"], _ptr(ne), mu.shape[0], _ptr(mu), o["c_pen"]))
+    oarr = (BuildOpts * n)(*ol)
+    rp = None
+    if rot is not None:
+        rot = [None if r is None else np.ascontiguousarray(r, dtype=np.float64) for r in rot]
+        keep["rot"] = rot
+        rp = (C.c_void_p * len(rot))(*[None if r is None else _ptr(r) for r in rot])
+    ids = (C.c_int * (n * n_copies))()
+    _check(ctx, library().lrbms_offline_build(ctx, n, probs, oarr, n_copies, rp, ids))
+    del keep
+    return list(ids)
 
 
 def lrbms_offline_load(ctx, problem: dict, offline: dict) -> int:

