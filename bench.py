@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark: batched LRBMS online steps/s and step latency on one GB300.
+
+Workload (default, "batch"): n_sims concurrent 2D two-phase simulations on a
+128x128 fine grid with 8x8 subdomains, seeded log-normal permeability
+(sigma 1, correlation 0.1), viscosity ratio U[2,20] per physical dataset,
+Corey relative permeabilities, M = 8 mobility profiles, requested local basis
+sizes U{5..30} per subdomain (capped at the number of independent snapshot
+restrictions). Offline data are built on the GPU by lrbms_offline_build from
+n_prob physical datasets; every other simulation is a copy with randomly
+rotated local bases (distinct bytes, identical physics). One step = one
+online step (Algorithm 3, step 5) of every simulation.
+
+Prints one JSON line. `value` is sim-steps/s with all data resident in HBM;
+`e2e` is the same metric through lrbms_step_io with the saturation read from
+and written to pinned host memory every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Batched LRBMS online steps/s and p99 step latency vs plain FP64 GPU path"
+FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA loop: 1.19)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: about 3 s of work)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-sims", type=int, default=512)
+    ap.add_argument("--n-prob", type=int, default=8)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--S", type=int, default=8)
+    ap.add_argument("--n-snap", type=int, default=40)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="storage of bases and components (mixed: FP32)")
+    ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"],
+                    help="reduced solve: FP64 Cholesky, or FP32 Cholesky with FP64 refinement")
+    ap.add_argument("--horizon", type=int, default=300, help="steps per simulation (warm-up + timed)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def workload_name(a) -> str:
+    return (f"{a.n_sims} concurrent 2D two-phase LRBMS simulations, {a.n}x{a.n} fine grid, "
+            f"{a.S}x{a.S} subdomains, basis sizes U{{5..30}}, M=8, viscosity ratio U[2,20]")
+
+
+def problem_inputs(a, p: int, rank: int = 0):
+    """Seeded inputs of physical dataset p (no method arithmetic)."""
+    import numpy as np
+    from synth import make_problem, simplex_params, basis_sizes
+    prob = make_problem("batch", sim_index=p + 1000 * rank, n=a.n, S=a.S)
+    n_sub = prob.Sx * prob.Sy
+    N_E = basis_sizes(n_sub, 5, 30, 31 + p + 1000 * rank)
+    mu = simplex_params(a.n_snap, prob.M, 57 + p + 1000 * rank)
+    return prob, N_E, mu, None
+
+
+def abi_problem(prob):
+    return dict(nx=prob.nx, ny=prob.ny, Sx=prob.Sx, Sy=prob.Sy, Lx=prob.Lx, Ly=prob.Ly, perm=prob.perm,
+                poro=prob.poro, eta_w=prob.eta_w, eta_o=prob.eta_o,
+                relperm=0 if prob.relperm == "corey" else 1, bc_type=prob.bc_type, p_D=prob.p_D,
+                v_N=prob.v_N, s_D=prob.s_D, s0=prob.s0, cfl=prob.cfl, dt_mode=0, dt_fixed=0.0,
+                dt_max=0.0, mean_weights=0)
+
+
+def penalty_scale(prob) -> float:
+    # c_pen = c_f / max(eta) with c_f = 20 max(eta)/min(eta) (penalty of Remark 1)
+    return 20.0 / min(prob.eta_w, prob.eta_o)
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def cpu_baseline_worker(args_dict, q):
+    """Time the CPU oracle's online step (as it stands) on one simulation of
+    the same workload, for about cpu_seconds of work."""
+    try:
+        import numpy as np
+        from types import SimpleNamespace
+        a = SimpleNamespace(**args_dict)
+        from oracle.grid import Coarse
+        from oracle.impes import FineModel
+        from oracle.offline import build_offline
+        from oracle.reduced import online_step
+        prob, N_E, mu, _ = problem_inputs(a, 0)
+        m = FineModel.from_problem(prob, c_pen=penalty_scale(prob))
+        co = Coarse(m.grid, prob.Sx, prob.Sy)
+        t0 = time.perf_counter()
+        off = build_offline(m, co, prob.s0, prob.n_steps, prob.M, kind="snapshots", mus=mu, N_E=N_E)
+        t_off = time.perf_counter() - t0
+        s = prob.s0.copy()
+        online_step(m, off, s)  # warm-up
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            s = online_step(m, off, s)["s"]
+            n += 1
+            if time.perf_counter() - t0 >= a.cpu_seconds:
+                break
+        el = time.perf_counter() - t0
+        try:
+            from threadpoolctl import threadpool_info
+            cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+        except Exception:
+            cores = os.cpu_count()
+        q.put(dict(value=n / el, unit="sim-steps/s", cores=int(cores), kind="oracle",
+                   sample=f"{n} online steps of 1 simulation of the same workload "
+                          f"(N={int(off.N)}), NumPy/SciPy FP64; offline build {t_off:.1f} s not timed",
+                   seconds=el))
+    except Exception as e:  # report, do not hide
+        q.put(dict(error=repr(e)))
+
+
+def start_cpu_baseline(a):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=cpu_baseline_worker, args=(vars(a), q), daemon=True)
+    p.start()
+    return p, q
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic work
+def solve_flops(N_E, Sx: int, refine: int = 1) -> float:
+    """FP64 flops of the envelope block Cholesky, the two substitutions and the
+    refinement, as implemented (per simulation)."""
+    n = len(N_E)
+    xoff = [0]
+    for v in N_E:
+        xoff.append(xoff[-1] + int(v))
+    fl = 0.0
+    for k in range(n):
+        jl = max(0, k - Sx)
+        Nk = N_E[k]
+        for j in range(jl, k + 1):
+            Nj = N_E[j]
+            ln = xoff[j] - xoff[jl]
+            if j < k:
+                fl += 2.0 * Nk * Nj * ln + Nk * Nj * (Nj + 1)
+            else:
+                fl += Nk * (Nk + 1) * ln + 2.0 * Nk ** 3 / 3.0
+    subst = 0.0
+    for k in range(n):
+        jl = max(0, k - Sx)
+        W = xoff[k + 1] - xoff[jl]
+        subst += 2.0 * 2.0 * N_E[k] * (W - N_E[k]) + 2.0 * N_E[k] * (N_E[k] + 1)
+    nnz = sum(int(v) ** 2 for v in N_E)
+    I = lambda e: e % Sx  # noqa: E731
+    for e in range(n):
+        if I(e) < Sx - 1 and e + 1 < n:
+            nnz += 2 * N_E[e] * N_E[e + 1]
+        if e + Sx < n:
+            nnz += 2 * N_E[e] * N_E[e + Sx]
+    return fl + subst * (1 + refine) + refine * 2.0 * nnz
+
+
+def stream_bytes(N_E, Sx: int, cells: int, M: int, elem: int) -> dict:
+    """Algorithmic bytes per simulation of the streaming phases."""
+    n = len(N_E)
+    a = sum(int(v) ** 2 for v in N_E)
+    for e in range(n):
+        if e % Sx < Sx - 1 and e + 1 < n:
+            a += N_E[e] * N_E[e + 1]
+        if e + Sx < n:
+            a += N_E[e] * N_E[e + Sx]
+    N = int(sum(N_E))
+    return {"assemble": (M + 1) * a * elem + a * 8 + (M + 1) * N * 8 + N * 8,
+            "reconstruct": sum(3 * cells * int(v) * elem for v in N_E) + 24 * cells * n + 8 * N}
+
+
+# ------------------------------------------------------------------ main arms
+def run_reference(a, rank: int, world: int):
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    p, q = start_cpu_baseline(a)
+    p.join()
+    r = q.get() if not q.empty() else {"error": "no result"}
+    if "error" in r:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle baseline failed: {r['error']}"}))
+        return
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / r["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample": "one simulation (CPU)"},
+            "cpu_baseline": {"value": r["value"], "unit": r["unit"], "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    _ = mp
+
+
+def main():
+    a = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = start_cpu_baseline(a)  # spawned before the first GPU call
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    from paper_1405_2810_gb300 import build, lrbms as L
+    from synth import random_orthogonal
+    build.build()
+
+    stream = torch.cuda.Stream()  # a real stream: the library and the events share it
+    torch.cuda.set_stream(stream)
+    free, _tot = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.45, 96 << 30))
+    prec = L.LRBMS_FP64 if a.precision == "fp64" else L.LRBMS_MIXED
+    solver = L.LRBMS_SOLVE_MIXED if a.solver == "mixed" else L.LRBMS_SOLVE_FP64
+    ctx = L.lrbms_create(precision=prec, max_slots=a.n_sims + 8, hbm_budget=budget,
+                         stream=stream.cuda_stream, device=local, solver=solver)
+
+    # ---- offline data on the GPU (not timed)
+    t0 = time.perf_counter()
+    n_copies = a.n_sims // a.n_prob
+    assert n_copies * a.n_prob == a.n_sims, "n_sims must be a multiple of n_prob"
+    ids, sizes = [], []
+    rng = np.random.default_rng(2024 + rank)
+    per_call = 4
+    for p0 in range(0, a.n_prob, per_call):
+        probs, opts, rots = [], [], []
+        for p in range(p0, min(a.n_prob, p0 + per_call)):
+            prob, N_E, mu, _ = problem_inputs(a, p, rank)
+            probs.append(abi_problem(prob))
+            opts.append(dict(M=prob.M, n_steps_T=prob.n_steps, N_E=N_E, mu=mu, c_pen=penalty_scale(prob),
+                             allow_fewer=1))
+            rots.append(N_E)
+        got_ids, got = L.lrbms_offline_build(ctx, probs, opts, 1, None, return_sizes=True)
+        for k, sid in enumerate(got_ids):
+            ids.append(sid)
+            sizes.append(got[k])
+            for r in range(1, n_copies):  # copies with randomly rotated local bases
+                Q = np.concatenate([random_orthogonal(int(v), rng).reshape(-1) for v in got[k]])
+                ids.append(L.lrbms_clone(ctx, sid, Q))
+    t_build = time.perf_counter() - t0
+    sizes = np.array(sizes)
+    N_mean = float(sizes.sum(axis=1).mean())
+    used, cap = L.lrbms_memory(ctx)
+
+    # ---- warm-up
+    st = L.lrbms_step(ctx, ids, max(a.warmup, 1))
+    assert np.all(st == 0), f"warm-up status {np.unique(st)}"
+    # steps for about 3 s if not given
+    K = a.steps
+    if K <= 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lrbms_step(ctx, ids, 1, wait=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        K = max(10, int(math.ceil(3000.0 / max(e0.elapsed_time(e1), 1e-3))))
+        K = min(K, a.horizon - max(a.warmup, 1) - 1)  # stay within the simulated horizon
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    L.lrbms_profile_start(ctx, K)
+    launches0 = L.lrbms_launch_count(ctx)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    L.lrbms_step(ctx, ids, K, wait=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = L.lrbms_launch_count(ctx) - launches0
+    phase_ms, step_ms = L.lrbms_profile_read(ctx, K)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    status = L.lrbms_step(ctx, ids, 0)
+    n_ok = int(np.sum(status == 0))
+    value = world * a.n_sims * K / (elapsed_ms / 1000.0)
+
+    # ---- end to end through lrbms_step_io with pinned host buffers
+    n_cells = a.n * a.n
+    Ke = a.e2e_steps or max(3, min(K, 20))
+    s_in = [torch.zeros(n_cells, dtype=torch.float64).pin_memory() for _ in ids]
+    s_out = [torch.empty(n_cells, dtype=torch.float64).pin_memory() for _ in ids]
+    L.lrbms_step_io(ctx, ids, 1, None, s_out)  # current state -> host
+    for i in range(len(ids)):
+        s_in[i].copy_(s_out[i])
+    L.lrbms_step_io(ctx, ids, 1, s_in, s_out)  # warm-up of the io path
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        for i in range(len(ids)):
+            s_in[i], s_out[i] = s_out[i], s_in[i]
+        L.lrbms_step_io(ctx, ids, 1, s_in, s_out)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * a.n_sims * Ke / e2e_s
+
+    # ---- plain FP64 single-simulation path: one simulation, one step per call
+    ctx1 = L.lrbms_create(precision=L.LRBMS_FP64, max_slots=2, hbm_budget=1 << 30, device=local)
+    prob, N_E, mu, _ = problem_inputs(a, 0, rank)
+    (one,) = L.lrbms_offline_build(ctx1, [abi_problem(prob)], [dict(M=prob.M, n_steps_T=prob.n_steps,
+                                   N_E=sizes[0], mu=mu, c_pen=penalty_scale(prob))], 1)
+    L.lrbms_step(ctx1, [one], 3)
+    n1 = max(5, min(50, K))
+    t0 = time.perf_counter()
+    for _ in range(n1):
+        L.lrbms_step(ctx1, [one], 1)
+    plain = n1 / (time.perf_counter() - t0)
+    L.lrbms_destroy(ctx1)
+
+    # ---- roofline of the dominant phase
+    names = L.PHASES
+    dom = int(np.argmax(phase_ms))
+    Sx = a.S
+    cells = (a.n // a.S) ** 2
+    elem = 8 if a.precision == "fp64" else 4
+    if names[dom] == "solve":
+        work = sum(solve_flops(list(sz), Sx) for sz in sizes) * n_copies * 1e-12
+        achieved = work / (phase_ms[dom] / 1000.0)
+        roof = {"bound": "alu", "kernel": "k_chol_solve", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit counts and clock)"}
+    else:
+        sb = [stream_bytes(list(sz), Sx, cells, 8, elem) for sz in sizes]
+        key = names[dom] if names[dom] in sb[0] else None
+        byt = sum(b.get(key, 0) for b in sb) * n_copies if key else 0
+        achieved = byt / (phase_ms[dom] / 1000.0) / 1e9
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None}
+
+    cpu_line = None
+    if cpu is not None:
+        proc, q = cpu
+        proc.join(timeout=900)
+        r = q.get() if not q.empty() else {"error": "cpu baseline did not finish"}
+        cpu_line = r if "error" in r else {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        steps_sorted = sorted(step_ms.tolist())
+        p50 = steps_sorted[len(steps_sorted) // 2]
+        p99 = steps_sorted[min(len(steps_sorted) - 1, int(math.ceil(0.99 * len(steps_sorted))) - 1)]
+        line = {
+            "metric": METRIC, "value": value, "unit": "sim-steps/s", "n_gpus": world, "steps": K,
+            "warmup": a.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": ("f64" if a.solver == "fp64" else "f64+f32") if a.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a), "n_sims": a.n_sims, "physical_datasets": a.n_prob,
+                       "grid": f"{a.n}x{a.n}", "subdomains": f"{a.S}x{a.S}", "M": 8,
+                       "basis_sizes_mean_N": N_mean, "precision": a.precision, "solver": a.solver,
+                       "l2": f"inputs larger than L2: {used / 2**30:.1f} GiB resident",
+                       "p50_step_ms": p50, "p99_step_ms": p99, "sims_ok": n_ok,
+                       "offline_build_s": t_build, "parallelism": f"replicas x{world}"},
+            "phases_ms": {n: float(v) for n, v in zip(names, phase_ms)},
+            "roofline": roof,
+            "plain_fp64_single_sim_steps_per_s": plain,
+            "vs_plain_fp64_single_sim": value / plain,
+            "e2e": {"value": e2e_value, "unit": "sim-steps/s", "h2d_bytes_per_step": 8 * n_cells * a.n_sims,
+                    "d2h_bytes_per_step": 8 * n_cells * a.n_sims},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu_line,
+        }
+        print(json.dumps(line))
+    L.lrbms_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -71,6 +71,7 @@ typedef enum {
 } lrbms_status;
 
 enum { LRBMS_FP64 = 0, LRBMS_MIXED = 1 };
+enum { LRBMS_SOLVE_FP64 = 0, LRBMS_SOLVE_MIXED = 1 };
 enum { LRBMS_COREY = 0, LRBMS_LINEAR = 1 };
 enum { LRBMS_DT_CFL = 0, LRBMS_DT_FIXED = 1 };
 
@@ -84,6 +85,13 @@ typedef struct {
   void* stream;      /* cudaStream_t for all work, or NULL for a stream
                         owned by the context                                */
   int device;        /* CUDA device ordinal                                 */
+  int solver;        /* reduced solve: LRBMS_SOLVE_FP64 (FP64 block Cholesky,
+                        FP64 substitutions) or LRBMS_SOLVE_MIXED (FP32 block
+                        Cholesky and substitutions, iterative refinement with
+                        FP64 residuals and updates; an FP32 factorisation that
+                        meets a non-positive pivot is redone in FP64)       */
+  int refine_iters;  /* refinement steps after the first solve; 0: default
+                        (1 for FP64, 4 for MIXED); at most 16               */
 } lrbms_config;
 
 /* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with
@@ -202,6 +210,9 @@ typedef struct {
   int n_snap;        /* number of snapshot parameters                          */
   const double* mu;  /* [n_snap][M] snapshot parameters (drawn by the caller)  */
   double c_pen;      /* penalty scale c_f / max(eta_w, eta_o)                  */
+  int allow_fewer;   /* 0: fail with LRBMS_E_FORMAT when a subdomain's snapshots
+                        give fewer than N_E independent functions; 1: keep the
+                        functions obtained (smaller N_E)                       */
 } lrbms_build_opts;
 
 /* Build the offline data of n_prob problems (same grids, one options entry
@@ -209,12 +220,44 @@ typedef struct {
  * local bases rotated by the orthogonal matrices rot[p*n_copies + r]
  * (concatenated row-major N_E x N_E per subdomain; NULL entry or NULL rot: no
  * rotation), which changes the stored bytes but not the online results.
- * sim_ids receives n_prob*n_copies slots. Scratch device memory is taken with
- * cudaMalloc and released before return. LRBMS_E_FORMAT if the snapshots do
- * not span the requested local basis sizes. */
+ * sim_ids receives n_prob*n_copies slots; achieved (optional, [n_prob][Sx*Sy])
+ * the local basis sizes built. Scratch device memory is taken with cudaMalloc
+ * and released before return. LRBMS_E_FORMAT if the snapshots do not span the
+ * requested local basis sizes and allow_fewer is 0. */
 int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
                         const lrbms_build_opts* opts, int n_copies,
-                        const double* const* rot, int* sim_ids);
+                        const double* const* rot, int* sim_ids, int* achieved);
+
+/* Admit a copy of resident simulation src whose local bases are rotated by
+ * the orthogonal matrices in rot (concatenated row-major N_E x N_E per
+ * subdomain, host or device; NULL: an unrotated copy): Phi_E Q_E, and
+ * Q_E^T (.) Q_E' for every component block and right-hand side. The online
+ * results are unchanged up to round-off; the stored bytes differ. The copy
+ * starts from src's current saturation, at time 0. */
+int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_id);
+
+/* Like lrbms_step, with the saturation exchanged with caller memory: before
+ * the first step each simulation's saturation is read from s_in[i], after the
+ * last step it is written to s_out[i] (n_cells doubles each; pinned host or
+ * device memory, read and written by kernels through unified addressing;
+ * NULL arrays skip the exchange). Waits for completion. */
+int lrbms_step_io(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int n_steps,
+                  const double* const* s_in, double* const* s_out, int* status);
+
+/* Phases of one step, in launch order. */
+enum {
+  LRBMS_PHASE_FIT = 0, LRBMS_PHASE_ASSEMBLE, LRBMS_PHASE_SOLVE, LRBMS_PHASE_RECONSTRUCT,
+  LRBMS_PHASE_FLUX, LRBMS_PHASE_CFL, LRBMS_PHASE_TRANSPORT, LRBMS_PHASE_FINALIZE,
+  LRBMS_N_PHASES
+};
+/* Profiling of live steps: with max_steps > 0 the next max_steps steps record
+ * a CUDA event before the first phase and after every phase, on the context
+ * stream (max_steps = 0 turns it off). */
+int lrbms_profile_start(lrbms_ctx* ctx, int max_steps);
+/* Wait, then report for the recorded steps the mean time of each phase
+ * (phase_ms[LRBMS_N_PHASES], milliseconds) and each step's time
+ * (step_ms[max_steps]); *n_recorded receives the number of steps recorded. */
+int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n_recorded);
 
 /* Wait for all enqueued work. */
 int lrbms_sync(lrbms_ctx* ctx);

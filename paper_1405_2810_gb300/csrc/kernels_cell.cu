@@ -380,6 +380,26 @@ __global__ void k_finalize(const SimDev* __restrict__ sims, const int* __restric
   S.steps[0] += 1;
 }
 
+// Saturation exchange with caller memory (pinned host or device pointers).
+__global__ void k_sat_in(const SimDev* __restrict__ sims, const int* __restrict__ active,
+                         const double* const* __restrict__ src) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const double* in = src[blockIdx.y];
+  if (!in) return;
+  double* s = S.s + (size_t)(S.steps[0] & 1) * S.n_cells;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.n_cells; e += gridDim.x * blockDim.x)
+    s[e] = in[e];
+}
+__global__ void k_sat_out(const SimDev* __restrict__ sims, const int* __restrict__ active,
+                          double* const* __restrict__ dst) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  double* out = dst[blockIdx.y];
+  if (!out) return;
+  const double* s = S.s + (size_t)(S.steps[0] & 1) * S.n_cells;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.n_cells; e += gridDim.x * blockDim.x)
+    out[e] = s[e];
+}
+
 __global__ void k_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
@@ -393,6 +413,12 @@ void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st) {
   size_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_to_float<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
+}
+
+void launch_sat_io(const SimDev* sims, const int* active, int n_active, const double* const* src,
+                   double* const* dst, cudaStream_t st) {
+  if (src) k_sat_in<<<dim3(16, n_active), 256, 0, st>>>(sims, active, src);
+  if (dst) k_sat_out<<<dim3(16, n_active), 256, 0, st>>>(sims, active, dst);
 }
 
 void launch_fit(const SimDev* sims, const int* active, int n_active, int max_tiles,

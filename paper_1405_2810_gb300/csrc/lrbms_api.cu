@@ -90,6 +90,8 @@ struct Slot {
 struct lrbms_ctx {
   int device = 0;
   int precision = LRBMS_FP64;
+  int solver = LRBMS_SOLVE_FP64;
+  int refine_iters = 1;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   Arena arena;
@@ -97,8 +99,12 @@ struct lrbms_ctx {
   SimDev* d_sims = nullptr;
   int* d_active = nullptr;
   std::vector<int> last_active;
+  const double** d_io = nullptr;  // [2 * max_slots] saturation exchange pointers
   std::string err;
   long long launches = 0;
+  // profiling of live steps
+  int prof_cap = 0, prof_n = 0;
+  std::vector<cudaEvent_t> prof_ev;
 };
 
 namespace {
@@ -136,12 +142,15 @@ extern "C" {
 int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   if (!out || !cfg) return LRBMS_E_ARG;
   *out = nullptr;
-  if (cfg->max_slots < 1 || cfg->hbm_budget == 0 ||
-      (cfg->precision != LRBMS_FP64 && cfg->precision != LRBMS_MIXED))
+  if (cfg->max_slots < 1 || cfg->hbm_budget == 0 || cfg->refine_iters < 0 || cfg->refine_iters > 16 ||
+      (cfg->precision != LRBMS_FP64 && cfg->precision != LRBMS_MIXED) ||
+      (cfg->solver != LRBMS_SOLVE_FP64 && cfg->solver != LRBMS_SOLVE_MIXED))
     return LRBMS_E_ARG;
   lrbms_ctx* ctx = new lrbms_ctx();
   ctx->device = cfg->device;
   ctx->precision = cfg->precision;
+  ctx->solver = cfg->solver;
+  ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 4 : 1);
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete ctx;
@@ -158,7 +167,8 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   }
   if (ctx->arena.init(cfg->hbm_budget) != cudaSuccess ||
       cudaMalloc(&ctx->d_sims, sizeof(SimDev) * cfg->max_slots) != cudaSuccess ||
-      cudaMalloc(&ctx->d_active, sizeof(int) * cfg->max_slots) != cudaSuccess) {
+      cudaMalloc(&ctx->d_active, sizeof(int) * cfg->max_slots) != cudaSuccess ||
+      cudaMalloc(&ctx->d_io, sizeof(double*) * 2 * cfg->max_slots) != cudaSuccess) {
     ctx->arena.release();
     if (ctx->d_sims) cudaFree(ctx->d_sims);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -177,6 +187,8 @@ int lrbms_destroy(lrbms_ctx* ctx) {
   ctx->arena.release();
   cudaFree(ctx->d_sims);
   cudaFree(ctx->d_active);
+  cudaFree(ctx->d_io);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return LRBMS_OK;
@@ -185,6 +197,11 @@ int lrbms_destroy(lrbms_ctx* ctx) {
 const char* lrbms_last_error(const lrbms_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx) { return ctx->stream; }
+int lrbms_internal_sim(lrbms_ctx* ctx, int id, SimDev* out) {
+  if (!valid_sim(ctx, id)) return LRBMS_E_STATE;
+  *out = ctx->slots[id].d;
+  return LRBMS_OK;
+}
 int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
 
 long long lrbms_launch_count(const lrbms_ctx* ctx) { return ctx ? ctx->launches : 0; }
@@ -293,7 +310,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_comp32 = mixed ? L.add(4 * Q * (size_t)a_tot) : 0;
   const size_t o_s = L.add(16 * (size_t)n_cells), o_p = L.add(24 * (size_t)n_cells);
   const size_t o_F = L.add(8 * (size_t)n_faces);
-  const size_t o_x = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N), o_y = L.add(8 * (size_t)N),
+  const size_t o_x = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N), o_y = L.add(16 * (size_t)N),
                o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N);
   const size_t o_A = L.add(8 * (size_t)a_tot);
   const size_t o_L = L.add(8 * (size_t)loff[n_sub]), o_Li = L.add(8 * (size_t)ioff[n_sub]);
@@ -422,16 +439,29 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     ctx->last_active = act;
   }
   const int mixed = ctx->precision == LRBMS_MIXED;
-  const int refine = 1;
   for (int k = 0; k < n_steps; ++k) {
+    cudaEvent_t* ev = nullptr;
+    if (ctx->prof_n < ctx->prof_cap) ev = &ctx->prof_ev[(size_t)ctx->prof_n++ * (LRBMS_N_PHASES + 1)];
+    auto mark = [&](int i) {
+      if (ev) cudaEventRecord(ev[i], st);
+    };
+    mark(0);
     lrbms::launch_fit(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    mark(1);
     lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st);
-    lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, refine, st);
+    mark(2);
+    lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, ctx->solver, ctx->refine_iters, st);
+    mark(3);
     lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st);
+    mark(4);
     lrbms::launch_flux(ctx->d_sims, ctx->d_active, n_sims, max_faces, st);
+    mark(5);
     lrbms::launch_cfl(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    mark(6);
     lrbms::launch_transport(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    mark(7);
     lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
+    mark(8);
     ctx->launches += 8;
   }
   CK(cudaGetLastError());
@@ -440,6 +470,83 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     for (int i = 0; i < n_sims; ++i)
       CK(cudaMemcpy(&status[i], ctx->slots[act[i]].d.status, sizeof(int), cudaMemcpyDeviceToHost));
   }
+  return LRBMS_OK;
+}
+
+int lrbms_step_io(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, const double* const* s_in,
+                  double* const* s_out, int* status) {
+  if (!ctx || n_sims < 1 || !ids) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  if (n_sims > (int)ctx->slots.size()) return fail(ctx, LRBMS_E_ARG, "too many simulations");
+  for (int i = 0; i < n_sims; ++i)
+    if (!valid_sim(ctx, ids[i])) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  std::vector<int> act(ids, ids + n_sims);
+  if (act != ctx->last_active) {
+    CK(cudaMemcpyAsync(ctx->d_active, act.data(), sizeof(int) * n_sims, cudaMemcpyHostToDevice, st));
+    ctx->last_active = act;
+  }
+  const size_t ms = ctx->slots.size();
+  std::vector<const double*> ptrs(2 * ms, nullptr);
+  for (int i = 0; i < n_sims; ++i) {
+    ptrs[i] = s_in ? s_in[i] : nullptr;
+    ptrs[ms + i] = s_out ? (const double*)s_out[i] : nullptr;
+  }
+  CK(cudaMemcpyAsync(ctx->d_io, ptrs.data(), sizeof(double*) * 2 * ms, cudaMemcpyHostToDevice, st));
+  if (s_in) {
+    lrbms::launch_sat_io(ctx->d_sims, ctx->d_active, n_sims, ctx->d_io, nullptr, st);
+    ctx->launches += 1;
+  }
+  int rc = lrbms_step(ctx, n_sims, ids, n_steps, nullptr);
+  if (rc) return rc;
+  if (s_out) {
+    lrbms::launch_sat_io(ctx->d_sims, ctx->d_active, n_sims, nullptr, (double* const*)(ctx->d_io + ms), st);
+    ctx->launches += 1;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  if (status)
+    for (int i = 0; i < n_sims; ++i)
+      CK(cudaMemcpy(&status[i], ctx->slots[ids[i]].d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  return LRBMS_OK;
+}
+
+int lrbms_profile_start(lrbms_ctx* ctx, int max_steps) {
+  if (!ctx || max_steps < 0) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t need = (size_t)max_steps * (LRBMS_N_PHASES + 1);
+  while (ctx->prof_ev.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ctx->prof_ev.push_back(e);
+  }
+  ctx->prof_cap = max_steps;
+  ctx->prof_n = 0;
+  return LRBMS_OK;
+}
+
+int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n_recorded) {
+  if (!ctx) return LRBMS_E_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int n = ctx->prof_n;
+  if (n_recorded) *n_recorded = n;
+  std::vector<double> acc(LRBMS_N_PHASES, 0.0);
+  for (int k = 0; k < n; ++k) {
+    cudaEvent_t* ev = &ctx->prof_ev[(size_t)k * (LRBMS_N_PHASES + 1)];
+    for (int ph = 0; ph < LRBMS_N_PHASES; ++ph) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, ev[ph], ev[ph + 1]));
+      acc[ph] += t;
+    }
+    if (step_ms) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, ev[0], ev[LRBMS_N_PHASES]));
+      step_ms[k] = t;
+    }
+  }
+  if (phase_ms)
+    for (int ph = 0; ph < LRBMS_N_PHASES; ++ph) phase_ms[ph] = n ? acc[ph] / n : 0.0;
+  ctx->prof_cap = 0;
   return LRBMS_OK;
 }
 

@@ -57,12 +57,12 @@ struct SimDev {
   const long long* ioff;    // [n_sub+1] inverse of diagonal block k: [N_k][N_k]
 
   // state and work arrays
-  double* s;        // [n_cells]
+  double* s;        // [2][n_cells] ping-pong; current = steps & 1
   double* p;        // [3][n_cells]
   double* F;        // [n_faces]
   double* x;        // [N]
   double* b;        // [N]
-  double* y;        // [N] forward-substitution work
+  double* y;        // [2N] substitution work (forward result, then backward result)
   double* rv;       // [N] refinement residual
   double* dv;       // [N] refinement correction
   double* A;        // [aoff[n_blocks]]
@@ -85,7 +85,7 @@ void launch_fit(const SimDev* sims, const int* active, int n_active, int max_til
                 cudaStream_t st);
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
                      int mixed, cudaStream_t st);
-void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int refine,
+void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
                        cudaStream_t st);
 void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
                         int mixed, cudaStream_t st);
@@ -97,5 +97,7 @@ void launch_transport(const SimDev* sims, const int* active, int n_active, int m
                       cudaStream_t st);
 void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st);
 void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st);
+void launch_sat_io(const SimDev* sims, const int* active, int n_active, const double* const* src,
+                   double* const* dst, cudaStream_t st);
 
 }  // namespace lrbms

@@ -678,7 +678,7 @@ struct FineSolver {
       d.A = b.get<double>(9 * (size_t)n_blocks);
       d.b = b.get<double>(3 * (size_t)n_cells);
       d.x = b.get<double>(3 * (size_t)n_cells);
-      d.y = b.get<double>(3 * (size_t)n_cells);
+      d.y = b.get<double>(6 * (size_t)n_cells);
       d.rv = b.get<double>(3 * (size_t)n_cells);
       d.dv = b.get<double>(3 * (size_t)n_cells);
       d.L = b.get<double>((size_t)lo[n_cells]);
@@ -703,13 +703,10 @@ struct FineSolver {
 
 using namespace lrbms;
 
-extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
-                                   const lrbms_build_opts* opts, int n_copies,
-                                   const double* const* rot, int* sim_ids);
-
 // Defined in lrbms_api.cu.
 extern "C" cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx);
 extern "C" int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg);
+extern "C" int lrbms_internal_sim(lrbms_ctx* ctx, int id, lrbms::SimDev* out);
 
 #define BCK(call)                                                              \
   do {                                                                         \
@@ -721,7 +718,7 @@ extern "C" int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg);
 
 extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
                                    const lrbms_build_opts* opts, int n_copies,
-                                   const double* const* rot, int* sim_ids) {
+                                   const double* const* rot, int* sim_ids, int* achieved) {
   if (!ctx || n_prob < 1 || !probs || !opts || n_copies < 1 || !sim_ids)
     return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad arguments");
   cudaStream_t st = lrbms_internal_stream(ctx);
@@ -794,7 +791,7 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
       jobs[p] = SysJob{p, 0, 3, 0, nullptr, init.sims[p].A, init.sims[p].A + 9 * (size_t)n_cells,
                        init.sims[p].b};
     if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "fine assembly");
-    launch_chol_solve(init.d_sims, init.d_active, n_prob, 1, st);
+    launch_chol_solve(init.d_sims, init.d_active, n_prob, 0, 1, st);
   }
   // ---- velocity, time-of-flight and profiles (steps 1(b), 1(c))
   std::vector<double*> hF(n_prob), hta(n_prob), htb(n_prob);
@@ -891,7 +888,7 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
       }
     }
     if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "snapshot assembly");
-    launch_chol_solve(snaps.d_sims, snaps.d_active, n_snap_tot, 1, st);
+    launch_chol_solve(snaps.d_sims, snaps.d_active, n_snap_tot, 0, 1, st);
   }
 
   // ---- local bases (step 2(e))
@@ -925,11 +922,33 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
     std::vector<int> got((size_t)n_prob * n_sub);
     BCK(cudaMemcpyAsync(got.data(), dgot, 4 * got.size(), cudaMemcpyDeviceToHost, st));
     BCK(cudaStreamSynchronize(st));
-    for (int p = 0; p < n_prob; ++p)
+    for (int p = 0; p < n_prob; ++p) {
+      bool fewer = false;
       for (int E = 0; E < n_sub; ++E)
-        if (got[p * n_sub + E] != NE[p][E])
-          return lrbms_internal_fail(ctx, LRBMS_E_FORMAT,
-                                     "too few independent snapshots for the requested local basis size");
+        if (got[p * n_sub + E] != NE[p][E]) {
+          if (!opts[p].allow_fewer)
+            return lrbms_internal_fail(ctx, LRBMS_E_FORMAT,
+                                       "too few independent snapshots for the requested local basis size");
+          fewer = true;
+        }
+      if (!fewer) continue;
+      // keep the functions obtained: compact the bases to the achieved sizes
+      std::vector<long long> off2(n_sub + 1, 0);
+      for (int E = 0; E < n_sub; ++E) off2[E + 1] = off2[E] + (long long)got[p * n_sub + E] * 3 * cells;
+      double* P2 = B.get<double>((size_t)off2[n_sub]);
+      if (!P2) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "basis buffers");
+      for (int E = 0; E < n_sub; ++E) {
+        BCK(cudaMemcpyAsync(P2 + off2[E], Phi[p] + phioff[p][E], 8 * (size_t)(off2[E + 1] - off2[E]),
+                            cudaMemcpyDeviceToDevice, st));
+        NE[p][E] = got[p * n_sub + E];
+      }
+      Phi[p] = P2;
+      phioff[p] = off2;
+    }
+    if (achieved) {
+      for (int p = 0; p < n_prob; ++p)
+        for (int E = 0; E < n_sub; ++E) achieved[p * n_sub + E] = NE[p][E];
+    }
   }
 
   // ---- components (Section 4.4): fine blocks per component, then projection
@@ -1063,4 +1082,74 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
   }
   BCK(cudaStreamSynchronize(st));
   return LRBMS_OK;
+}
+
+extern "C" int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_id) {
+  if (!ctx || !sim_id) return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad arguments");
+  SimDev d;
+  if (lrbms_internal_sim(ctx, src, &d)) return lrbms_internal_fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  cudaStream_t st = lrbms_internal_stream(ctx);
+  BCK(cudaStreamSynchronize(st));
+  const int n_sub = d.n_sub, n_cf = d.n_cf, Q = d.M + 1, cells = d.cx * d.cy;
+  std::vector<int> NE(n_sub), xoff(n_sub + 1);
+  std::vector<long long> aoff(d.n_blocks + 1), phioff(n_sub);
+  BCK(cudaMemcpy(NE.data(), d.NE, 4 * (size_t)n_sub, cudaMemcpyDeviceToHost));
+  BCK(cudaMemcpy(xoff.data(), d.xoff, 4 * (size_t)(n_sub + 1), cudaMemcpyDeviceToHost));
+  BCK(cudaMemcpy(aoff.data(), d.aoff, 8 * (size_t)(d.n_blocks + 1), cudaMemcpyDeviceToHost));
+  BCK(cudaMemcpy(phioff.data(), d.phi_off, 8 * (size_t)n_sub, cudaMemcpyDeviceToHost));
+  std::vector<int> cfm(n_cf), cfp(n_cf);
+  {
+    int f = 0;
+    for (int J = 0; J < d.Sy; ++J)
+      for (int I = 0; I + 1 < d.Sx; ++I, ++f) cfm[f] = J * d.Sx + I, cfp[f] = J * d.Sx + I + 1;
+    for (int J = 0; J + 1 < d.Sy; ++J)
+      for (int I = 0; I < d.Sx; ++I, ++f) cfm[f] = J * d.Sx + I, cfp[f] = (J + 1) * d.Sx + I;
+  }
+  std::vector<long long> qoff(n_sub + 1, 0);
+  for (int E = 0; E < n_sub; ++E) qoff[E + 1] = qoff[E] + (long long)NE[E] * NE[E];
+  const long long phi_tot = phioff[n_sub - 1] + (long long)NE[n_sub - 1] * 3 * cells;
+  DevBuf B;
+  double* rPhi = B.get<double>((size_t)phi_tot);
+  double* rcomp = B.get<double>((size_t)Q * aoff[d.n_blocks]);
+  double* rrhs = B.get<double>((size_t)Q * xoff[n_sub]);
+  double* dQ = B.get<double>((size_t)qoff[n_sub]);
+  double* s0 = B.get<double>((size_t)d.n_cells);
+  if (!rPhi || !rcomp || !rrhs || !dQ || !s0) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "clone buffers");
+  int steps = 0;
+  BCK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
+  BCK(cudaMemcpyAsync(s0, d.s + (size_t)(steps & 1) * d.n_cells, 8 * (size_t)d.n_cells, cudaMemcpyDeviceToDevice, st));
+  const double *uPhi = d.Phi, *ucomp = d.comp, *urhs = d.rhs;
+  if (rot) {
+    BCK(cudaMemcpyAsync(dQ, rot, 8 * (size_t)qoff[n_sub], cudaMemcpyDefault, st));
+    std::vector<RotJob> rj;
+    for (int E = 0; E < n_sub; ++E) {
+      rj.push_back(RotJob{0, NE[E], NE[E], 3 * cells, Q, dQ + qoff[E], dQ + qoff[E], d.Phi + phioff[E], rPhi + phioff[E]});
+      rj.push_back(RotJob{1, NE[E], NE[E], 0, Q, dQ + qoff[E], dQ + qoff[E], d.comp + (size_t)Q * aoff[E],
+                          rcomp + (size_t)Q * aoff[E]});
+      rj.push_back(RotJob{2, NE[E], NE[E], 0, Q, dQ + qoff[E], dQ + qoff[E], d.rhs + (size_t)Q * xoff[E],
+                          rrhs + (size_t)Q * xoff[E]});
+    }
+    for (int c = 0; c < n_cf; ++c)
+      rj.push_back(RotJob{1, NE[cfm[c]], NE[cfp[c]], 0, Q, dQ + qoff[cfm[c]], dQ + qoff[cfp[c]],
+                          d.comp + (size_t)Q * aoff[n_sub + c], rcomp + (size_t)Q * aoff[n_sub + c]});
+    RotJob* dj = B.get<RotJob>(rj.size());
+    if (!dj) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "rotation jobs");
+    BCK(cudaMemcpyAsync(dj, rj.data(), sizeof(RotJob) * rj.size(), cudaMemcpyHostToDevice, st));
+    k_rotate<<<(unsigned)rj.size(), 256, 0, st>>>(dj);
+    BCK(cudaGetLastError());
+    uPhi = rPhi; ucomp = rcomp; urhs = rrhs;
+  }
+  lrbms_problem pr{};
+  pr.nx = d.nx; pr.ny = d.ny; pr.Sx = d.Sx; pr.Sy = d.Sy;
+  pr.Lx = d.hx * d.nx; pr.Ly = d.hy * d.ny;
+  pr.perm = d.perm; pr.poro = d.poro; pr.eta_w = 1.0 / d.inv_eta_w; pr.eta_o = 1.0 / d.inv_eta_o;
+  pr.relperm = d.relperm; pr.bc_type = d.bc_type; pr.p_D = d.p_D; pr.v_N = d.v_N; pr.s_D = d.s_D;
+  pr.s0 = s0; pr.cfl = d.cfl; pr.dt_mode = d.dt_mode; pr.dt_fixed = d.dt_fixed; pr.dt_max = d.dt_max;
+  pr.mean_weights = d.swapped;
+  lrbms_offline off{};
+  off.M = d.M; off.N_E = d.NE; off.prof_idx = d.prof_idx; off.prof = d.prof; off.Gpinv = d.Gpinv;
+  off.Phi = uPhi; off.Dblk = ucomp; off.Fblk = n_cf ? ucomp + (size_t)Q * aoff[n_sub] : nullptr;
+  off.rhs = urhs; off.c_pen = d.c_pen; off.Lf = d.Lf;
+  BCK(cudaStreamSynchronize(st));
+  return lrbms_offline_load(ctx, &pr, &off, sim_id);
 }

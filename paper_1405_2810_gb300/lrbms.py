@@ -31,10 +31,12 @@ LRBMS_COREY = 0
 LRBMS_LINEAR = 1
 LRBMS_DT_CFL = 0
 LRBMS_DT_FIXED = 1
+LRBMS_SOLVE_FP64 = 0
+LRBMS_SOLVE_MIXED = 1
 FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS = range(9)
 
 EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offline_build",
-            "lrbms_release", "lrbms_step",
+            "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
             "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count",
             "lrbms_last_error"]
@@ -48,7 +50,8 @@ class LrbmsError(RuntimeError):
 
 class Config(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_slots", C.c_int), ("hbm_budget", C.c_size_t),
-                ("stream", C.c_void_p), ("device", C.c_int)]
+                ("stream", C.c_void_p), ("device", C.c_int), ("solver", C.c_int),
+                ("refine_iters", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -70,7 +73,7 @@ class Offline(C.Structure):
 
 class BuildOpts(C.Structure):
     _fields_ = [("M", C.c_int), ("n_steps_T", C.c_int), ("N_E", C.c_void_p), ("n_snap", C.c_int),
-                ("mu", C.c_void_p), ("c_pen", C.c_double)]
+                ("mu", C.c_void_p), ("c_pen", C.c_double), ("allow_fewer", C.c_int)]
 
 
 _lib = None
@@ -88,7 +91,11 @@ def library() -> C.CDLL:
         lib.lrbms_destroy.argtypes = [vp]
         lib.lrbms_offline_load.argtypes = [vp, C.POINTER(Problem), C.POINTER(Offline), C.POINTER(i)]
         lib.lrbms_offline_build.argtypes = [vp, i, C.POINTER(Problem), C.POINTER(BuildOpts), i,
-                                            C.POINTER(vp), C.POINTER(i)]
+                                            C.POINTER(vp), C.POINTER(i), C.POINTER(i)]
+        lib.lrbms_clone.argtypes = [vp, i, vp, C.POINTER(i)]
+        lib.lrbms_step_io.argtypes = [vp, i, vp, i, C.POINTER(vp), C.POINTER(vp), vp]
+        lib.lrbms_profile_start.argtypes = [vp, i]
+        lib.lrbms_profile_read.argtypes = [vp, dp, dp, C.POINTER(i)]
         lib.lrbms_release.argtypes = [vp, i]
         lib.lrbms_step.argtypes = [vp, i, vp, i, vp]
         lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
@@ -130,8 +137,9 @@ def _as(a, dtype):
 
 
 # ------------------------------------------------------------------ C-ABI names
-def lrbms_create(precision=LRBMS_FP64, max_slots=64, hbm_budget=8 << 30, stream=None, device=0):
-    cfg = Config(precision, max_slots, hbm_budget, stream, device)
+def lrbms_create(precision=LRBMS_FP64, max_slots=64, hbm_budget=8 << 30, stream=None, device=0,
+                 solver=LRBMS_SOLVE_FP64, refine_iters=0):
+    cfg = Config(precision, max_slots, hbm_budget, stream, device, solver, refine_iters)
     h = C.c_void_p()
     _check(None, library().lrbms_create(C.byref(h), C.byref(cfg)))
     return h
@@ -155,7 +163,7 @@ def _problem_struct(problem: dict, keep: dict) -> Problem:
                    problem.get("dt_max", 0.0), problem.get("mean_weights", 0))
 
 
-def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None):
+def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return_sizes=False):
     """Build offline data on the GPU for each problem (dicts as for
     lrbms_offline_load; opts: dicts with M, n_steps_T, N_E, mu, c_pen) and
     admit n_copies simulations per problem. rot: optional list (len
@@ -170,7 +178,8 @@ def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None):
         mu = np.ascontiguousarray(o["mu"], dtype=np.float64)
         keep[id(ne)] = ne
         keep[id(mu)] = mu
-        ol.append(BuildOpts(o["M"], o["n_steps_T"], _ptr(ne), mu.shape[0], _ptr(mu), o["c_pen"]))
+        ol.append(BuildOpts(o["M"], o["n_steps_T"], _ptr(ne), mu.shape[0], _ptr(mu), o["c_pen"],
+                            int(o.get("allow_fewer", 0))))
     oarr = (BuildOpts * n)(*ol)
     rp = None
     if rot is not None:
@@ -178,9 +187,22 @@ def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None):
         keep["rot"] = rot
         rp = (C.c_void_p * len(rot))(*[None if r is None else _ptr(r) for r in rot])
     ids = (C.c_int * (n * n_copies))()
-    _check(ctx, library().lrbms_offline_build(ctx, n, probs, oarr, n_copies, rp, ids))
+    n_sub = problems[0]["Sx"] * problems[0]["Sy"]
+    got = (C.c_int * (n * n_sub))()
+    _check(ctx, library().lrbms_offline_build(ctx, n, probs, oarr, n_copies, rp, ids, got))
     del keep
+    if return_sizes:
+        return list(ids), np.array(got, dtype=np.int32).reshape(n, n_sub)
     return list(ids)
+
+
+def lrbms_clone(ctx, src: int, rot=None) -> int:
+    """Admit a copy of simulation src with local bases rotated by rot
+    (concatenated per-subdomain orthogonal matrices) or unrotated."""
+    r = _as(rot, np.float64)
+    sid = C.c_int()
+    _check(ctx, library().lrbms_clone(ctx, src, _ptr(r), C.byref(sid)))
+    return sid.value
 
 
 def lrbms_offline_load(ctx, problem: dict, offline: dict) -> int:
@@ -221,6 +243,36 @@ def lrbms_step(ctx, sim_ids, n_steps: int = 1, wait: bool = True):
     status = np.zeros(len(ids), dtype=np.int32) if wait else None
     _check(ctx, library().lrbms_step(ctx, len(ids), _ptr(ids), n_steps, _ptr(status)))
     return status
+
+
+N_PHASES = 8
+PHASES = ["fit", "assemble", "solve", "reconstruct", "flux", "cfl", "transport", "finalize"]
+
+
+def lrbms_step_io(ctx, sim_ids, n_steps: int, s_in=None, s_out=None):
+    """Step with the saturation exchanged with caller memory: s_in / s_out are
+    lists of pinned host (or device) buffers, one per simulation."""
+    ids = np.ascontiguousarray(sim_ids, dtype=np.int32)
+    n = len(ids)
+    pin = (C.c_void_p * n)(*[_ptr(a) for a in s_in]) if s_in is not None else None
+    pout = (C.c_void_p * n)(*[_ptr(a) for a in s_out]) if s_out is not None else None
+    status = np.zeros(n, dtype=np.int32)
+    _check(ctx, library().lrbms_step_io(ctx, n, _ptr(ids), n_steps, pin, pout, _ptr(status)))
+    return status
+
+
+def lrbms_profile_start(ctx, max_steps: int):
+    _check(ctx, library().lrbms_profile_start(ctx, max_steps))
+
+
+def lrbms_profile_read(ctx, max_steps: int):
+    """Returns (mean ms per phase [N_PHASES], ms per recorded step)."""
+    ph = np.zeros(N_PHASES)
+    st = np.zeros(max(max_steps, 1))
+    n = C.c_int()
+    _check(ctx, library().lrbms_profile_read(ctx, ph.ctypes.data_as(C.POINTER(C.c_double)),
+                                             st.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n)))
+    return ph, st[: n.value]
 
 
 def lrbms_run(ctx, sim_id: int, n_steps: int, s_out=None, p_out=None, flux_out=None):

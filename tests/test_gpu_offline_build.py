@@ -95,3 +95,41 @@ def test_builder_rejects_unreachable_basis_size(L):
         L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 1)
     assert ei.value.code == L.LRBMS_E_FORMAT
     L.lrbms_destroy(ctx)
+
+
+def test_clone_rotated_matches_source(L):
+    prob, m, co, NE, mus = _setup()
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=4)
+    opts = dict(M=prob.M, n_steps_T=prob.n_steps, N_E=NE, mu=mus, c_pen=m.c_pen)
+    (src,) = L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 1)
+    rng = np.random.default_rng(5)
+    Q = np.concatenate([random_orthogonal(int(n), rng).reshape(-1) for n in NE])
+    cp = L.lrbms_clone(ctx, src, Q)
+    plain = L.lrbms_clone(ctx, src, None)
+    assert list(L.lrbms_step(ctx, [src, cp, plain], 6)) == [0, 0, 0]
+    a, b, c = (L.lrbms_get_field(ctx, i, L.FIELD_S) for i in (src, cp, plain))
+    assert rel(b, a) < 1e-10
+    assert np.array_equal(c, a)
+    L.lrbms_destroy(ctx)
+
+
+def test_step_io_and_profiling(L):
+    """Saturation exchange with pinned host memory gives the same steps as
+    lrbms_step; the profiler records every phase of every step."""
+    import torch
+    prob, m, co, NE, mus = _setup()
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=4)
+    opts = dict(M=prob.M, n_steps_T=prob.n_steps, N_E=NE, mu=mus, c_pen=m.c_pen)
+    ids = L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 2)
+    L.lrbms_profile_start(ctx, 3)
+    L.lrbms_step(ctx, [ids[0]], 3)
+    ph, st = L.lrbms_profile_read(ctx, 3)
+    assert len(st) == 3 and np.all(ph > 0) and abs(st.sum() / 3 - ph.sum()) < 0.05 * st.mean() + 1e-3
+    s_in = torch.from_numpy(L.lrbms_get_field(ctx, ids[0], L.FIELD_S)).pin_memory()
+    s_out = torch.empty_like(s_in).pin_memory()
+    L.lrbms_set_saturation(ctx, ids[1], prob.s0 + 0.5)  # overwritten by s_in below
+    L.lrbms_step(ctx, [ids[0]], 1)
+    st = L.lrbms_step_io(ctx, [ids[1]], 1, [s_in], [s_out])
+    assert st[0] == 0
+    assert np.array_equal(s_out.numpy(), L.lrbms_get_field(ctx, ids[0], L.FIELD_S))
+    L.lrbms_destroy(ctx)

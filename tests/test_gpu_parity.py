@@ -63,9 +63,13 @@ def _compare_step(L, ctx, sid, c, s, ref=None):
     return ref
 
 
-def test_single_step_every_field(L):
+SOLVERS = [0, 1]  # FP64 block Cholesky; FP32 block Cholesky with FP64 refinement
+
+
+@pytest.mark.parametrize("solver", SOLVERS, ids=["fp64-solve", "mixed-solve"])
+def test_single_step_every_field(L, solver):
     c = case("small")
-    ctx = _ctx(L)
+    ctx = _ctx(L, solver=solver)
     sid = _load(L, ctx, c)
     st = L.lrbms_step(ctx, [sid], 1)
     assert st[0] == 0
@@ -73,11 +77,12 @@ def test_single_step_every_field(L):
     L.lrbms_destroy(ctx)
 
 
-def test_trajectory_and_mass_balance(L):
+@pytest.mark.parametrize("solver", SOLVERS, ids=["fp64-solve", "mixed-solve"])
+def test_trajectory_and_mass_balance(L, solver):
     """Whole 50-step trajectory of the 32x32 / 4x4 case; the cumulative
     boundary outflow equals the loss of water volume to FP64 round-off."""
     prob, m, co, off = c = case("small")
-    ctx = _ctx(L)
+    ctx = _ctx(L, solver=solver)
     sid = _load(L, ctx, c)
     s = prob.s0.copy()
     t = 0.0
@@ -126,13 +131,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("solver", SOLVERS, ids=["fp64-solve", "mixed-solve"])
 @pytest.mark.parametrize("label,kw", CASES, ids=[c[0] for c in CASES])
-def test_cases_three_steps(L, label, kw):
+def test_cases_three_steps(L, label, kw, solver):
     """Three steps, each started from the oracle's own state (so every
     step is compared on identical inputs)."""
     c = case(**kw)
     prob, m, co, off = c
-    ctx = _ctx(L)
+    ctx = _ctx(L, solver=solver)
     sid = _load(L, ctx, c)
     s = prob.s0.copy()
     for _ in range(3):
@@ -158,19 +164,20 @@ def test_dense_profiles_and_fixed_dt(L):
     L.lrbms_destroy(ctx)
 
 
-def test_batch_equals_alone_bitwise(L):
+@pytest.mark.parametrize("solver", SOLVERS, ids=["fp64-solve", "mixed-solve"])
+def test_batch_equals_alone_bitwise(L, solver):
     """Simulations of different shapes and basis sizes stepped in one launch
     give bitwise the same results as each stepped alone."""
     cs = [case("small"), case("rect", kind="snapshots", n=(72, 40), S=(6, 4)),
           case("paper_bc", p_inflow=0.0), case("small", kind="snapshots")]
-    ctx = _ctx(L)
+    ctx = _ctx(L, solver=solver)
     ids = [_load(L, ctx, c) for c in cs]
     st = L.lrbms_step(ctx, ids, 5)
     assert list(st) == [0] * len(cs)
     mixed = [L.lrbms_get_field(ctx, i, L.FIELD_S) for i in ids]
     L.lrbms_destroy(ctx)
     for c, sm in zip(cs, mixed):
-        ctx = _ctx(L)
+        ctx = _ctx(L, solver=solver)
         sid = _load(L, ctx, c)
         assert L.lrbms_step(ctx, [sid], 5)[0] == 0
         alone = L.lrbms_get_field(ctx, sid, L.FIELD_S)
