@@ -259,6 +259,32 @@ int lrbms_profile_start(lrbms_ctx* ctx, int max_steps);
  * (step_ms[max_steps]); *n_recorded receives the number of steps recorded. */
 int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n_recorded);
 
+/* Solve one reduced system (c + sum_q theta_q b_q) x = rhs, already
+ * assembled, without allocating anything. The paper has no counterpart: it is
+ * for callers that cannot call cudaMalloc, for example a host process whose
+ * device memory belongs to another allocator, or a time-critical loop in
+ * which the synchronisation and possible failure of an allocation are not
+ * allowed. No context is needed and nothing is allocated on the host or the
+ * device; all working memory (factor panels, diagonal inverses, work vectors,
+ * offset tables) is a fixed 32 MiB array in device memory that every GPU
+ * loading the library holds until the process exits.
+ *   Sx, Sy  coarse grid; N_E [Sx*Sy] local basis sizes (host memory, 1..64)
+ *   A       device, assembled blocks in the layout of LRBMS_FIELD_A
+ *           (per subdomain [N_E][N_E], then per coarse face [N_E-][N_E+])
+ *   rhs     device, [N]; x: device, [N] output
+ *   solver  LRBMS_SOLVE_FP64 or LRBMS_SOLVE_MIXED; refine_iters as in
+ *           lrbms_config (0: default)
+ *   stream  cudaStream_t (NULL: the legacy default stream)
+ * Returns LRBMS_E_BUDGET if the system needs more than the 32 MiB array,
+ * LRBMS_E_NOT_SPD if a pivot is not positive, LRBMS_E_ARG on bad arguments.
+ * The call waits for the stream. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. Every call uses the same
+ * array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
+int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double* A, const double* rhs,
+                        double* x, int solver, int refine_iters, void* stream);
+
 /* Wait for all enqueued work. */
 int lrbms_sync(lrbms_ctx* ctx);
 

@@ -21,11 +21,6 @@ namespace lrbms {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // theta = G^+ (sum over tiles of the fit partials), by warp 0; w[0] = 1.
 __device__ void compute_weights(const SimDev& S, double* w, double* rsh, bool store) {
   const int M = S.M;
@@ -386,6 +381,57 @@ __global__ void k_chol_solve(const SimDev* __restrict__ sims, const int* __restr
   solve_refine<double>(S, S.L, S.Linv, mode == 1 ? iters : iters, sm);
 }
 
+// ---------------------------------------------------------------- static scratch
+// Reduced solve for callers that must not allocate device memory: the factor
+// panels, diagonal inverses, work vectors and offset tables live in this
+// file-scope array, which every GPU that loads the library holds until exit.
+constexpr size_t kNoAllocBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Offset tables from the basis sizes (one thread; n_sub is modest).
+__global__ void k_noalloc_tables(SimDev S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int* NE = const_cast<int*>(S.NE);
+  int* xoff = const_cast<int*>(S.xoff);
+  long long* aoff = const_cast<long long*>(S.aoff);
+  long long* loff = const_cast<long long*>(S.loff);
+  long long* ioff = const_cast<long long*>(S.ioff);
+  xoff[0] = 0;
+  for (int E = 0; E < S.n_sub; ++E) xoff[E + 1] = xoff[E] + NE[E];
+  aoff[0] = 0;
+  for (int E = 0; E < S.n_sub; ++E) aoff[E + 1] = aoff[E] + (long long)NE[E] * NE[E];
+  int b = S.n_sub;
+  for (int J = 0; J < S.Sy; ++J)
+    for (int I = 0; I + 1 < S.Sx; ++I, ++b) aoff[b + 1] = aoff[b] + (long long)NE[J * S.Sx + I] * NE[J * S.Sx + I + 1];
+  for (int J = 0; J + 1 < S.Sy; ++J)
+    for (int I = 0; I < S.Sx; ++I, ++b) aoff[b + 1] = aoff[b] + (long long)NE[J * S.Sx + I] * NE[(J + 1) * S.Sx + I];
+  loff[0] = 0;
+  ioff[0] = 0;
+  for (int k = 0; k < S.n_sub; ++k) {
+    loff[k + 1] = loff[k] + (long long)NE[k] * (xoff[k + 1] - xoff[jlo_of(k, S.Sx)]);
+    ioff[k + 1] = ioff[k] + (long long)NE[k] * NE[k];
+  }
+  S.status[0] = kStOk;
+}
+
+__global__ void k_chol_solve_static(SimDev S, int mode, int iters) {
+  extern __shared__ double sm[];
+  if (mode == 1) {
+    float* Lf = reinterpret_cast<float*>(S.L);
+    float* Lif = reinterpret_cast<float*>(S.Linv);
+    if (factor<float>(S, Lf, Lif, reinterpret_cast<float*>(sm))) {
+      solve_refine<float>(S, Lf, Lif, iters, reinterpret_cast<float*>(sm));
+      return;
+    }
+    __syncthreads();
+  }
+  if (!factor<double>(S, S.L, S.Linv, sm)) {
+    if (threadIdx.x == 0) S.status[0] = kStNotSpd;
+    return;
+  }
+  solve_refine<double>(S, S.L, S.Linv, iters, sm);
+}
+
 }  // namespace
 
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
@@ -403,3 +449,82 @@ void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int 
 }
 
 }  // namespace lrbms
+
+// ---------------------------------------------------------------- C ABI
+#include "lrbms.h"
+
+namespace {
+constexpr int kMaxDevices = 64;
+unsigned char* g_noalloc_dev[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double* A, const double* rhs,
+                                   double* x, int solver, int refine_iters, void* stream) {
+  using namespace lrbms;
+  if (Sx < 1 || Sy < 1 || !N_E || !A || !rhs || !x || refine_iters < 0 || refine_iters > 16 ||
+      (solver != LRBMS_SOLVE_FP64 && solver != LRBMS_SOLVE_MIXED))
+    return LRBMS_E_ARG;
+  const int n_sub = Sx * Sy;
+  const int n_cf = Sy * (Sx - 1) + (Sy - 1) * Sx;
+  // sizes from the caller's (host) basis sizes; no host or device allocation
+  long long N = 0, l_tot = 0, i_tot = 0;
+  for (int E = 0; E < n_sub; ++E) {
+    if (N_E[E] < 1 || N_E[E] > 64) return LRBMS_E_ARG;
+    N += N_E[E];
+    i_tot += (long long)N_E[E] * N_E[E];
+  }
+  {
+    long long x0 = 0;  // running prefix for the envelope widths
+    for (int k = 0; k < n_sub; ++k) {
+      const int jl = jlo_of(k, Sx);
+      long long base = 0;
+      for (int j = 0; j < jl; ++j) base += N_E[j];
+      x0 += N_E[k];
+      l_tot += (long long)N_E[k] * (x0 - base);
+    }
+  }
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  size_t off = 0;
+  const size_t o_NE = off; off = up(off + 4 * (size_t)n_sub);
+  const size_t o_xoff = off; off = up(off + 4 * (size_t)(n_sub + 1));
+  const size_t o_aoff = off; off = up(off + 8 * (size_t)(n_sub + n_cf + 1));
+  const size_t o_loff = off; off = up(off + 8 * (size_t)(n_sub + 1));
+  const size_t o_ioff = off; off = up(off + 8 * (size_t)(n_sub + 1));
+  const size_t o_status = off; off = up(off + 4);
+  const size_t o_L = off; off = up(off + 8 * (size_t)l_tot);
+  const size_t o_Li = off; off = up(off + 8 * (size_t)i_tot);
+  const size_t o_y = off; off = up(off + 16 * (size_t)N);
+  const size_t o_rv = off; off = up(off + 8 * (size_t)N);
+  const size_t o_dv = off; off = up(off + 8 * (size_t)N);
+  if (off > kNoAllocBytes) return LRBMS_E_BUDGET;  // system larger than the static scratch
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LRBMS_E_CUDA;
+  if (!g_noalloc_dev[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LRBMS_E_CUDA;
+    g_noalloc_dev[dev] = static_cast<unsigned char*>(ptr);
+  }
+  unsigned char* base = g_noalloc_dev[dev];
+  cudaStream_t st = (cudaStream_t)stream;
+  SimDev S{};
+  S.Sx = Sx; S.Sy = Sy; S.n_sub = n_sub; S.n_cf = n_cf; S.n_blocks = n_sub + n_cf; S.N = (int)N;
+  S.NE = (const int*)(base + o_NE); S.xoff = (const int*)(base + o_xoff);
+  S.aoff = (const long long*)(base + o_aoff); S.loff = (const long long*)(base + o_loff);
+  S.ioff = (const long long*)(base + o_ioff); S.status = (int*)(base + o_status);
+  S.L = (double*)(base + o_L); S.Linv = (double*)(base + o_Li); S.y = (double*)(base + o_y);
+  S.rv = (double*)(base + o_rv); S.dv = (double*)(base + o_dv);
+  S.A = const_cast<double*>(A); S.b = const_cast<double*>(rhs); S.x = x;
+  if (cudaMemcpyAsync(base + o_NE, N_E, 4 * (size_t)n_sub, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return LRBMS_E_CUDA;
+  k_noalloc_tables<<<1, 1, 0, st>>>(S);
+  const int mode = solver == LRBMS_SOLVE_MIXED ? 1 : 0;
+  const int iters = refine_iters > 0 ? refine_iters : (mode == 1 ? 4 : 1);
+  k_chol_solve_static<<<1, 256, 64 * 64 * sizeof(double), st>>>(S, mode, iters);
+  if (cudaGetLastError() != cudaSuccess) return LRBMS_E_CUDA;
+  int status = 0;
+  if (cudaMemcpyAsync(&status, base + o_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return LRBMS_E_CUDA;
+  return status == 0 ? LRBMS_OK : LRBMS_E_NOT_SPD;
+}

@@ -38,7 +38,7 @@ FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT
 EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offline_build",
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
-            "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count",
+            "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count", "lrbms_solve_noalloc",
             "lrbms_last_error"]
 
 
@@ -93,6 +93,7 @@ def library() -> C.CDLL:
         lib.lrbms_offline_build.argtypes = [vp, i, C.POINTER(Problem), C.POINTER(BuildOpts), i,
                                             C.POINTER(vp), C.POINTER(i), C.POINTER(i)]
         lib.lrbms_clone.argtypes = [vp, i, vp, C.POINTER(i)]
+        lib.lrbms_solve_noalloc.argtypes = [i, i, vp, vp, vp, vp, i, i, vp]
         lib.lrbms_step_io.argtypes = [vp, i, vp, i, C.POINTER(vp), C.POINTER(vp), vp]
         lib.lrbms_profile_start.argtypes = [vp, i]
         lib.lrbms_profile_read.argtypes = [vp, dp, dp, C.POINTER(i)]
@@ -301,6 +302,15 @@ def lrbms_get_field(ctx, sim_id: int, field: int, dtype=np.float64):
     out = np.empty(nb // np.dtype(dtype).itemsize, dtype=dtype)
     _check(ctx, library().lrbms_get_field(ctx, sim_id, field, _ptr(out), nb))
     return out
+
+
+def lrbms_solve_noalloc(Sx: int, Sy: int, N_E, A, rhs, x, solver=LRBMS_SOLVE_FP64, refine_iters=0,
+                        stream=None) -> int:
+    """Solve an assembled reduced system with no allocation (A, rhs, x:
+    device arrays with data_ptr(); N_E: host int32). Returns the status code."""
+    ne = np.ascontiguousarray(N_E, dtype=np.int32)
+    return int(library().lrbms_solve_noalloc(Sx, Sy, _ptr(ne), _ptr(A), _ptr(rhs), _ptr(x), solver,
+                                             refine_iters, stream))
 
 
 def lrbms_sync(ctx):
