@@ -123,7 +123,7 @@ typedef struct {
  * hand side); q = 1..M hold b_q and d_q. */
 typedef struct {
   int M;
-  const int* N_E;          /* [Sx*Sy] local basis sizes (>= 1)               */
+  const int* N_E;          /* [Sx*Sy] local basis sizes, 1..32               */
   const uint8_t* prof_idx; /* [nx*ny] first profile index q (2..M) whose value
                               is lambda(1) (profiles of Algorithm 2, step 1(c)),
                               or NULL                                       */
@@ -268,7 +268,7 @@ int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n
  * device; all working memory (factor panels, diagonal inverses, work vectors,
  * offset tables) is a fixed 32 MiB array in device memory that every GPU
  * loading the library holds until the process exits.
- *   Sx, Sy  coarse grid; N_E [Sx*Sy] local basis sizes (host memory, 1..64)
+ *   Sx, Sy  coarse grid; N_E [Sx*Sy] local basis sizes (host memory, 1..32)
  *   A       device, assembled blocks in the layout of LRBMS_FIELD_A
  *           (per subdomain [N_E][N_E], then per coarse face [N_E-][N_E+])
  *   rhs     device, [N]; x: device, [N] output

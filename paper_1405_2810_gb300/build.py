@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrbms.so")
-SOURCES = ["lrbms_api.cu", "kernels_cell.cu", "kernels_solve.cu", "offline_build.cu"]
+SOURCES = ["lrbms_api.cu", "kernels_cell.cu", "kernels_solve.cu", "kernels_fine.cu", "offline_build.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -4,7 +4,7 @@
 //   fixed-order sum of the fit partials), then every block
 //   A_b = c_b + sum_q theta_q (b_q)_b and every subdomain right-hand side
 //   b_E = e_E + sum_q theta_q (d_q)_E, streamed from the component arrays.
-// chol_solve: one CTA per simulation. The matrix is symmetric positive
+// chol_solve: one warp per simulation. The matrix is symmetric positive
 //   definite with a 5-point block pattern over the Sx x Sy subdomains; in
 //   lexicographic subdomain order its Cholesky factor lives in the envelope
 //   j in [k - Sx, k] of every block row k. Block row k of L is kept as a dense
@@ -105,280 +105,733 @@ __global__ void k_assemble32(const SimDev* __restrict__ sims, const int* __restr
   }
 }
 
-// Index of the assembled coupling block between subdomain k and its left
-// (dir 0) or lower (dir 1) neighbour; -1 if none.
-__device__ __forceinline__ int coupling_block(const SimDev& S, int k, int dir) {
-  const int I = k % S.Sx, J = k / S.Sx;
-  if (dir == 0) return I > 0 ? S.n_sub + J * (S.Sx - 1) + (I - 1) : -1;
-  return J > 0 ? S.n_sub + S.Sy * (S.Sx - 1) + (J - 1) * S.Sx + I : -1;
+// ---------------------------------------------------------------- bulk-copy ring
+// Chunks of the factor (a block of a panel, or a diagonal inverse) are copied
+// from global to shared memory by cp.async.bulk, each completing on the
+// mbarrier of its slot; the copies of the next chunks run while the warp
+// computes on the current one. Every wait is bounded.
+constexpr int kRing = 4;                     // slots of the factorisation ring
+constexpr int kSlot = kMaxNE * kMaxNE + 8;   // elements per slot: one 32 x 32 block + alignment slack
+constexpr int kMaxSlots = 32;                // mbarriers per warp
+constexpr long long kWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-// ... and with its right (dir 2) or upper (dir 3) neighbour.
-__device__ __forceinline__ int coupling_block_up(const SimDev& S, int k, int dir) {
-  const int I = k % S.Sx, J = k / S.Sx;
-  if (dir == 2) return I < S.Sx - 1 ? S.n_sub + J * (S.Sx - 1) + I : -1;
-  return J < S.Sy - 1 ? S.n_sub + S.Sy * (S.Sx - 1) + J * S.Sx + I : -1;
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (int it = 0; it < (1 << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > kWaitCycles) break;
+  }
+  return false;
 }
 
-// Sum over a group of G lanes (G a power of two dividing 32, groups aligned
-// inside warps); every lane of the warp must call it.
+// Warp-uniform ring state: slot n of the stream lives in slot n % nslot and
+// completes on barrier n % nslot; ph holds the parity awaited next on each barrier.
 template <typename T>
-__device__ __forceinline__ T group_sum(T v, int G) {
-  for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+struct Ring {
+  T* base;
+  uint64_t* bar;
+  int* dl;  // per slot: element offset of the chunk within its aligned copy
+  int nslot;
+  unsigned issued, consumed;
+  unsigned ph;
+  bool ok;
+};
+
+// Issue the copy of `count` elements starting at element `off` of `src`
+// (src 16-byte aligned): the copy starts at the 16-byte boundary at or below
+// `off` and its size is rounded up to 16 bytes.
+template <typename T>
+__device__ __forceinline__ void ring_issue(Ring<T>& r, const T* src, long long off, int count, int lane) {
+  constexpr int kA = 16 / (int)sizeof(T);
+  const int d = (int)(off & (kA - 1));
+  const uint32_t bytes = (uint32_t)(((d + count) * (int)sizeof(T) + 15) & ~15);
+  const int s = (int)(r.issued % (unsigned)r.nslot);
+  if (lane == 0) {
+    r.dl[s] = d;  // published to the waiting lanes by the arrive (release) below
+    mbar_expect_tx(&r.bar[s], bytes);
+    bulk_g2s(r.base + (size_t)s * kSlot, src + (off - d), bytes, &r.bar[s]);
+  }
+  ++r.issued;
 }
 
-// Envelope block Cholesky of the assembled A (FP64) with factor storage T.
-// Returns false if a pivot is not positive (or not finite).
+// Wait for the next chunk; returns its first element (slot + alignment offset).
 template <typename T>
-__device__ bool factor(const SimDev& S, T* Lst, T* Linv, T* tmp) {
+__device__ __forceinline__ const T* ring_wait(Ring<T>& r) {
+  const int s = (int)(r.consumed % (unsigned)r.nslot);
+  if (!mbar_wait(&r.bar[s], (r.ph >> s) & 1u)) r.ok = false;
+  r.ph ^= 1u << s;
+  return r.base + (size_t)s * kSlot + r.dl[s];
+}
+
+__device__ __forceinline__ void ring_release_sync() { __syncwarp(); }
+
+// Bounded wait for every copy still in flight (error paths).
+template <typename T>
+__device__ void ring_drain(Ring<T>& r) {
+  while (r.consumed < r.issued) {
+    const int s = (int)(r.consumed % (unsigned)r.nslot);
+    mbar_wait(&r.bar[s], (r.ph >> s) & 1u);
+    r.ph ^= 1u << s;
+    ++r.consumed;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- per-warp shared memory
+struct SolveMeta {
+  int* NE;
+  int* xoff;
+  long long* loff;
+  long long* ioff;
+};
+
+__host__ __device__ inline size_t meta_bytes(int n_sub) {
+  return ((size_t)4 * (2 * n_sub + 1) + 15) / 16 * 16 + (size_t)16 * (n_sub + 1);
+}
+__host__ __device__ inline size_t round4(size_t v) { return (v + 3) & ~(size_t)3; }
+// Offset tables, mbarriers and slot offsets, the panel R of the current block
+// row (padded columns), the factorisation ring, the substitution vectors [2N]
+// and [32].
+__host__ __device__ inline size_t warp_smem_bytes(int n_sub, int panel_words, int N, size_t elem) {
+  return meta_bytes(n_sub) + 12 * kMaxSlots +
+         elem * (round4(panel_words) + (size_t)kRing * kSlot + round4(2 * (size_t)N) + 32);
+}
+
+template <typename T>
+struct WarpSmem {
+  SolveMeta mt;
+  uint64_t* bar;
+  int* dl;   // [kMaxSlots]
+  T* R;      // [panel_words]
+  T* ring;   // [kRing][kSlot]
+  T* yz;     // [2N]
+  T* tv;     // [32]
+  int n_sub_slots;  // slots of the substitution ring, which spans R and the factor ring
+  unsigned ph;      // parity awaited next on each mbarrier
+};
+
+template <typename T>
+__device__ WarpSmem<T> warp_carve_and_load(const SimDev& S, unsigned char* b, int lane) {
+  WarpSmem<T> m;
+  const int ns = S.n_sub;
+  m.mt.NE = reinterpret_cast<int*>(b);
+  m.mt.xoff = m.mt.NE + ns;
+  const size_t o = ((size_t)4 * (2 * ns + 1) + 15) / 16 * 16;
+  m.mt.loff = reinterpret_cast<long long*>(b + o);
+  m.mt.ioff = m.mt.loff + (ns + 1);
+  m.bar = reinterpret_cast<uint64_t*>(b + meta_bytes(ns));
+  m.dl = reinterpret_cast<int*>(b + meta_bytes(ns) + 8 * kMaxSlots);
+  T* t = reinterpret_cast<T*>(b + meta_bytes(ns) + 12 * kMaxSlots);
+  const size_t rw = round4((size_t)S.panel_words);
+  m.R = t;
+  m.ring = t + rw;
+  m.yz = m.ring + (size_t)kRing * kSlot;
+  m.tv = m.yz + round4(2 * (size_t)S.N);
+  const size_t nss = (rw + (size_t)kRing * kSlot) / kSlot;
+  m.n_sub_slots = nss > (size_t)kMaxSlots ? kMaxSlots : (int)nss;
+  m.ph = 0;
+  for (int i = lane; i < ns; i += 32) m.mt.NE[i] = S.NE[i];
+  for (int i = lane; i <= ns; i += 32) {
+    m.mt.xoff[i] = S.xoff[i];
+    m.mt.loff[i] = S.loff[i];
+    m.mt.ioff[i] = S.ioff[i];
+  }
+  if (lane == 0) {
+    for (int i = 0; i < kMaxSlots; ++i) mbar_init(&m.bar[i], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  return m;
+}
+
+// Invalidate the mbarriers (before the shared memory is carved again).
+__device__ void warp_release_barriers(uint64_t* bar, int lane) {
+  __syncwarp();
+  if (lane == 0)
+    for (int i = 0; i < kMaxSlots; ++i) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[i])) : "memory");
+  __syncwarp();
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float vget(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+// Padded width of block row k in R: sum over its envelope of round4(N_i).
+__device__ __forceinline__ int padded_width(const SolveMeta& mt, int jl, int k) {
+  int w = 0;
+  for (int i = jl; i <= k; ++i) w += (mt.NE[i] + 3) & ~3;
+  return w;
+}
+// Row stride of R for padded width Wc: 16-byte aligned rows whose starts fall
+// on 16 (mod 32) bytes when Wc * sizeof(T) is a multiple of 32, so that a
+// column read by lanes over rows spreads over 8 bank groups.
+template <typename T>
+__device__ __forceinline__ int row_stride(int Wc) {
+  return ((Wc * (int)sizeof(T)) & 31) == 0 ? Wc + 16 / (int)sizeof(T) : Wc;
+}
+
+// Row-GEMM on one warp, lane = output column c (< ncols):
+//   C[r][c] (SET: =, else -=) sum_{t < 4 NV} A[r][t] B[t][c],  r < nrows,
+// A rows in shared memory (16-byte aligned, zero beyond the true inner size),
+// B element (t, c) at Bp[t * bst + c * bsc] for t < nt (zero for t >= nt).
+// Four rows per pass for independent accumulation chains; in SET mode C may
+// alias A (every row is read by all lanes before it is written).
+template <typename T, int NV, bool SET>
+__device__ __forceinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* C, int ldc, int nrows, const T* Bp,
+                                           int bst, int bsc, int nt, int ncols, int lane) {
+  using V = typename Vec16<T>::type;
+  constexpr int kV = Vec16<T>::n;
+  constexpr int NT = 4 * NV;
+  T b[NT];
+  const bool act = lane < ncols;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) b[t] = (act && t < nt) ? Bp[t * bst + lane * bsc] : T(0);
+  int r = 0;
+  for (; r + 3 < nrows; r += 4) {
+    T acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = T(0);
+#pragma unroll
+    for (int v = 0; v < NT / kV; ++v) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const V x = reinterpret_cast<const V*>(A + (r + i) * lda)[v];
+#pragma unroll
+        for (int e = 0; e < kV; ++e) acc[i][e & 1] = fma(vget(x, e), b[v * kV + e], acc[i][e & 1]);
+      }
+    }
+    if (SET) __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (SET) C[(r + i) * ldc + lane] = acc[i][0] + acc[i][1];
+        else C[(r + i) * ldc + lane] -= acc[i][0] + acc[i][1];
+      }
+    }
+  }
+  for (; r < nrows; ++r) {
+    T a0 = T(0), a1 = T(0);
+#pragma unroll
+    for (int v = 0; v < NT / kV; ++v) {
+      const V x = reinterpret_cast<const V*>(A + r * lda)[v];
+#pragma unroll
+      for (int e = 0; e < kV; ++e) {
+        if (e & 1) a1 = fma(vget(x, e), b[v * kV + e], a1);
+        else a0 = fma(vget(x, e), b[v * kV + e], a0);
+      }
+    }
+    if (SET) __syncwarp();
+    if (act) {
+      if (SET) C[r * ldc + lane] = a0 + a1;
+      else C[r * ldc + lane] -= a0 + a1;
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, bool SET>
+__device__ __forceinline__ void rowgemm(const T* A, int lda, T* C, int ldc, int nrows, const T* Bp, int bst,
+                                        int bsc, int nt, int ncols, int lane) {
+  switch ((nt + 3) >> 2) {
+    case 1: rowgemm_nv<T, 1, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 2: rowgemm_nv<T, 2, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 3: rowgemm_nv<T, 3, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 4: rowgemm_nv<T, 4, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 5: rowgemm_nv<T, 5, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 6: rowgemm_nv<T, 6, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 7: rowgemm_nv<T, 7, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    default: rowgemm_nv<T, 8, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+  }
+}
+
+// Chunk sequence of the factorisation of block row k: for every j in
+// [jlo_k, k): the transposed inverse of L_jj, then L_{j'j} for j' in (j, k)
+// (rows of the transposed panel j' at the columns of block j).
+struct FactorSeq {
+  int k, j, jp;
+  __device__ bool done() const { return j >= k; }
+  __device__ void next() {
+    if (++jp >= k) {
+      ++j;
+      jp = j;
+    }
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void factor_issue(Ring<T>& r, FactorSeq& q, const SolveMeta& mt, int Sx, const T* LT,
+                                             const T* Linv, int lane) {
+  const int Nj = mt.NE[q.j];
+  if (q.jp == q.j) {
+    ring_issue<T>(r, Linv, mt.ioff[q.j] + ((Nj * Nj + 3) & ~3), Nj * Nj, lane);
+  } else {
+    const int Njp = mt.NE[q.jp];
+    const long long off = mt.loff[q.jp] + (long long)(mt.xoff[q.j] - mt.xoff[jlo_of(q.jp, Sx)]) * Njp;
+    ring_issue<T>(r, LT, off, Nj * Njp, lane);
+  }
+  q.next();
+}
+
+// Envelope block Cholesky of the assembled A (FP64) with factor storage T, by
+// one warp. Block row k is formed in R and processed right-looking within the
+// row: for each block j of the envelope, X_j = R_j L_jj^-T is finalised (and
+// stored as L_kj), then every later block j' of the row, the diagonal one
+// included, is updated, R_j' -= X_j L_{j'j}^T (lane = column of j'; for the
+// diagonal block L_kj = X_j). L_kk = chol(R_kk) and its inverse are computed
+// in registers (lane = row). Panels are stored transposed, LT_k [W_k][N_k];
+// inverses [N_k][N_k]. Returns kFacOk, kFacPivot on a non-positive (or
+// non-finite) pivot, or kFacTimeout if a copy did not complete.
+constexpr int kFacOk = 0, kFacPivot = 1, kFacTimeout = 2;
+
+template <typename T>
+__device__ int wfactor(const SimDev& S, T* LT, T* Linv, WarpSmem<T>& m, int lane) {
+  using V = typename Vec16<T>::type;
+  constexpr int kV = Vec16<T>::n;
+  const SolveMeta& mt = m.mt;
   const int nsub = S.n_sub, Sx = S.Sx;
-  __shared__ int bad;
-  __shared__ T dsh;
-  if (threadIdx.x == 0) bad = 0;
+  const unsigned full = 0xffffffffu;
+  T* R = m.R;
+  Ring<T> rg{m.ring, m.bar, m.dl, kRing, 0u, 0u, m.ph, true};
+  bool badp = false;
   for (int k = 0; k < nsub; ++k) {
     const int jl = jlo_of(k, Sx);
-    const int base = S.xoff[jl];
-    const int W = S.xoff[k + 1] - base;
-    const int Nk = S.NE[k];
-    T* R = Lst + S.loff[k];
-    for (int i = threadIdx.x; i < Nk * W; i += blockDim.x) R[i] = T(0);
-    __syncthreads();
-    {
-      const double* Akk = S.A + S.aoff[k];
-      const int cd = S.xoff[k] - base;
-      for (int i = threadIdx.x; i < Nk * Nk; i += blockDim.x) {
-        const int r = i / Nk, c = i - r * Nk;
-        R[r * W + cd + c] = (T)Akk[i];
-      }
-      for (int dir = 0; dir < 2; ++dir) {
-        const int bblk = coupling_block(S, k, dir);
-        if (bblk < 0) continue;
-        const int j = dir == 0 ? k - 1 : k - Sx;
-        const int Nj = S.NE[j];
-        const double* Ab = S.A + S.aoff[bblk];  // [N_j][N_k] = A_{j,k}
-        const int cj = S.xoff[j] - base;
-        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
-          const int r = i / Nj, c = i - r * Nj;  // A_{k,j}[r][c] = A_{j,k}[c][r]
-          R[r * W + cj + c] = (T)Ab[c * Nk + r];
-        }
-      }
-    }
-    __syncthreads();
-    for (int j = jl; j <= k; ++j) {
-      const int Nj = S.NE[j];
-      const int c0 = S.xoff[j] - base;
-      const int jlj = jlo_of(j, Sx);
-      const int Wj = S.xoff[j + 1] - S.xoff[jlj];
-      const T* Lj = Lst + S.loff[j];
-      const int offj = base - S.xoff[jlj];
-      const int len = c0;
-      if (len > 0) {
-        // R[:, c0:c0+Nj] -= R[:, 0:len] L_j[:, offj:offj+len]^T, each output a
-        // dot product split over a group of G lanes when outputs are few
-        const int n_out = Nk * Nj;
-        int G = 1;
-        while (G < 32 && 2 * G * n_out <= (int)blockDim.x && G < len) G *= 2;
-        const int lg = threadIdx.x & (G - 1), grp = threadIdx.x / G, n_grp = blockDim.x / G;
-        for (int o0 = 0; o0 < n_out; o0 += n_grp) {
-          const int o = o0 + grp;
-          const int r = o / Nj, c = o - r * Nj;
-          const bool live = o < n_out && !(j == k && c > r);
-          T acc = T(0);
-          if (live) {
-            const T* a = R + (size_t)r * W;
-            const T* bb = Lj + (size_t)c * Wj + offj;
-            for (int t = lg; t < len; t += G) acc = fma(a[t], bb[t], acc);
+    const int base = mt.xoff[jl];
+    const int Nk = mt.NE[k];
+    const int Wc = padded_width(mt, jl, k);
+    const int Wp = row_stride<T>(Wc);
+    const int pck = Wc - ((Nk + 3) & ~3);
+    // every chunk of this row refers to rows written before it
+    FactorSeq q{k, jl, jl};
+    while (!q.done() && (int)(rg.issued - rg.consumed) < rg.nslot) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+    {  // R <- assembled blocks of A (diagonal, left, lower), zero elsewhere and in the padding
+      const int I = k % Sx, J = k / Sx;
+      int pc = 0;
+      for (int i = jl; i <= k; ++i) {
+        const int Ni = mt.NE[i], Np = (Ni + 3) & ~3;
+        const double* blk = nullptr;
+        if (i == k) blk = S.A + S.aoff[k];
+        else if (I > 0 && i == k - 1) blk = S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)];        // [N_i][N_k]
+        else if (J > 0 && i == k - Sx) blk = S.A + S.aoff[nsub + S.Sy * (Sx - 1) + (J - 1) * Sx + I];  // [N_i][N_k]
+        if (i == k) {  // lanes over columns, 8 rows of loads in flight
+          for (int r0 = 0; r0 < Nk; r0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (r0 + u < Nk && lane < Nk) ? blk[(r0 + u) * Nk + lane] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (r0 + u < Nk && lane < Np) R[(r0 + u) * Wp + pc + lane] = (T)v[u];
           }
-          if (G > 1) acc = group_sum(acc, G);
-          if (live && lg == 0) R[r * W + c0 + c] -= acc;
-        }
-        __syncthreads();
-      }
-      if (j < k) {
-        const T* Li = Linv + S.ioff[j];
-        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
-          const int r = i / Nj, c = i - r * Nj;
-          T acc = T(0);
-          for (int t = 0; t <= c; ++t) acc = fma(R[r * W + c0 + t], Li[c * Nj + t], acc);
-          tmp[i] = acc;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < Nk * Nj; i += blockDim.x) {
-          const int r = i / Nj, c = i - r * Nj;
-          R[r * W + c0 + c] = tmp[i];
-        }
-        __syncthreads();
-      } else {
-        for (int c = 0; c < Nk; ++c) {
-          if (threadIdx.x == 0) {
-            const T d = R[c * W + c0 + c];
-            if (!(d > T(0)) || !isfinite((double)d)) bad = 1;
-            dsh = sqrt(d);
-            R[c * W + c0 + c] = dsh;
+        } else if (blk) {  // A_{k,i}[r][c] = blk[c][r]: lanes over r read coalesced
+          for (int c0 = 0; c0 < Np; c0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (c0 + u < Ni && lane < Nk) ? blk[(c0 + u) * Nk + lane] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (c0 + u < Np && lane < Nk) R[lane * Wp + pc + c0 + u] = (T)v[u];
           }
-          __syncthreads();
-          if (bad) return false;
-          for (int r = c + 1 + threadIdx.x; r < Nk; r += blockDim.x) R[r * W + c0 + c] /= dsh;
-          __syncthreads();
-          const int m = Nk - c - 1;
-          for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-            const int r = c + 1 + i / m, t = c + 1 + i % m;
-            if (t <= r) R[r * W + c0 + t] -= R[r * W + c0 + c] * R[t * W + c0 + c];
-          }
-          __syncthreads();
+        } else {
+          for (int r = 0; r < Nk; ++r)
+            if (lane < Np) R[r * Wp + pc + lane] = T(0);
         }
-        // zero the strict upper triangle and invert the diagonal block
-        for (int i = threadIdx.x; i < Nk * Nk; i += blockDim.x) {
-          const int r = i / Nk, c = i - r * Nk;
-          if (c > r) R[r * W + c0 + c] = T(0);
-        }
-        __syncthreads();
-        T* Li = Linv + S.ioff[k];
-        for (int col = threadIdx.x; col < Nk; col += blockDim.x) {
-          for (int r = 0; r < Nk; ++r) {
-            if (r < col) {
-              Li[r * Nk + col] = T(0);
-              continue;
-            }
-            T sum = (r == col) ? T(1) : T(0);
-            for (int t = col; t < r; ++t) sum -= R[r * W + c0 + t] * Li[t * Nk + col];
-            Li[r * Nk + col] = sum / R[r * W + c0 + r];
-          }
-        }
-        __syncthreads();
+        pc += Np;
       }
     }
+    __syncwarp();
+    T* LTk = LT + mt.loff[k];
+    int pcj = 0;
+    for (int j = jl; j < k; ++j) {
+      const int Nj = mt.NE[j];
+      const int Njp4 = (Nj + 3) & ~3;
+      {  // (1) X_j = R_j L_jj^-T (in place); B = (L_jj^-1)^T
+        const T* LiT = ring_wait<T>(rg);
+        rowgemm<T, true>(R + pcj, Wp, R + pcj, Wp, Nk, LiT, Nj, 1, Nj, Nj, lane);
+        if (!q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+        ++rg.consumed;
+        // L_kj = X_j into the transposed panel (lanes over rows: coalesced)
+        const int gj = mt.xoff[j] - base;
+        if (lane < Nk)
+          for (int c = 0; c < Nj; ++c) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pcj + c];
+      }
+      // (2) R_j' -= X_j L_{j'j}^T for j' in (j, k]
+      int pcjp = pcj + Njp4;
+      for (int jp = j + 1; jp <= k; ++jp) {
+        const int Njp = mt.NE[jp];
+        if (jp < k) {
+          const long long off = mt.loff[jp] + (long long)(mt.xoff[j] - mt.xoff[jlo_of(jp, Sx)]) * Njp;
+          const T* Lc = ring_wait<T>(rg);  // [t][c'] = L_{j'j}[c'][t]
+          rowgemm<T, false>(R + pcj, Wp, R + pcjp, Wp, Nk, Lc, Njp, 1, Nj, Njp, lane);
+          if (!q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+          ++rg.consumed;
+        } else {  // diagonal block: L_kj = X_j, B[t][c] = X_j[c][t]
+          rowgemm<T, false>(R + pcj, Wp, R + pcjp, Wp, Nk, R + pcj, 1, Wp, Nj, Njp, lane);
+        }
+        pcjp += (Njp + 3) & ~3;
+      }
+      pcj += Njp4;
+    }
+    // diagonal block: Cholesky in registers, lane i holds row i
+    T v[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      if (t >= Nk) break;
+      v[t] = (lane < Nk && t <= lane) ? R[lane * Wp + pck + t] : T(0);
+    }
+    T mydinv = T(1);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      if (c >= Nk) break;
+      T piv = __shfl_sync(full, v[c], c);
+      if (!(piv > T(0)) || !isfinite((double)piv)) {
+        badp = true;
+        piv = T(1);
+      }
+      const T d = sqrt(piv);
+      const T inv = T(1) / d;
+      if (lane == c) mydinv = inv;
+      const T lc = (lane == c) ? d : ((lane > c) ? v[c] * inv : v[c]);
+      v[c] = lc;
+#pragma unroll
+      for (int t = c + 1; t < 32; ++t) {
+        if (t >= Nk) break;
+        const T ltc = __shfl_sync(full, lc, t);
+        if (lane >= t) v[t] = fma(-lc, ltc, v[t]);
+      }
+    }
+    // inverse, lane = column: y[r] = Linv[r][lane]
+    T y[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      if (r >= Nk) break;
+      T s = (r == lane) ? T(1) : T(0);
+#pragma unroll
+      for (int t = 0; t < r; ++t) s = fma(-__shfl_sync(full, v[t], r), y[t], s);
+      const T dinv = __shfl_sync(full, mydinv, r);
+      y[r] = (r >= lane) ? s * dinv : T(0);
+    }
+    T* Li = Linv + mt.ioff[k];
+    T* LiT = Li + ((Nk * Nk + 3) & ~3);
+    const int gk = mt.xoff[k] - base;
+    if (lane < Nk) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c >= Nk) break;
+        LTk[(size_t)(gk + c) * Nk + lane] = (c <= lane) ? v[c] : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        if (r >= Nk) break;
+        Li[r * Nk + lane] = y[r];
+        LiT[lane * Nk + r] = y[r];
+      }
+    }
+    fence_proxy_async();  // the next rows copy these panels with the async proxy
+    __syncwarp();
+    const bool timed_out = !__all_sync(full, rg.ok);
+    if (__any_sync(full, badp) || timed_out) {
+      ring_drain<T>(rg);
+      m.ph = rg.ph;
+      return timed_out ? kFacTimeout : kFacPivot;
+    }
+  }
+  m.ph = rg.ph;
+  return kFacOk;
+}
+
+// Chunk sequence of the substitutions. Forward, block row k ascending: the
+// rows of panel k at the columns of each j in [jlo_k, k), then (L_kk^-1)^T.
+// Backward, k descending: L_kk^-1 first, then the same panel chunks. The
+// state advances incrementally (j = -1 marks the inverse).
+struct SubstSeq {
+  int k, j, jl, Nk, dir;
+  long long poff;  // element offset of chunk j within the factor
+};
+
+__device__ __forceinline__ SubstSeq subst_begin(const SolveMeta& mt, int Sx, int k, int dir) {
+  SubstSeq q;
+  q.k = k;
+  q.dir = dir;
+  q.jl = jlo_of(k, Sx);
+  q.Nk = mt.NE[k];
+  q.poff = mt.loff[k];
+  q.j = dir > 0 ? (q.jl < k ? q.jl : -1) : -1;
+  return q;
+}
+
+template <typename T>
+__device__ __forceinline__ void subst_issue(Ring<T>& r, SubstSeq& q, const SolveMeta& mt, int Sx, int nsub,
+                                            const T* LT, const T* Linv, int lane) {
+  const int Nk = q.Nk;
+  if (q.j < 0) {
+    ring_issue<T>(r, Linv, mt.ioff[q.k] + (q.dir > 0 ? ((Nk * Nk + 3) & ~3) : 0), Nk * Nk, lane);
+    if (q.dir > 0) {
+      if (q.k + 1 < nsub) q = subst_begin(mt, Sx, q.k + 1, 1);
+      else q.k = nsub;
+    } else {
+      q.j = q.jl < q.k ? q.jl : -2;  // -2: row done
+    }
+  } else {
+    const int Nj = mt.NE[q.j];
+    ring_issue<T>(r, LT, q.poff, Nj * Nk, lane);
+    q.poff += (long long)Nj * Nk;
+    if (++q.j == q.k) q.j = q.dir > 0 ? -1 : -2;
+  }
+  if (q.dir < 0 && q.j == -2) {
+    if (q.k > 0) q = subst_begin(mt, Sx, q.k - 1, -1);
+    else q.k = -1;
+  }
+}
+__device__ __forceinline__ bool subst_done(const SubstSeq& q, int nsub) { return q.dir > 0 ? q.k >= nsub : q.k < 0; }
+
+// Solve L L^T out = in with the transposed panels (arithmetic in T), by one
+// warp; y and z live in shared memory. Returns false if a copy did not complete.
+template <typename T>
+__device__ bool wsubstitute(const SimDev& S, const T* LT, const T* Linv, const double* in, double* out,
+                            WarpSmem<T>& m, int lane) {
+  const SolveMeta& mt = m.mt;
+  const int nsub = S.n_sub, Sx = S.Sx, N = S.N;
+  T* y = m.yz;
+  T* z = y + N;
+  T* tv = m.tv;
+  Ring<T> rg{m.R, m.bar, m.dl, m.n_sub_slots, 0u, 0u, m.ph, true};
+  for (int i = lane; i < N; i += 32) {
+    y[i] = (T)in[i];
+    z[i] = T(0);
+  }
+  SubstSeq q = subst_begin(mt, Sx, 0, 1);
+  while (!subst_done(q, nsub) && (int)(rg.issued - rg.consumed) < rg.nslot) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+  __syncwarp();
+  // forward: y_k = L_kk^-1 (in_k - sum_j L_kj y_j)
+  for (int k = 0; k < nsub; ++k) {
+    const int jl = jlo_of(k, Sx);
+    const int Nk = mt.NE[k], xk = mt.xoff[k];
+    T a0 = (lane < Nk) ? y[xk + lane] : T(0), a1 = T(0);
+    for (int j = jl; j < k; ++j) {
+      const int Nj = mt.NE[j];
+      const T* P = ring_wait<T>(rg);  // [g][c]
+      const T* yj = y + mt.xoff[j];
+      if (lane < Nk) {
+        T a2 = T(0), a3 = T(0);
+        int g = 0;
+        for (; g + 3 < Nj; g += 4) {
+          a0 = fma(-P[g * Nk + lane], yj[g], a0);
+          a1 = fma(-P[(g + 1) * Nk + lane], yj[g + 1], a1);
+          a2 = fma(-P[(g + 2) * Nk + lane], yj[g + 2], a2);
+          a3 = fma(-P[(g + 3) * Nk + lane], yj[g + 3], a3);
+        }
+        for (; g < Nj; ++g) a0 = fma(-P[g * Nk + lane], yj[g], a0);
+        a1 += a2 + a3;
+      }
+      ring_release_sync();
+      if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+      ++rg.consumed;
+    }
+    const T* LiT = ring_wait<T>(rg);
+    if (lane < Nk) tv[lane] = a0 + a1;
+    __syncwarp();
+    T yk = T(0), yk1 = T(0);
+    if (lane < Nk) {  // y_k[c] = sum_{t <= c} Linv[c][t] tv[t]
+      int t = 0;
+      for (; t + 1 <= lane; t += 2) {
+        yk = fma(LiT[t * Nk + lane], tv[t], yk);
+        yk1 = fma(LiT[(t + 1) * Nk + lane], tv[t + 1], yk1);
+      }
+      if (t <= lane) yk = fma(LiT[t * Nk + lane], tv[t], yk);
+      yk += yk1;
+    }
+    ring_release_sync();
+    if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+    ++rg.consumed;
+    if (lane < Nk) y[xk + lane] = yk;
+    __syncwarp();
+  }
+  // backward: z_k = L_kk^-T (y_k - p_k), then p_j += L_kj^T z_k for j < k
+  q = subst_begin(mt, Sx, nsub - 1, -1);
+  while (!subst_done(q, nsub) && (int)(rg.issued - rg.consumed) < rg.nslot) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+  for (int k = nsub - 1; k >= 0; --k) {
+    const int jl = jlo_of(k, Sx);
+    const int Nk = mt.NE[k], xk = mt.xoff[k];
+    const T* Li = ring_wait<T>(rg);
+    if (lane < Nk) tv[lane] = y[xk + lane] - z[xk + lane];
+    __syncwarp();
+    T zc = T(0);
+    if (lane < Nk) {
+      for (int r = lane; r < Nk; ++r) zc = fma(Li[r * Nk + lane], tv[r], zc);
+    }
+    ring_release_sync();
+    if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+    ++rg.consumed;
+    if (lane < Nk) z[xk + lane] = zc;
+    __syncwarp();
+    const T* zk = z + xk;
+    for (int j = jl; j < k; ++j) {
+      const int Nj = mt.NE[j];
+      const T* P = ring_wait<T>(rg);  // [g][c]
+      if (lane < Nj) {  // lane = g; rotated for even N_k
+        const int g = lane;
+        int c = (Nk & 1) ? 0 : g % Nk;
+        T a0 = T(0);
+        for (int u = 0; u < Nk; ++u) {
+          a0 = fma(P[g * Nk + c], zk[c], a0);
+          if (++c == Nk) c = 0;
+        }
+        z[mt.xoff[j] + g] += a0;
+      }
+      ring_release_sync();
+      if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+      ++rg.consumed;
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < N; i += 32) out[i] = (double)z[i];
+  __syncwarp();
+  m.ph = rg.ph;
+  return __all_sync(0xffffffffu, rg.ok);
+}
+
+// acc += sum_{c < n} a[c * sa] xs[c] with four chains (FP64).
+__device__ __forceinline__ double dot_strided(const double* __restrict__ a, int sa, const double* xs, int n,
+                                              double acc) {
+  double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = 0;
+  for (; c + 3 < n; c += 4) {
+    acc = fma(a[c * sa], xs[c], acc);
+    a1 = fma(a[(c + 1) * sa], xs[c + 1], a1);
+    a2 = fma(a[(c + 2) * sa], xs[c + 2], a2);
+    a3 = fma(a[(c + 3) * sa], xs[c + 3], a3);
+  }
+  for (; c < n; ++c) acc = fma(a[c * sa], xs[c], acc);
+  return (acc + a1) + (a2 + a3);
+}
+
+// r = b - A x with the block-sparse assembled A, in FP64, by one warp; x is
+// staged in the shared work area xs [N] (FP64).
+__device__ void wresidual(const SimDev& S, const SolveMeta& mt, const double* x, const double* b, double* r,
+                          double* xs, int lane) {
+  const int Sx = S.Sx, Sy = S.Sy, nsub = S.n_sub;
+  for (int i = lane; i < S.N; i += 32) xs[i] = x[i];
+  __syncwarp();
+  for (int E = 0; E < nsub; ++E) {
+    const int NE = mt.NE[E], x0 = mt.xoff[E];
+    const int I = E % Sx, J = E / Sx;
+    if (lane < NE) {
+      const int i = lane;
+      // diagonal block (symmetric: column i read coalesced)
+      double acc = dot_strided(S.A + S.aoff[E] + i, NE, xs + x0, NE, 0.0);
+      if (I > 0) {  // left neighbour: A_{E,E-1} = blk^T, blk [N_{E-1}][N_E]
+        const int j = E - 1;
+        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)] + i, NE, xs + mt.xoff[j], mt.NE[j], acc);
+      }
+      if (J > 0) {  // lower neighbour
+        const int j = E - Sx;
+        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + (J - 1) * Sx + I] + i, NE, xs + mt.xoff[j], mt.NE[j], acc);
+      }
+      if (I < Sx - 1) {  // right neighbour: A_{E,E+1} = blk [N_E][N_{E+1}]
+        const int j = E + 1, Nj = mt.NE[j];
+        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + I] + (size_t)i * Nj, 1, xs + mt.xoff[j], Nj, acc);
+      }
+      if (J < Sy - 1) {  // upper neighbour
+        const int j = E + Sx, Nj = mt.NE[j];
+        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + J * Sx + I] + (size_t)i * Nj, 1, xs + mt.xoff[j], Nj, acc);
+      }
+      r[x0 + i] = b[x0 + i] - acc;
+    }
+  }
+  __syncwarp();
+}
+
+// x = (L L^T)^-1 b, then `iters` refinement steps x += (L L^T)^-1 (b - A x)
+// with the residual in FP64. Returns false if a copy did not complete.
+template <typename T>
+__device__ bool wsolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, WarpSmem<T>& m, int lane) {
+  if (!wsubstitute<T>(S, Lst, Linv, S.b, S.x, m, lane)) return false;
+  for (int it = 0; it < iters; ++it) {
+    wresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz), lane);
+    if (!wsubstitute<T>(S, Lst, Linv, S.rv, S.dv, m, lane)) return false;
+    for (int i = lane; i < S.N; i += 32) S.x[i] += S.dv[i];
+    __syncwarp();
   }
   return true;
 }
 
-// Solve L L^T out = in with factor storage T (arithmetic in T); y is work.
-template <typename T>
-__device__ void substitute(const SimDev& S, const T* Lst, const T* Linv, const double* in,
-                           double* out, T* y, T* t) {
-  const int nsub = S.n_sub, Sx = S.Sx;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = 0; k < nsub; ++k) {
-    const int jl = jlo_of(k, Sx);
-    const int base = S.xoff[jl];
-    const int W = S.xoff[k + 1] - base;
-    const int Nk = S.NE[k];
-    const int off = W - Nk;
-    const T* R = Lst + S.loff[k];
-    for (int r = warp; r < Nk; r += nw) {
-      T acc = T(0);
-      for (int g = lane; g < off; g += 32) acc = fma(R[(size_t)r * W + g], y[base + g], acc);
-      acc = group_sum(acc, 32);
-      if (lane == 0) t[r] = (T)in[S.xoff[k] + r] - acc;
-    }
-    __syncthreads();
-    const T* Li = Linv + S.ioff[k];
-    for (int r = threadIdx.x; r < Nk; r += blockDim.x) {
-      T acc = T(0);
-      for (int c = 0; c <= r; ++c) acc = fma(Li[r * Nk + c], t[c], acc);
-      y[S.xoff[k] + r] = acc;
-    }
-    __syncthreads();
-  }
-  // backward: the second half of y holds the solution in T
-  T* z = y + S.N;
-  for (int k = nsub - 1; k >= 0; --k) {
-    const int Nk = S.NE[k];
-    const int kmax = min(k + Sx, nsub - 1);
-    for (int c = warp; c < Nk; c += nw) {
-      T acc = T(0);
-      for (int kk = k + 1; kk <= kmax; ++kk) {
-        const int jl2 = jlo_of(kk, Sx);
-        const int W2 = S.xoff[kk + 1] - S.xoff[jl2];
-        const int col = S.xoff[k] - S.xoff[jl2] + c;
-        const T* R2 = Lst + S.loff[kk];
-        const int N2 = S.NE[kk];
-        for (int r = lane; r < N2; r += 32) acc = fma(R2[(size_t)r * W2 + col], z[S.xoff[kk] + r], acc);
-      }
-      acc = group_sum(acc, 32);
-      if (lane == 0) t[c] = y[S.xoff[k] + c] - acc;
-    }
-    __syncthreads();
-    const T* Li = Linv + S.ioff[k];
-    for (int c = threadIdx.x; c < Nk; c += blockDim.x) {
-      T acc = T(0);
-      for (int r = c; r < Nk; ++r) acc = fma(Li[r * Nk + c], t[r], acc);
-      z[S.xoff[k] + c] = acc;
-    }
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < S.N; i += blockDim.x) out[i] = (double)z[i];
-  __syncthreads();
-}
+// FP32 factor (one warp per simulation): a simulation whose FP32
+// factorisation meets a non-positive pivot is marked for the FP64 kernel.
+constexpr int kStRetry64 = 1;
 
-// r = b - A x with the block-sparse assembled A, in FP64.
-__device__ void residual(const SimDev& S, const double* x, const double* b, double* r) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int E = 0; E < S.n_sub; ++E) {
-    const int NE = S.NE[E], x0 = S.xoff[E];
-    for (int i = warp; i < NE; i += nw) {
-      double acc = 0.0;
-      const double* Ad = S.A + S.aoff[E];
-      for (int c = lane; c < NE; c += 32) acc = fma(Ad[i * NE + c], x[x0 + c], acc);
-      for (int dir = 0; dir < 2; ++dir) {  // neighbours earlier in the order: A_{E,j} = blk^T
-        const int bb = coupling_block(S, E, dir);
-        if (bb < 0) continue;
-        const int j = dir == 0 ? E - 1 : E - S.Sx;
-        const int Nj = S.NE[j];
-        const double* Ab = S.A + S.aoff[bb];  // [N_j][N_E]
-        for (int c = lane; c < Nj; c += 32) acc = fma(Ab[c * NE + i], x[S.xoff[j] + c], acc);
-      }
-      for (int dir = 2; dir < 4; ++dir) {  // neighbours later in the order: A_{E,j} = blk
-        const int bb = coupling_block_up(S, E, dir);
-        if (bb < 0) continue;
-        const int j = dir == 2 ? E + 1 : E + S.Sx;
-        const int Nj = S.NE[j];
-        const double* Ab = S.A + S.aoff[bb];  // [N_E][N_j]
-        for (int c = lane; c < Nj; c += 32) acc = fma(Ab[i * Nj + c], x[S.xoff[j] + c], acc);
-      }
-      acc = group_sum(acc, 32);
-      if (lane == 0) r[x0 + i] = b[x0 + i] - acc;
-    }
-  }
-  __syncthreads();
-}
-
-// x = (L L^T)^-1 b, then `iters` refinement steps x += (L L^T)^-1 (b - A x)
-// with the residual in FP64.
-template <typename T>
-__device__ void solve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, T* sm) {
-  T* y = reinterpret_cast<T*>(S.y);  // [2N] of T (the y array holds 2N doubles)
-  substitute<T>(S, Lst, Linv, S.b, S.x, y, sm);
-  for (int it = 0; it < iters; ++it) {
-    residual(S, S.x, S.b, S.rv);
-    substitute<T>(S, Lst, Linv, S.rv, S.dv, y, sm);
-    for (int i = threadIdx.x; i < S.N; i += blockDim.x) S.x[i] += S.dv[i];
-    __syncthreads();
-  }
-}
-
-// mode 0: FP64 factor, `iters` refinement steps.
-// mode 1: FP32 factor with FP64 residuals (`iters` steps); a simulation whose
-//         FP32 factorisation meets a non-positive pivot is factorised in FP64.
-__global__ void k_chol_solve(const SimDev* __restrict__ sims, const int* __restrict__ active,
-                             int mode, int iters) {
-  const SimDev& S = sims[active[blockIdx.x]];
+__global__ void __launch_bounds__(32) k_wsolve32(const SimDev* __restrict__ sims, const int* __restrict__ active,
+                                                 int n_active, int iters) {
+  const int lane = threadIdx.x & 31;
+  const int a = blockIdx.x;
+  if (a >= n_active) return;
+  const SimDev& S = sims[active[a]];
   if (S.status[0] != kStOk) return;
   extern __shared__ double sm[];
-  if (mode == 1) {
-    float* Lf = reinterpret_cast<float*>(S.L);
-    float* Lif = reinterpret_cast<float*>(S.Linv);
-    if (factor<float>(S, Lf, Lif, reinterpret_cast<float*>(sm))) {
-      solve_refine<float>(S, Lf, Lif, iters, reinterpret_cast<float*>(sm));
-      return;
-    }
-    __syncthreads();
+  unsigned char* b = reinterpret_cast<unsigned char*>(sm);
+  float* Lf = reinterpret_cast<float*>(S.L);
+  float* Lif = reinterpret_cast<float*>(S.Linv);
+  WarpSmem<float> m = warp_carve_and_load<float>(S, b, lane);
+  const int f = wfactor<float>(S, Lf, Lif, m, lane);
+  if (f == kFacOk) {
+    if (!wsolve_refine<float>(S, Lf, Lif, iters, m, lane) && lane == 0) S.status[0] = kStTimeout;
+  } else if (lane == 0) {
+    S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
   }
-  if (!factor<double>(S, S.L, S.Linv, sm)) {
-    if (threadIdx.x == 0) S.status[0] = kStNotSpd;
+}
+
+// FP64 factor. only_retry: process only the simulations marked by the FP32 kernel.
+__global__ void __launch_bounds__(32) k_wsolve64(const SimDev* __restrict__ sims, const int* __restrict__ active,
+                                                 int n_active, int iters, int only_retry) {
+  const int lane = threadIdx.x & 31;
+  const int a = blockIdx.x;
+  if (a >= n_active) return;
+  const SimDev& S = sims[active[a]];
+  const int st = S.status[0];
+  if (only_retry ? st != kStRetry64 : st != kStOk) return;
+  __syncwarp();
+  if (lane == 0) S.status[0] = kStOk;
+  extern __shared__ double sm[];
+  unsigned char* b = reinterpret_cast<unsigned char*>(sm);
+  WarpSmem<double> m = warp_carve_and_load<double>(S, b, lane);
+  const int f = wfactor<double>(S, S.L, S.Linv, m, lane);
+  if (f != kFacOk) {
+    if (lane == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  solve_refine<double>(S, S.L, S.Linv, mode == 1 ? iters : iters, sm);
+  if (!wsolve_refine<double>(S, S.L, S.Linv, iters, m, lane) && lane == 0) S.status[0] = kStTimeout;
 }
 
 // ---------------------------------------------------------------- static scratch
@@ -407,29 +860,36 @@ __global__ void k_noalloc_tables(SimDev S) {
     for (int I = 0; I < S.Sx; ++I, ++b) aoff[b + 1] = aoff[b] + (long long)NE[J * S.Sx + I] * NE[(J + 1) * S.Sx + I];
   loff[0] = 0;
   ioff[0] = 0;
-  for (int k = 0; k < S.n_sub; ++k) {
-    loff[k + 1] = loff[k] + (long long)NE[k] * (xoff[k + 1] - xoff[jlo_of(k, S.Sx)]);
-    ioff[k + 1] = ioff[k] + (long long)NE[k] * NE[k];
-  }
+  solve_offsets(S.n_sub, S.Sx, NE, xoff, loff, ioff);
   S.status[0] = kStOk;
 }
 
-__global__ void k_chol_solve_static(SimDev S, int mode, int iters) {
+__global__ void __launch_bounds__(32) k_wsolve_static(SimDev S, int mode, int iters) {
+  const int lane = threadIdx.x & 31;
   extern __shared__ double sm[];
+  unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   if (mode == 1) {
     float* Lf = reinterpret_cast<float*>(S.L);
     float* Lif = reinterpret_cast<float*>(S.Linv);
-    if (factor<float>(S, Lf, Lif, reinterpret_cast<float*>(sm))) {
-      solve_refine<float>(S, Lf, Lif, iters, reinterpret_cast<float*>(sm));
+    WarpSmem<float> mf = warp_carve_and_load<float>(S, b, lane);
+    const int f = wfactor<float>(S, Lf, Lif, mf, lane);
+    if (f == kFacOk) {
+      if (!wsolve_refine<float>(S, Lf, Lif, iters, mf, lane) && lane == 0) S.status[0] = kStTimeout;
       return;
     }
-    __syncthreads();
+    if (f == kFacTimeout) {
+      if (lane == 0) S.status[0] = kStTimeout;
+      return;
+    }
+    warp_release_barriers(mf.bar, lane);
   }
-  if (!factor<double>(S, S.L, S.Linv, sm)) {
-    if (threadIdx.x == 0) S.status[0] = kStNotSpd;
+  WarpSmem<double> md = warp_carve_and_load<double>(S, b, lane);
+  const int f = wfactor<double>(S, S.L, S.Linv, md, lane);
+  if (f != kFacOk) {
+    if (lane == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  solve_refine<double>(S, S.L, S.Linv, iters, sm);
+  if (!wsolve_refine<double>(S, S.L, S.Linv, iters, md, lane) && lane == 0) S.status[0] = kStTimeout;
 }
 
 }  // namespace
@@ -442,10 +902,31 @@ void launch_assemble(const SimDev* sims, const int* active, int n_active, int ma
     k_assemble<<<dim3(max_blocks, n_active), 128, 0, st>>>(sims, active);
 }
 
-void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
-                       cudaStream_t st) {
-  const size_t smem = 64 * 64 * sizeof(double);  // max_NE <= 64 (checked at load)
-  k_chol_solve<<<n_active, 256, smem, st>>>(sims, active, mode, iters);
+size_t solve_smem_bytes(int n_sub, int panel_words, int max_w, int N, size_t elem) {
+  (void)max_w;
+  return warp_smem_bytes(n_sub, panel_words, N, elem);
+}
+
+static cudaError_t set_smem(const void* fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// One warp (one CTA) per simulation; the CTAs spread over the SMs, as many
+// per SM as their shared memory allows.
+cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
+                              const SolveShape& sh, cudaStream_t st) {
+  cudaError_t e;
+  if (n_active <= 0) return cudaSuccess;
+  if (mode == 1) {
+    const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
+    if ((e = set_smem((const void*)k_wsolve32, s32)) != cudaSuccess) return e;
+    k_wsolve32<<<n_active, 32, s32, st>>>(sims, active, n_active, iters);
+  }
+  const size_t s64 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(double));
+  if ((e = set_smem((const void*)k_wsolve64, s64)) != cudaSuccess) return e;
+  k_wsolve64<<<n_active, 32, s64, st>>>(sims, active, n_active, iters, mode == 1 ? 1 : 0);
+  return cudaGetLastError();
 }
 
 }  // namespace lrbms
@@ -455,6 +936,7 @@ void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int 
 
 namespace {
 constexpr int kMaxDevices = 64;
+constexpr int kNoAllocMaxSub = 4096;
 unsigned char* g_noalloc_dev[kMaxDevices] = {nullptr};
 }  // namespace
 
@@ -469,20 +951,19 @@ extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double*
   // sizes from the caller's (host) basis sizes; no host or device allocation
   long long N = 0, l_tot = 0, i_tot = 0;
   for (int E = 0; E < n_sub; ++E) {
-    if (N_E[E] < 1 || N_E[E] > 64) return LRBMS_E_ARG;
+    if (N_E[E] < 1 || N_E[E] > kMaxNE) return LRBMS_E_ARG;
     N += N_E[E];
-    i_tot += (long long)N_E[E] * N_E[E];
+    i_tot += 2 * (long long)round4((size_t)N_E[E] * N_E[E]);
   }
-  {
-    long long x0 = 0;  // running prefix for the envelope widths
-    for (int k = 0; k < n_sub; ++k) {
-      const int jl = jlo_of(k, Sx);
-      long long base = 0;
-      for (int j = 0; j < jl; ++j) base += N_E[j];
-      x0 += N_E[k];
-      l_tot += (long long)N_E[k] * (x0 - base);
-    }
-  }
+  // prefix sums on the stack (no allocation); n_sub is capped for this reason
+  if (n_sub > kNoAllocMaxSub) return LRBMS_E_BUDGET;
+  int xo[kNoAllocMaxSub + 1];
+  xo[0] = 0;
+  for (int E = 0; E < n_sub; ++E) xo[E + 1] = xo[E] + N_E[E];
+  for (int k = 0; k < n_sub; ++k) l_tot += (long long)round4((size_t)N_E[k] * (xo[k + 1] - xo[jlo_of(k, Sx)]));
+  int panel_words = 0, max_w = 0;
+  solve_panel_sizes(n_sub, Sx, N_E, xo, &panel_words, &max_w);
+  if (solve_smem_bytes(n_sub, panel_words, max_w, (int)N, sizeof(double)) > kMaxSolveSmem) return LRBMS_E_BUDGET;
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
   size_t off = 0;
   const size_t o_NE = off; off = up(off + 4 * (size_t)n_sub);
@@ -515,16 +996,22 @@ extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double*
   S.L = (double*)(base + o_L); S.Linv = (double*)(base + o_Li); S.y = (double*)(base + o_y);
   S.rv = (double*)(base + o_rv); S.dv = (double*)(base + o_dv);
   S.A = const_cast<double*>(A); S.b = const_cast<double*>(rhs); S.x = x;
+  S.panel_words = panel_words;
+  S.max_w = max_w;
   if (cudaMemcpyAsync(base + o_NE, N_E, 4 * (size_t)n_sub, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return LRBMS_E_CUDA;
   k_noalloc_tables<<<1, 1, 0, st>>>(S);
   const int mode = solver == LRBMS_SOLVE_MIXED ? 1 : 0;
   const int iters = refine_iters > 0 ? refine_iters : (mode == 1 ? 4 : 1);
-  k_chol_solve_static<<<1, 256, 64 * 64 * sizeof(double), st>>>(S, mode, iters);
+  const size_t smem = solve_smem_bytes(n_sub, panel_words, max_w, (int)N, sizeof(double));
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_wsolve_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return LRBMS_E_BUDGET;
+  k_wsolve_static<<<1, 32, smem, st>>>(S, mode, iters);
   if (cudaGetLastError() != cudaSuccess) return LRBMS_E_CUDA;
   int status = 0;
   if (cudaMemcpyAsync(&status, base + o_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return LRBMS_E_CUDA;
-  return status == 0 ? LRBMS_OK : LRBMS_E_NOT_SPD;
+  return status == 0 ? LRBMS_OK : status == kStTimeout ? LRBMS_E_TIMEOUT : LRBMS_E_NOT_SPD;
 }

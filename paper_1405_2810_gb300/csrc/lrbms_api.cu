@@ -256,8 +256,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemcpy(NE.data(), off->N_E, sizeof(int) * n_sub, cudaMemcpyDefault));
   int max_NE = 0;
   for (int E = 0; E < n_sub; ++E) {
-    if (NE[E] < 1 || NE[E] > 64 || NE[E] > 3 * cells)
-      return fail(ctx, LRBMS_E_FORMAT, "local basis sizes must be in 1..min(64, 3*cells_E)");
+    if (NE[E] < 1 || NE[E] > lrbms::kMaxNE || NE[E] > 3 * cells)
+      return fail(ctx, LRBMS_E_FORMAT, "local basis sizes must be in 1..min(32, 3*cells_E)");
     max_NE = NE[E] > max_NE ? NE[E] : max_NE;
   }
   std::vector<int> xoff(n_sub + 1, 0);
@@ -284,11 +284,11 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const long long a_tot = aoff[n_blocks];
   const long long d_tot = aoff[n_sub];  // diagonal blocks
   std::vector<long long> loff(n_sub + 1, 0), ioff(n_sub + 1, 0);
-  for (int k = 0; k < n_sub; ++k) {
-    const int jl = lrbms::jlo_of(k, Sx);
-    loff[k + 1] = loff[k] + (long long)NE[k] * (xoff[k + 1] - xoff[jl]);
-    ioff[k + 1] = ioff[k] + (long long)NE[k] * NE[k];
-  }
+  lrbms::solve_offsets(n_sub, Sx, NE.data(), xoff.data(), loff.data(), ioff.data());
+  int panel_words = 0, max_w = 0;
+  lrbms::solve_panel_sizes(n_sub, Sx, NE.data(), xoff.data(), &panel_words, &max_w);
+  if (lrbms::solve_smem_bytes(n_sub, panel_words, max_w, N, sizeof(double)) > lrbms::kMaxSolveSmem)
+    return fail(ctx, LRBMS_E_FORMAT, "reduced system too large for the on-chip solve (shared memory)");
   const int n_tiles = (n_cells + lrbms::kCellTile - 1) / lrbms::kCellTile;
   const bool mixed = ctx->precision == LRBMS_MIXED;
   const size_t Q = (size_t)M + 1;
@@ -329,6 +329,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.nx = nx; d.ny = ny; d.Sx = Sx; d.Sy = Sy; d.cx = cx; d.cy = cy;
   d.n_cells = n_cells; d.n_sub = n_sub; d.n_cf = n_cf; d.nb = nb; d.nxf = nxf; d.n_faces = n_faces;
   d.M = M; d.N = N; d.max_NE = max_NE; d.n_tiles = n_tiles; d.n_blocks = n_blocks;
+  d.panel_words = panel_words;
+  d.max_w = max_w;
   d.relperm = pr->relperm; d.swapped = pr->mean_weights; d.prof_mode = off->prof_idx ? 0 : 1;
   d.dt_mode = pr->dt_mode;
   d.hx = pr->Lx / nx; d.hy = pr->Ly / ny; d.vol = d.hx * d.hy; d.c_pen = off->c_pen; d.Lf = off->Lf;
@@ -425,9 +427,14 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
   CK(cudaSetDevice(ctx->device));
   std::vector<int> act(ids, ids + n_sims);
   int max_tiles = 0, max_blocks = 0, max_sub = 0, max_faces = 0;
+  lrbms::SolveShape sh{0, 0, 0, 0};
   for (int id : act) {
     if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
     const SimDev& d = ctx->slots[id].d;
+    sh.n_sub = std::max(sh.n_sub, d.n_sub);
+    sh.panel_words = std::max(sh.panel_words, d.panel_words);
+    sh.max_w = std::max(sh.max_w, d.max_w);
+    sh.N = std::max(sh.N, d.N);
     max_tiles = std::max(max_tiles, d.n_tiles);
     max_blocks = std::max(max_blocks, d.n_blocks + d.n_sub);
     max_sub = std::max(max_sub, d.n_sub);
@@ -450,7 +457,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(1);
     lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st);
     mark(2);
-    lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, ctx->solver, ctx->refine_iters, st);
+    CK(lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, ctx->solver, ctx->refine_iters, sh, st));
     mark(3);
     lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st);
     mark(4);

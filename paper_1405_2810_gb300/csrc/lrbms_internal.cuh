@@ -16,6 +16,7 @@ constexpr int kFaceThreads = 256;
 constexpr int kStOk = 0;
 constexpr int kStNotSpd = -4;
 constexpr int kStNonFinite = -5;
+constexpr int kStTimeout = -6;
 
 // Everything a kernel needs about one simulation. Lives in device memory,
 // one entry per slot; all pointers point into the context's arena.
@@ -24,6 +25,8 @@ struct SimDev {
   int nx, ny, Sx, Sy, cx, cy;
   int n_cells, n_sub, n_cf, nb, nxf, n_faces;
   int M, N, max_NE;
+  int panel_words;  // max over block rows of N_k * (padded W_k): shared-memory panel of the solve
+  int max_w;        // widest block row W_k of the solve
   int n_tiles;      // ceil(n_cells / kCellTile)
   int n_blocks;     // n_sub + n_cf assembled blocks
   int relperm, swapped, prof_mode, dt_mode;
@@ -53,8 +56,10 @@ struct SimDev {
   const double* rhs;        // subdomain E at (M+1)*xoff[E]: [M+1][N_E]
 
   // block Cholesky factor (envelope of the lexicographic subdomain order)
-  const long long* loff;    // [n_sub+1] row panel k: [N_k][W_k], W_k = xoff[k+1]-xoff[jlo_k]
-  const long long* ioff;    // [n_sub+1] inverse of diagonal block k: [N_k][N_k]
+  const long long* loff;    // [n_sub+1] panel k stored transposed: [W_k][N_k], W_k = xoff[k+1]-xoff[jlo_k];
+                            // offsets are multiples of 4 elements (16-byte aligned copies)
+  const long long* ioff;    // [n_sub+1] inverse of diagonal block k, [N_k][N_k], then its transpose;
+                            // same alignment
 
   // state and work arrays
   double* s;        // [2][n_cells] ping-pong; current = steps & 1
@@ -85,8 +90,49 @@ void launch_fit(const SimDev* sims, const int* active, int n_active, int max_til
                 cudaStream_t st);
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
                      int mixed, cudaStream_t st);
-void launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
-                       cudaStream_t st);
+constexpr int kMaxNE = 32;  // local basis sizes 1..32 (one warp lane per row)
+constexpr size_t kMaxSolveSmem = 220 * 1024;  // leaves room for static shared memory
+// Shape maxima over the simulations of one solve launch.
+struct SolveShape {
+  int n_sub, panel_words, max_w, N;
+};
+// Shared memory of the solve kernels for elements of `elem` bytes.
+size_t solve_smem_bytes(int n_sub, int panel_words, int max_w, int N, size_t elem);
+// Shared-memory panel size (elements) and widest block row of the reduced
+// solve for basis sizes NE with prefix sums xoff (lengths n_sub, n_sub + 1).
+// In shared memory every block of a row starts on a multiple of 4 columns and
+// a row may carry up to 4 columns of stride padding.
+inline void solve_panel_sizes(int n_sub, int Sx, const int* NE, const int* xoff, int* panel_words,
+                              int* max_w) {
+  int pw = 0, mw = 0;
+  for (int k = 0; k < n_sub; ++k) {
+    const int W = xoff[k + 1] - xoff[jlo_of(k, Sx)];
+    int Wp = 0;
+    for (int i = jlo_of(k, Sx); i <= k; ++i) Wp += (NE[i] + 3) & ~3;
+    if (NE[k] * (Wp + 4) > pw) pw = NE[k] * (Wp + 4);
+    if (W > mw) mw = W;
+  }
+  *panel_words = pw;
+  *max_w = mw;
+}
+// Offsets of the factor panels and diagonal inverses (multiples of 4 elements;
+// block k holds L_kk^-1 and then (L_kk^-1)^T).
+__host__ __device__ inline void solve_offsets(int n_sub, int Sx, const int* NE, const int* xoff, long long* loff,
+                                              long long* ioff) {
+  loff[0] = 0;
+  ioff[0] = 0;
+  for (int k = 0; k < n_sub; ++k) {
+    const long long w = (long long)NE[k] * (xoff[k + 1] - xoff[jlo_of(k, Sx)]);
+    loff[k + 1] = loff[k] + ((w + 3) & ~3LL);
+    ioff[k + 1] = ioff[k] + 2 * (((long long)NE[k] * NE[k] + 3) & ~3LL);  // inverse and its transpose
+  }
+}
+// mode 0: FP64 factor; mode 1: FP32 factor (FP64 for simulations whose FP32
+// factorisation meets a non-positive pivot). Both refine with FP64 residuals.
+cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
+                              const SolveShape& sh, cudaStream_t st);
+// FP64 solve of the fine systems of the offline builder (one-cell blocks).
+cudaError_t launch_fine_solve(const SimDev* sims, const int* active, int n_active, cudaStream_t st);
 void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
                         int mixed, cudaStream_t st);
 void launch_flux(const SimDev* sims, const int* active, int n_active, int max_faces,

@@ -6,8 +6,8 @@
 // The fine SWIP-DG system (Section 3.2) of a P1 pressure on one-cell blocks
 // has exactly the 5-point block pattern the online solver factorises, so every
 // fine solve here runs through the same envelope block Cholesky
-// (launch_chol_solve) on a "fine" system with Sx = nx, Sy = ny and three
-// unknowns per block.
+// on a "fine" system with Sx = nx, Sy = ny and three unknowns per block
+// (launch_fine_solve).
 //
 // Local SWIP matrices use closed forms for rectangles: on a face with
 // tangential coordinate t in [-1,1], the P1 traces are alpha + beta t, so
@@ -791,7 +791,7 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
       jobs[p] = SysJob{p, 0, 3, 0, nullptr, init.sims[p].A, init.sims[p].A + 9 * (size_t)n_cells,
                        init.sims[p].b};
     if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "fine assembly");
-    launch_chol_solve(init.d_sims, init.d_active, n_prob, 0, 1, st);
+    BCK(launch_fine_solve(init.d_sims, init.d_active, n_prob, st));
   }
   // ---- velocity, time-of-flight and profiles (steps 1(b), 1(c))
   std::vector<double*> hF(n_prob), hta(n_prob), htb(n_prob);
@@ -888,7 +888,7 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
       }
     }
     if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "snapshot assembly");
-    launch_chol_solve(snaps.d_sims, snaps.d_active, n_snap_tot, 0, 1, st);
+    BCK(launch_fine_solve(snaps.d_sims, snaps.d_active, n_snap_tot, st));
   }
 
   // ---- local bases (step 2(e))
@@ -904,8 +904,8 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
   for (int p = 0; p < n_prob; ++p) {
     BCK(cudaMemcpy(NE[p].data(), opts[p].N_E, 4 * (size_t)n_sub, cudaMemcpyDefault));
     for (int E = 0; E < n_sub; ++E) {
-      if (NE[p][E] < 1 || NE[p][E] > 64 || NE[p][E] > 3 * cells)
-        return lrbms_internal_fail(ctx, LRBMS_E_ARG, "local basis sizes must be in 1..min(64, 3 cells_E)");
+      if (NE[p][E] < 1 || NE[p][E] > kMaxNE || NE[p][E] > 3 * cells)
+        return lrbms_internal_fail(ctx, LRBMS_E_ARG, "local basis sizes must be in 1..min(32, 3 cells_E)");
       phioff[p][E + 1] = phioff[p][E] + (long long)NE[p][E] * 3 * cells;
     }
     Phi[p] = B.get<double>((size_t)phioff[p][n_sub]);

@@ -43,7 +43,7 @@ def test_noalloc_solve_matches_step_twice(L, solver):
 
 def test_noalloc_rejects_oversized_system(L):
     import torch
-    NE = np.full(64 * 64, 64, dtype=np.int32)  # factor far beyond the fixed array
+    NE = np.full(64 * 64, 32, dtype=np.int32)  # factor far beyond the fixed array
     A = torch.zeros(1, dtype=torch.float64, device="cuda")
     rc = L.lrbms_solve_noalloc(64, 64, NE, A, A, A)
     assert rc == L.LRBMS_E_BUDGET
