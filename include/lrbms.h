@@ -90,8 +90,11 @@ typedef struct {
                         Cholesky and substitutions, iterative refinement with
                         FP64 residuals and updates; an FP32 factorisation that
                         meets a non-positive pivot is redone in FP64)       */
-  int refine_iters;  /* refinement steps after the first solve; 0: default
-                        (1 for FP64, 4 for MIXED); at most 16               */
+  int refine_iters;  /* most refinement steps after the first solve; 0:
+                        default (1 for FP64, 6 for MIXED); at most 16. The
+                        refinement stops early once the next correction,
+                        predicted from the last two, is below 1e-12 of the
+                        solution (max norms)                                */
 } lrbms_config;
 
 /* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with

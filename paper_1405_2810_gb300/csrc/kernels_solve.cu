@@ -4,7 +4,7 @@
 //   fixed-order sum of the fit partials), then every block
 //   A_b = c_b + sum_q theta_q (b_q)_b and every subdomain right-hand side
 //   b_E = e_E + sum_q theta_q (d_q)_E, streamed from the component arrays.
-// chol_solve: one warp per simulation. The matrix is symmetric positive
+// chol_solve: one CTA of four warps per simulation. The matrix is symmetric positive
 //   definite with a 5-point block pattern over the Sx x Sy subdomains; in
 //   lexicographic subdomain order its Cholesky factor lives in the envelope
 //   j in [k - Sx, k] of every block row k. Block row k of L is kept as a dense
@@ -107,12 +107,15 @@ __global__ void k_assemble32(const SimDev* __restrict__ sims, const int* __restr
 
 // ---------------------------------------------------------------- bulk-copy ring
 // Chunks of the factor (a block of a panel, or a diagonal inverse) are copied
-// from global to shared memory by cp.async.bulk, each completing on the
-// mbarrier of its slot; the copies of the next chunks run while the warp
-// computes on the current one. Every wait is bounded.
+// from global to shared memory by cp.async.bulk, each completing on the "full"
+// mbarrier of its slot; consumers release a slot on its "empty" mbarrier
+// before the producer (lane 0 of warp 0) refills it. The copies of the next
+// chunks run while the CTA computes on the current one. Every wait is bounded.
+constexpr int kNW = 4;                       // warps per simulation
+constexpr int kThreads = 32 * kNW;
 constexpr int kRing = 4;                     // slots of the factorisation ring
 constexpr int kSlot = kMaxNE * kMaxNE + 8;   // elements per slot: one 32 x 32 block + alignment slack
-constexpr int kMaxSlots = 32;                // mbarriers per warp
+constexpr int kMaxSlots = 32;                // slots (and full/empty mbarrier pairs) at most
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -121,6 +124,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -128,6 +134,9 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -155,60 +164,83 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// Warp-uniform ring state: slot n of the stream lives in slot n % nslot and
-// completes on barrier n % nslot; ph holds the parity awaited next on each barrier.
+// Ring state (all threads walk the same chunk stream): chunk n lives in slot
+// n % nslot; ph holds the parity awaited next on each full barrier. Producer
+// state, meaningful in warp 0: eph, the parity awaited next on each empty
+// barrier; used, the barriers filled before; fpar, the number of fills of each
+// barrier mod 2. Barrier s always pairs with slot s of the current ring.
 template <typename T>
 struct Ring {
   T* base;
-  uint64_t* bar;
+  uint64_t* full;
+  uint64_t* empty;
   int* dl;  // per slot: element offset of the chunk within its aligned copy
   int nslot;
   unsigned issued, consumed;
-  unsigned ph;
+  unsigned ph, eph, used, fpar;
   bool ok;
 };
 
-// Issue the copy of `count` elements starting at element `off` of `src`
-// (src 16-byte aligned): the copy starts at the 16-byte boundary at or below
-// `off` and its size is rounded up to 16 bytes.
+// Producer (called by warp 0; lane 0 copies): the copy of `count` elements
+// starting at element `off` of `src` (src 16-byte aligned) starts at the
+// 16-byte boundary at or below `off` and its size is rounded up to 16 bytes.
+// A slot filled before is refilled once its empty barrier has completed.
 template <typename T>
 __device__ __forceinline__ void ring_issue(Ring<T>& r, const T* src, long long off, int count, int lane) {
   constexpr int kA = 16 / (int)sizeof(T);
   const int d = (int)(off & (kA - 1));
   const uint32_t bytes = (uint32_t)(((d + count) * (int)sizeof(T) + 15) & ~15);
   const int s = (int)(r.issued % (unsigned)r.nslot);
+  if (r.used & (1u << s)) {  // after a timed-out wait, no further waits (fail fast)
+    if (lane == 0 && r.ok && !mbar_wait(&r.empty[s], (r.eph >> s) & 1u)) r.ok = false;
+    r.eph ^= 1u << s;
+  }
+  r.used |= 1u << s;
+  r.fpar ^= 1u << s;
   if (lane == 0) {
-    r.dl[s] = d;  // published to the waiting lanes by the arrive (release) below
-    mbar_expect_tx(&r.bar[s], bytes);
-    bulk_g2s(r.base + (size_t)s * kSlot, src + (off - d), bytes, &r.bar[s]);
+    r.dl[s] = d;  // published to the waiting threads by the arrive (release) below
+    mbar_expect_tx(&r.full[s], bytes);
+    bulk_g2s(r.base + (size_t)s * kSlot, src + (off - d), bytes, &r.full[s]);
   }
   ++r.issued;
 }
 
-// Wait for the next chunk; returns its first element (slot + alignment offset).
+// Consumer: wait for the next chunk; returns its first element.
 template <typename T>
 __device__ __forceinline__ const T* ring_wait(Ring<T>& r) {
   const int s = (int)(r.consumed % (unsigned)r.nslot);
-  if (!mbar_wait(&r.bar[s], (r.ph >> s) & 1u)) r.ok = false;
+  if (r.ok && !mbar_wait(&r.full[s], (r.ph >> s) & 1u)) r.ok = false;  // fail fast after a timeout
   r.ph ^= 1u << s;
   return r.base + (size_t)s * kSlot + r.dl[s];
 }
-
-__device__ __forceinline__ void ring_release_sync() { __syncwarp(); }
-
-// Bounded wait for every copy still in flight (error paths).
+// Consumer done with the chunk (after ring_wait): `count` arrivals on its
+// empty barrier (kNW consumers of 1, or one consumer of kNW).
 template <typename T>
-__device__ void ring_drain(Ring<T>& r) {
-  while (r.consumed < r.issued) {
-    const int s = (int)(r.consumed % (unsigned)r.nslot);
-    mbar_wait(&r.bar[s], (r.ph >> s) & 1u);
-    r.ph ^= 1u << s;
-    ++r.consumed;
-  }
+__device__ __forceinline__ void ring_release(Ring<T>& r, int lane, uint32_t count) {
+  const int s = (int)(r.consumed % (unsigned)r.nslot);
   __syncwarp();
+  if (lane == 0) mbar_arrive(&r.empty[s], count);
+  ++r.consumed;
+}
+// A chunk consumed by another warp.
+template <typename T>
+__device__ __forceinline__ void ring_skip(Ring<T>& r) {
+  const int s = (int)(r.consumed % (unsigned)r.nslot);
+  r.ph ^= 1u << s;
+  ++r.consumed;
 }
 
-// ---------------------------------------------------------------- per-warp shared memory
+// Error paths: bounded wait by the producer (lane 0 of the leader warp) for
+// the last fill of every barrier, so that no copy is in flight when the CTA exits.
+__device__ __forceinline__ int vwarp();
+template <typename T>
+__device__ void ring_drain(const Ring<T>& r) {
+  if ((threadIdx.x & 31) == 0 && vwarp() == 0)
+    for (int s = 0; s < kMaxSlots; ++s)
+      if (r.used & (1u << s)) mbar_wait(&r.full[s], ((~r.fpar) >> s) & 1u);
+}
+
+// ---------------------------------------------------------------- per-CTA shared memory
 struct SolveMeta {
   int* NE;
   int* xoff;
@@ -220,67 +252,88 @@ __host__ __device__ inline size_t meta_bytes(int n_sub) {
   return ((size_t)4 * (2 * n_sub + 1) + 15) / 16 * 16 + (size_t)16 * (n_sub + 1);
 }
 __host__ __device__ inline size_t round4(size_t v) { return (v + 3) & ~(size_t)3; }
-// Offset tables, mbarriers and slot offsets, the panel R of the current block
-// row (padded columns), the factorisation ring, the substitution vectors [2N]
-// and [32].
+constexpr size_t kBarBytes = 8 * kMaxSlots * 2 + 4 * kMaxSlots + 16;  // full, empty, dl, flags
+// Offset tables, barriers, slot offsets and flags, per-warp partial vectors
+// [kNW][32], the panel R of the current block row (padded columns), the
+// factorisation ring, the substitution vectors [2N] and [32].
 __host__ __device__ inline size_t warp_smem_bytes(int n_sub, int panel_words, int N, size_t elem) {
-  return meta_bytes(n_sub) + 12 * kMaxSlots +
-         elem * (round4(panel_words) + (size_t)kRing * kSlot + round4(2 * (size_t)N) + 32);
+  return meta_bytes(n_sub) + kBarBytes +
+         elem * (32 * kNW + round4(panel_words) + (size_t)kRing * kSlot + round4(2 * (size_t)N) + 32);
 }
 
 template <typename T>
-struct WarpSmem {
+struct CtaSmem {
   SolveMeta mt;
-  uint64_t* bar;
-  int* dl;   // [kMaxSlots]
-  T* R;      // [panel_words]
-  T* ring;   // [kRing][kSlot]
-  T* yz;     // [2N]
-  T* tv;     // [32]
+  uint64_t* full;   // [kMaxSlots]
+  uint64_t* empty;  // [kMaxSlots]
+  int* dl;          // [kMaxSlots]
+  int* flag;        // [0] non-positive pivot, [1] copy timeout
+  T* part;          // [kNW][32]
+  T* R;             // [panel_words]
+  T* ring;          // [kRing][kSlot]
+  T* yz;            // [2N]
+  T* tv;            // [32]
   int n_sub_slots;  // slots of the substitution ring, which spans R and the factor ring
-  unsigned ph;      // parity awaited next on each mbarrier
+  unsigned ph;      // ring state carried between the factorisation and the substitutions
+  unsigned eph, used, fpar;
 };
 
 template <typename T>
-__device__ WarpSmem<T> warp_carve_and_load(const SimDev& S, unsigned char* b, int lane) {
-  WarpSmem<T> m;
+__device__ CtaSmem<T> cta_carve_and_load(const SimDev& S, unsigned char* b) {
+  CtaSmem<T> m;
   const int ns = S.n_sub;
   m.mt.NE = reinterpret_cast<int*>(b);
   m.mt.xoff = m.mt.NE + ns;
   const size_t o = ((size_t)4 * (2 * ns + 1) + 15) / 16 * 16;
   m.mt.loff = reinterpret_cast<long long*>(b + o);
   m.mt.ioff = m.mt.loff + (ns + 1);
-  m.bar = reinterpret_cast<uint64_t*>(b + meta_bytes(ns));
-  m.dl = reinterpret_cast<int*>(b + meta_bytes(ns) + 8 * kMaxSlots);
-  T* t = reinterpret_cast<T*>(b + meta_bytes(ns) + 12 * kMaxSlots);
+  unsigned char* bb = b + meta_bytes(ns);
+  m.full = reinterpret_cast<uint64_t*>(bb);
+  m.empty = m.full + kMaxSlots;
+  m.dl = reinterpret_cast<int*>(m.empty + kMaxSlots);
+  m.flag = m.dl + kMaxSlots;
+  T* t = reinterpret_cast<T*>(bb + kBarBytes);
   const size_t rw = round4((size_t)S.panel_words);
-  m.R = t;
-  m.ring = t + rw;
+  m.part = t;
+  m.R = t + 32 * kNW;
+  m.ring = m.R + rw;
   m.yz = m.ring + (size_t)kRing * kSlot;
   m.tv = m.yz + round4(2 * (size_t)S.N);
   const size_t nss = (rw + (size_t)kRing * kSlot) / kSlot;
   m.n_sub_slots = nss > (size_t)kMaxSlots ? kMaxSlots : (int)nss;
-  m.ph = 0;
-  for (int i = lane; i < ns; i += 32) m.mt.NE[i] = S.NE[i];
-  for (int i = lane; i <= ns; i += 32) {
+  m.ph = m.eph = m.used = m.fpar = 0;
+  for (int i = threadIdx.x; i < ns; i += kThreads) m.mt.NE[i] = S.NE[i];
+  for (int i = threadIdx.x; i <= ns; i += kThreads) {
     m.mt.xoff[i] = S.xoff[i];
     m.mt.loff[i] = S.loff[i];
     m.mt.ioff[i] = S.ioff[i];
   }
-  if (lane == 0) {
-    for (int i = 0; i < kMaxSlots; ++i) mbar_init(&m.bar[i], 1);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kMaxSlots; ++i) {
+      mbar_init(&m.full[i], 1);
+      mbar_init(&m.empty[i], kNW);
+    }
+    m.flag[0] = 0;
+    m.flag[1] = 0;
     fence_mbar_init();
   }
-  __syncwarp();
+  __syncthreads();
   return m;
 }
 
+// Role of the warp within its CTA: the leader (role 0: producer, diagonal
+// factorisations, inverse steps) rotates with the CTA index, so that the
+// leaders of the CTAs sharing an SM sit on different SM sub-partitions.
+__device__ __forceinline__ int vwarp() {
+  return (int)(((threadIdx.x >> 5) + kNW - blockIdx.x % kNW) % kNW);
+}
+
 // Invalidate the mbarriers (before the shared memory is carved again).
-__device__ void warp_release_barriers(uint64_t* bar, int lane) {
-  __syncwarp();
-  if (lane == 0)
-    for (int i = 0; i < kMaxSlots; ++i) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[i])) : "memory");
-  __syncwarp();
+__device__ void cta_release_barriers(uint64_t* full) {
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 2 * kMaxSlots; ++i) mbar_inval(&full[i]);
+  __syncthreads();
 }
 
 template <typename T> struct Vec16;
@@ -366,6 +419,7 @@ __device__ __forceinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* 
 template <typename T, bool SET>
 __device__ __forceinline__ void rowgemm(const T* A, int lda, T* C, int ldc, int nrows, const T* Bp, int bst,
                                         int bsc, int nt, int ncols, int lane) {
+  if (nrows <= 0) return;
   switch ((nt + 3) >> 2) {
     case 1: rowgemm_nv<T, 1, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
     case 2: rowgemm_nv<T, 2, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
@@ -407,26 +461,26 @@ __device__ __forceinline__ void factor_issue(Ring<T>& r, FactorSeq& q, const Sol
 }
 
 // Envelope block Cholesky of the assembled A (FP64) with factor storage T, by
-// one warp. Block row k is formed in R and processed right-looking within the
-// row: for each block j of the envelope, X_j = R_j L_jj^-T is finalised (and
-// stored as L_kj), then every later block j' of the row, the diagonal one
-// included, is updated, R_j' -= X_j L_{j'j}^T (lane = column of j'; for the
-// diagonal block L_kj = X_j). L_kk = chol(R_kk) and its inverse are computed
-// in registers (lane = row). Panels are stored transposed, LT_k [W_k][N_k];
-// inverses [N_k][N_k]. Returns kFacOk, kFacPivot on a non-positive (or
+// the kNW warps of one CTA, each owning a contiguous range of the rows of the
+// current block row. Block row k is formed in R and processed right-looking:
+// for each block j of the envelope, X_j = R_j L_jj^-T is finalised (L_kj =
+// X_j), then the later off-diagonal blocks j' of the row are updated, R_j' -=
+// X_j L_{j'j}^T (lane = column of j'); these steps touch only the warp's own
+// rows. After a CTA barrier the diagonal block is updated with all X_j, and
+// warp 0 computes L_kk = chol(R_kk) and its inverse in registers (lane = row).
+// Panels are stored transposed, LT_k [W_k][N_k]; block k of the inverses holds
+// L_kk^-1 and its transpose. Returns kFacOk, kFacPivot on a non-positive (or
 // non-finite) pivot, or kFacTimeout if a copy did not complete.
 constexpr int kFacOk = 0, kFacPivot = 1, kFacTimeout = 2;
 
 template <typename T>
-__device__ int wfactor(const SimDev& S, T* LT, T* Linv, WarpSmem<T>& m, int lane) {
-  using V = typename Vec16<T>::type;
-  constexpr int kV = Vec16<T>::n;
+__device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
   const SolveMeta& mt = m.mt;
   const int nsub = S.n_sub, Sx = S.Sx;
   const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = vwarp();
   T* R = m.R;
-  Ring<T> rg{m.ring, m.bar, m.dl, kRing, 0u, 0u, m.ph, true};
-  bool badp = false;
+  Ring<T> rg{m.ring, m.full, m.empty, m.dl, kRing, 0u, 0u, m.ph, m.eph, m.used, m.fpar, true};
   for (int k = 0; k < nsub; ++k) {
     const int jl = jlo_of(k, Sx);
     const int base = mt.xoff[jl];
@@ -434,10 +488,12 @@ __device__ int wfactor(const SimDev& S, T* LT, T* Linv, WarpSmem<T>& m, int lane
     const int Wc = padded_width(mt, jl, k);
     const int Wp = row_stride<T>(Wc);
     const int pck = Wc - ((Nk + 3) & ~3);
-    // every chunk of this row refers to rows written before it
+    const int r0 = (w * Nk) / kNW, r1 = ((w + 1) * Nk) / kNW, nr = r1 - r0;
+    // every chunk of this row refers to rows written (and fenced) before it
     FactorSeq q{k, jl, jl};
-    while (!q.done() && (int)(rg.issued - rg.consumed) < rg.nslot) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
-    {  // R <- assembled blocks of A (diagonal, left, lower), zero elsewhere and in the padding
+    if (w == 0)
+      while (!q.done() && (int)(rg.issued - rg.consumed) < rg.nslot) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+    {  // own rows of R <- assembled blocks of A (diagonal, left, lower), zero elsewhere and in the padding
       const int I = k % Sx, J = k / Sx;
       int pc = 0;
       for (int i = jl; i <= k; ++i) {
@@ -446,26 +502,24 @@ __device__ int wfactor(const SimDev& S, T* LT, T* Linv, WarpSmem<T>& m, int lane
         if (i == k) blk = S.A + S.aoff[k];
         else if (I > 0 && i == k - 1) blk = S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)];        // [N_i][N_k]
         else if (J > 0 && i == k - Sx) blk = S.A + S.aoff[nsub + S.Sy * (Sx - 1) + (J - 1) * Sx + I];  // [N_i][N_k]
-        if (i == k) {  // lanes over columns, 8 rows of loads in flight
-          for (int r0 = 0; r0 < Nk; r0 += 8) {
-            double v[8];
+        if (i == k) {  // lanes over columns
+          double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (r0 + u < Nk && lane < Nk) ? blk[(r0 + u) * Nk + lane] : 0.0;
+          for (int u = 0; u < 8; ++u) v[u] = (u < nr && lane < Nk) ? blk[(r0 + u) * Nk + lane] : 0.0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (r0 + u < Nk && lane < Np) R[(r0 + u) * Wp + pc + lane] = (T)v[u];
-          }
-        } else if (blk) {  // A_{k,i}[r][c] = blk[c][r]: lanes over r read coalesced
+          for (int u = 0; u < 8; ++u)
+            if (u < nr && lane < Np) R[(r0 + u) * Wp + pc + lane] = (T)v[u];
+        } else if (blk) {  // A_{k,i}[r][c] = blk[c][r]: lanes over own rows read coalesced
           for (int c0 = 0; c0 < Np; c0 += 8) {
             double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (c0 + u < Ni && lane < Nk) ? blk[(c0 + u) * Nk + lane] : 0.0;
+            for (int u = 0; u < 8; ++u) v[u] = (c0 + u < Ni && lane < nr) ? blk[(c0 + u) * Nk + r0 + lane] : 0.0;
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (c0 + u < Np && lane < Nk) R[lane * Wp + pc + c0 + u] = (T)v[u];
+              if (c0 + u < Np && lane < nr) R[(r0 + lane) * Wp + pc + c0 + u] = (T)v[u];
           }
         } else {
-          for (int r = 0; r < Nk; ++r)
+          for (int r = r0; r < r1; ++r)
             if (lane < Np) R[r * Wp + pc + lane] = T(0);
         }
         pc += Np;
@@ -473,102 +527,124 @@ __device__ int wfactor(const SimDev& S, T* LT, T* Linv, WarpSmem<T>& m, int lane
     }
     __syncwarp();
     T* LTk = LT + mt.loff[k];
+    T* Rw = R + r0 * Wp;
     int pcj = 0;
     for (int j = jl; j < k; ++j) {
       const int Nj = mt.NE[j];
       const int Njp4 = (Nj + 3) & ~3;
-      {  // (1) X_j = R_j L_jj^-T (in place); B = (L_jj^-1)^T
+      {  // X_j = R_j L_jj^-T on own rows (in place); B = (L_jj^-1)^T
         const T* LiT = ring_wait<T>(rg);
-        rowgemm<T, true>(R + pcj, Wp, R + pcj, Wp, Nk, LiT, Nj, 1, Nj, Nj, lane);
-        if (!q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
-        ++rg.consumed;
-        // L_kj = X_j into the transposed panel (lanes over rows: coalesced)
-        const int gj = mt.xoff[j] - base;
-        if (lane < Nk)
-          for (int c = 0; c < Nj; ++c) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pcj + c];
+        rowgemm<T, true>(Rw + pcj, Wp, Rw + pcj, Wp, nr, LiT, Nj, 1, Nj, Nj, lane);
+        ring_release<T>(rg, lane, 1);
+        if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
       }
-      // (2) R_j' -= X_j L_{j'j}^T for j' in (j, k]
+      // R_j' -= X_j L_{j'j}^T for j' in (j, k), own rows
       int pcjp = pcj + Njp4;
-      for (int jp = j + 1; jp <= k; ++jp) {
+      for (int jp = j + 1; jp < k; ++jp) {
         const int Njp = mt.NE[jp];
-        if (jp < k) {
-          const long long off = mt.loff[jp] + (long long)(mt.xoff[j] - mt.xoff[jlo_of(jp, Sx)]) * Njp;
-          const T* Lc = ring_wait<T>(rg);  // [t][c'] = L_{j'j}[c'][t]
-          rowgemm<T, false>(R + pcj, Wp, R + pcjp, Wp, Nk, Lc, Njp, 1, Nj, Njp, lane);
-          if (!q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
-          ++rg.consumed;
-        } else {  // diagonal block: L_kj = X_j, B[t][c] = X_j[c][t]
-          rowgemm<T, false>(R + pcj, Wp, R + pcjp, Wp, Nk, R + pcj, 1, Wp, Nj, Njp, lane);
-        }
+        const T* Lc = ring_wait<T>(rg);  // [t][c'] = L_{j'j}[c'][t]
+        rowgemm<T, false>(Rw + pcj, Wp, Rw + pcjp, Wp, nr, Lc, Njp, 1, Nj, Njp, lane);
+        ring_release<T>(rg, lane, 1);
+        if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
         pcjp += (Njp + 3) & ~3;
       }
       pcj += Njp4;
     }
-    // diagonal block: Cholesky in registers, lane i holds row i
-    T v[32];
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      if (t >= Nk) break;
-      v[t] = (lane < Nk && t <= lane) ? R[lane * Wp + pck + t] : T(0);
-    }
-    T mydinv = T(1);
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      if (c >= Nk) break;
-      T piv = __shfl_sync(full, v[c], c);
-      if (!(piv > T(0)) || !isfinite((double)piv)) {
-        badp = true;
-        piv = T(1);
+    __syncthreads();  // every X_j of the row is final
+    {  // L_kj = X_j into the transposed panel (lanes over rows: coalesced), all warps
+      int pc = 0;
+      for (int j = jl; j < k; ++j) {
+        const int Nj = mt.NE[j], gj = mt.xoff[j] - base;
+        if (lane < Nk)
+          for (int c = w; c < Nj; c += kNW) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
+        pc += (Nj + 3) & ~3;
       }
-      const T d = sqrt(piv);
-      const T inv = T(1) / d;
-      if (lane == c) mydinv = inv;
-      const T lc = (lane == c) ? d : ((lane > c) ? v[c] * inv : v[c]);
-      v[c] = lc;
+    }
+    {  // R_kk -= sum_j X_j X_j^T on own rows; B[t][c] = X_j[c][t]
+      int pc = 0;
+      for (int j = jl; j < k; ++j) {
+        const int Nj = mt.NE[j];
+        rowgemm<T, false>(Rw + pc, Wp, Rw + pck, Wp, nr, R + pc, 1, Wp, Nj, Nk, lane);
+        pc += (Nj + 3) & ~3;
+      }
+    }
+    __syncthreads();
+    if (w == 0) {  // diagonal block: Cholesky in registers, lane i holds row i
+      bool badp = false;
+      T v[32];
 #pragma unroll
-      for (int t = c + 1; t < 32; ++t) {
+      for (int t = 0; t < 32; ++t) {
         if (t >= Nk) break;
-        const T ltc = __shfl_sync(full, lc, t);
-        if (lane >= t) v[t] = fma(-lc, ltc, v[t]);
+        v[t] = (lane < Nk && t <= lane) ? R[lane * Wp + pck + t] : T(0);
       }
-    }
-    // inverse, lane = column: y[r] = Linv[r][lane]
-    T y[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      if (r >= Nk) break;
-      T s = (r == lane) ? T(1) : T(0);
-#pragma unroll
-      for (int t = 0; t < r; ++t) s = fma(-__shfl_sync(full, v[t], r), y[t], s);
-      const T dinv = __shfl_sync(full, mydinv, r);
-      y[r] = (r >= lane) ? s * dinv : T(0);
-    }
-    T* Li = Linv + mt.ioff[k];
-    T* LiT = Li + ((Nk * Nk + 3) & ~3);
-    const int gk = mt.xoff[k] - base;
-    if (lane < Nk) {
+      T mydinv = T(1);
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         if (c >= Nk) break;
-        LTk[(size_t)(gk + c) * Nk + lane] = (c <= lane) ? v[c] : T(0);
+        T piv = __shfl_sync(full, v[c], c);
+        if (!(piv > T(0)) || !isfinite((double)piv)) {
+          badp = true;
+          piv = T(1);
+        }
+        const T d = sqrt(piv);
+        const T inv = T(1) / d;
+        if (lane == c) mydinv = inv;
+        const T lc = (lane == c) ? d : ((lane > c) ? v[c] * inv : v[c]);
+        v[c] = lc;
+#pragma unroll
+        for (int t = c + 1; t < 32; ++t) {
+          if (t >= Nk) break;
+          const T ltc = __shfl_sync(full, lc, t);
+          if (lane >= t) v[t] = fma(-lc, ltc, v[t]);
+        }
       }
+      // inverse, lane = column: y[r] = Linv[r][lane]
+      T y[32];
 #pragma unroll
       for (int r = 0; r < 32; ++r) {
         if (r >= Nk) break;
-        Li[r * Nk + lane] = y[r];
-        LiT[lane * Nk + r] = y[r];
+        T s = (r == lane) ? T(1) : T(0);
+#pragma unroll
+        for (int t = 0; t < r; ++t) s = fma(-__shfl_sync(full, v[t], r), y[t], s);
+        const T dinv = __shfl_sync(full, mydinv, r);
+        y[r] = (r >= lane) ? s * dinv : T(0);
       }
+      T* Li = Linv + mt.ioff[k];
+      T* LiT = Li + ((Nk * Nk + 3) & ~3);
+      const int gk = mt.xoff[k] - base;
+      if (lane < Nk) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          if (c >= Nk) break;
+          LTk[(size_t)(gk + c) * Nk + lane] = (c <= lane) ? v[c] : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          if (r >= Nk) break;
+          Li[r * Nk + lane] = y[r];
+          LiT[lane * Nk + r] = y[r];
+        }
+      }
+      if (__any_sync(full, badp) && lane == 0) m.flag[0] = 1;
     }
+    if (!rg.ok) m.flag[1] = 1;
     fence_proxy_async();  // the next rows copy these panels with the async proxy
-    __syncwarp();
-    const bool timed_out = !__all_sync(full, rg.ok);
-    if (__any_sync(full, badp) || timed_out) {
+    __syncthreads();
+    if (m.flag[0] | m.flag[1]) {
+      const int code = m.flag[1] ? kFacTimeout : kFacPivot;
       ring_drain<T>(rg);
       m.ph = rg.ph;
-      return timed_out ? kFacTimeout : kFacPivot;
+      m.eph = rg.eph;
+      m.used = rg.used;
+      m.fpar = rg.fpar;
+      __syncthreads();
+      return code;
     }
   }
   m.ph = rg.ph;
+  m.eph = rg.eph;
+  m.used = rg.used;
+  m.fpar = rg.fpar;
   return kFacOk;
 }
 
@@ -617,110 +693,147 @@ __device__ __forceinline__ void subst_issue(Ring<T>& r, SubstSeq& q, const Solve
 }
 __device__ __forceinline__ bool subst_done(const SubstSeq& q, int nsub) { return q.dir > 0 ? q.k >= nsub : q.k < 0; }
 
-// Solve L L^T out = in with the transposed panels (arithmetic in T), by one
-// warp; y and z live in shared memory. Returns false if a copy did not complete.
+// Solve L L^T out = in with the transposed panels (arithmetic in T) by the
+// CTA; y and z live in shared memory. The chunks of a block row are shared
+// out over the warps (chunk i of the row to warp i mod kNW, the inverse to
+// warp 0). Warp 0 produces: after every chunk it passes it tops the ring up,
+// each refill of a slot waiting for the release of the slot's previous chunk
+// (a chunk that warp 0 has passed and whose owner reaches it without crossing
+// a CTA barrier). Returns false if a copy did not complete.
 template <typename T>
-__device__ bool wsubstitute(const SimDev& S, const T* LT, const T* Linv, const double* in, double* out,
-                            WarpSmem<T>& m, int lane) {
+__device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const double* in, double* out,
+                            CtaSmem<T>& m) {
   const SolveMeta& mt = m.mt;
   const int nsub = S.n_sub, Sx = S.Sx, N = S.N;
+  const int lane = threadIdx.x & 31, w = vwarp();
   T* y = m.yz;
   T* z = y + N;
   T* tv = m.tv;
-  Ring<T> rg{m.R, m.bar, m.dl, m.n_sub_slots, 0u, 0u, m.ph, true};
-  for (int i = lane; i < N; i += 32) {
+  T* part = m.part;
+  Ring<T> rg{m.R, m.full, m.empty, m.dl, m.n_sub_slots, 0u, 0u, m.ph, m.eph, m.used, m.fpar, true};
+  SubstSeq q = subst_begin(mt, Sx, 0, 1);
+  auto refill = [&]() {
+    if (w == 0)
+      while (!subst_done(q, nsub) && (int)(rg.issued - rg.consumed) < rg.nslot)
+        subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+  };
+  for (int i = threadIdx.x; i < N; i += kThreads) {
     y[i] = (T)in[i];
     z[i] = T(0);
   }
-  SubstSeq q = subst_begin(mt, Sx, 0, 1);
-  while (!subst_done(q, nsub) && (int)(rg.issued - rg.consumed) < rg.nslot) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
-  __syncwarp();
+  refill();
+  __syncthreads();
   // forward: y_k = L_kk^-1 (in_k - sum_j L_kj y_j)
   for (int k = 0; k < nsub; ++k) {
     const int jl = jlo_of(k, Sx);
     const int Nk = mt.NE[k], xk = mt.xoff[k];
-    T a0 = (lane < Nk) ? y[xk + lane] : T(0), a1 = T(0);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     for (int j = jl; j < k; ++j) {
-      const int Nj = mt.NE[j];
-      const T* P = ring_wait<T>(rg);  // [g][c]
-      const T* yj = y + mt.xoff[j];
-      if (lane < Nk) {
-        T a2 = T(0), a3 = T(0);
-        int g = 0;
-        for (; g + 3 < Nj; g += 4) {
-          a0 = fma(-P[g * Nk + lane], yj[g], a0);
-          a1 = fma(-P[(g + 1) * Nk + lane], yj[g + 1], a1);
-          a2 = fma(-P[(g + 2) * Nk + lane], yj[g + 2], a2);
-          a3 = fma(-P[(g + 3) * Nk + lane], yj[g + 3], a3);
+      if (((j - jl) % kNW) != w) {
+        ring_skip<T>(rg);
+      } else {
+        const int Nj = mt.NE[j];
+        const T* P = ring_wait<T>(rg);  // [g][c]
+        const T* yj = y + mt.xoff[j];
+        if (lane < Nk) {
+          int g = 0;
+          for (; g + 3 < Nj; g += 4) {
+            a0 = fma(-P[g * Nk + lane], yj[g], a0);
+            a1 = fma(-P[(g + 1) * Nk + lane], yj[g + 1], a1);
+            a2 = fma(-P[(g + 2) * Nk + lane], yj[g + 2], a2);
+            a3 = fma(-P[(g + 3) * Nk + lane], yj[g + 3], a3);
+          }
+          for (; g < Nj; ++g) a0 = fma(-P[g * Nk + lane], yj[g], a0);
         }
-        for (; g < Nj; ++g) a0 = fma(-P[g * Nk + lane], yj[g], a0);
-        a1 += a2 + a3;
+        ring_release<T>(rg, lane, kNW);
       }
-      ring_release_sync();
-      if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
-      ++rg.consumed;
+      refill();
     }
-    const T* LiT = ring_wait<T>(rg);
-    if (lane < Nk) tv[lane] = a0 + a1;
-    __syncwarp();
-    T yk = T(0), yk1 = T(0);
-    if (lane < Nk) {  // y_k[c] = sum_{t <= c} Linv[c][t] tv[t]
-      int t = 0;
-      for (; t + 1 <= lane; t += 2) {
-        yk = fma(LiT[t * Nk + lane], tv[t], yk);
-        yk1 = fma(LiT[(t + 1) * Nk + lane], tv[t + 1], yk1);
+    part[w * 32 + lane] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (w == 0) {
+      const T* LiT = ring_wait<T>(rg);
+      if (lane < Nk) {
+        T t = y[xk + lane];
+#pragma unroll
+        for (int u = 0; u < kNW; ++u) t += part[u * 32 + lane];
+        tv[lane] = t;
       }
-      if (t <= lane) yk = fma(LiT[t * Nk + lane], tv[t], yk);
-      yk += yk1;
+      __syncwarp();
+      T yk = T(0), yk1 = T(0);
+      if (lane < Nk) {  // y_k[c] = sum_{t <= c} Linv[c][t] tv[t]
+        int t = 0;
+        for (; t + 1 <= lane; t += 2) {
+          yk = fma(LiT[t * Nk + lane], tv[t], yk);
+          yk1 = fma(LiT[(t + 1) * Nk + lane], tv[t + 1], yk1);
+        }
+        if (t <= lane) yk = fma(LiT[t * Nk + lane], tv[t], yk);
+        yk += yk1;
+      }
+      ring_release<T>(rg, lane, kNW);
+      if (lane < Nk) y[xk + lane] = yk;
+    } else {
+      ring_skip<T>(rg);
     }
-    ring_release_sync();
-    if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
-    ++rg.consumed;
-    if (lane < Nk) y[xk + lane] = yk;
-    __syncwarp();
+    refill();
+    __syncthreads();
   }
   // backward: z_k = L_kk^-T (y_k - p_k), then p_j += L_kj^T z_k for j < k
   q = subst_begin(mt, Sx, nsub - 1, -1);
-  while (!subst_done(q, nsub) && (int)(rg.issued - rg.consumed) < rg.nslot) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
+  refill();
   for (int k = nsub - 1; k >= 0; --k) {
     const int jl = jlo_of(k, Sx);
     const int Nk = mt.NE[k], xk = mt.xoff[k];
-    const T* Li = ring_wait<T>(rg);
-    if (lane < Nk) tv[lane] = y[xk + lane] - z[xk + lane];
-    __syncwarp();
-    T zc = T(0);
-    if (lane < Nk) {
-      for (int r = lane; r < Nk; ++r) zc = fma(Li[r * Nk + lane], tv[r], zc);
+    if (w == 0) {
+      const T* Li = ring_wait<T>(rg);
+      if (lane < Nk) tv[lane] = y[xk + lane] - z[xk + lane];
+      __syncwarp();
+      T zc = T(0);
+      if (lane < Nk)
+        for (int r = lane; r < Nk; ++r) zc = fma(Li[r * Nk + lane], tv[r], zc);
+      ring_release<T>(rg, lane, kNW);
+      if (lane < Nk) z[xk + lane] = zc;
+    } else {
+      ring_skip<T>(rg);
     }
-    ring_release_sync();
-    if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
-    ++rg.consumed;
-    if (lane < Nk) z[xk + lane] = zc;
-    __syncwarp();
+    refill();
+    __syncthreads();
     const T* zk = z + xk;
     for (int j = jl; j < k; ++j) {
-      const int Nj = mt.NE[j];
-      const T* P = ring_wait<T>(rg);  // [g][c]
-      if (lane < Nj) {  // lane = g; rotated for even N_k
-        const int g = lane;
-        int c = (Nk & 1) ? 0 : g % Nk;
-        T a0 = T(0);
-        for (int u = 0; u < Nk; ++u) {
-          a0 = fma(P[g * Nk + c], zk[c], a0);
-          if (++c == Nk) c = 0;
+      if (((j - jl) % kNW) != w) {
+        ring_skip<T>(rg);
+      } else {
+        const int Nj = mt.NE[j];
+        const T* P = ring_wait<T>(rg);  // [g][c]
+        if (lane < Nj) {  // lane = g; rotated for even N_k
+          const int g = lane;
+          int c = (Nk & 1) ? 0 : g % Nk;
+          T a0 = T(0);
+          for (int u = 0; u < Nk; ++u) {
+            a0 = fma(P[g * Nk + c], zk[c], a0);
+            if (++c == Nk) c = 0;
+          }
+          z[mt.xoff[j] + g] += a0;
         }
-        z[mt.xoff[j] + g] += a0;
+        ring_release<T>(rg, lane, kNW);
       }
-      ring_release_sync();
-      if (!subst_done(q, nsub)) subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
-      ++rg.consumed;
+      refill();
     }
+    __syncthreads();
   }
-  __syncwarp();
-  for (int i = lane; i < N; i += 32) out[i] = (double)z[i];
-  __syncwarp();
+  for (int i = threadIdx.x; i < N; i += kThreads) out[i] = (double)z[i];
+  if (!rg.ok) m.flag[1] = 1;
   m.ph = rg.ph;
-  return __all_sync(0xffffffffu, rg.ok);
+  m.eph = rg.eph;
+  m.used = rg.used;
+  m.fpar = rg.fpar;
+  __syncthreads();
+  if (m.flag[1]) {
+    ring_drain<T>(rg);
+    __syncthreads();
+    return false;
+  }
+  return true;
 }
 
 // acc += sum_{c < n} a[c * sa] xs[c] with four chains (FP64).
@@ -738,14 +851,15 @@ __device__ __forceinline__ double dot_strided(const double* __restrict__ a, int 
   return (acc + a1) + (a2 + a3);
 }
 
-// r = b - A x with the block-sparse assembled A, in FP64, by one warp; x is
-// staged in the shared work area xs [N] (FP64).
-__device__ void wresidual(const SimDev& S, const SolveMeta& mt, const double* x, const double* b, double* r,
-                          double* xs, int lane) {
+// r = b - A x with the block-sparse assembled A, in FP64, by the CTA
+// (subdomain E to warp E mod kNW); x is staged in the shared work area xs [N].
+__device__ void cresidual(const SimDev& S, const SolveMeta& mt, const double* x, const double* b, double* r,
+                          double* xs) {
   const int Sx = S.Sx, Sy = S.Sy, nsub = S.n_sub;
-  for (int i = lane; i < S.N; i += 32) xs[i] = x[i];
-  __syncwarp();
-  for (int E = 0; E < nsub; ++E) {
+  const int lane = threadIdx.x & 31, w = vwarp();
+  for (int i = threadIdx.x; i < S.N; i += kThreads) xs[i] = x[i];
+  __syncthreads();
+  for (int E = w; E < nsub; E += kNW) {
     const int NE = mt.NE[E], x0 = mt.xoff[E];
     const int I = E % Sx, J = E / Sx;
     if (lane < NE) {
@@ -771,30 +885,62 @@ __device__ void wresidual(const SimDev& S, const SolveMeta& mt, const double* x,
       r[x0 + i] = b[x0 + i] - acc;
     }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
-// x = (L L^T)^-1 b, then `iters` refinement steps x += (L L^T)^-1 (b - A x)
-// with the residual in FP64. Returns false if a copy did not complete.
+// max over the CTA of v (every thread passes its partial); red: [kNW] doubles.
+__device__ __forceinline__ double cta_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = red[0];
+#pragma unroll
+  for (int u = 1; u < kNW; ++u) r = fmax(r, red[u]);
+  __syncthreads();
+  return r;
+}
+
+// x = (L L^T)^-1 b, then up to `iters` refinement steps x += (L L^T)^-1 (b - A x)
+// with the residual in FP64. The refinement stops once the next correction,
+// predicted from the contraction of the last two, ||dv_k|| min(1,
+// ||dv_k|| / ||dv_{k-1}||), is below kRefineTol ||x|| (max norms; ||dv_0|| :=
+// ||x_0||). Returns false if a copy did not complete.
+constexpr double kRefineTol = 1e-12;
+
 template <typename T>
-__device__ bool wsolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, WarpSmem<T>& m, int lane) {
-  if (!wsubstitute<T>(S, Lst, Linv, S.b, S.x, m, lane)) return false;
+__device__ bool csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
+  if (!csubstitute<T>(S, Lst, Linv, S.b, S.x, m)) return false;
+  double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < S.N; i += kThreads) mx = fmax(mx, fabs(S.x[i]));
+  double prev = cta_max(mx, red);
   for (int it = 0; it < iters; ++it) {
-    wresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz), lane);
-    if (!wsubstitute<T>(S, Lst, Linv, S.rv, S.dv, m, lane)) return false;
-    for (int i = lane; i < S.N; i += 32) S.x[i] += S.dv[i];
-    __syncwarp();
+    cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
+    if (!csubstitute<T>(S, Lst, Linv, S.rv, S.dv, m)) return false;
+    double mdv = 0.0;
+    mx = 0.0;
+    for (int i = threadIdx.x; i < S.N; i += kThreads) {
+      const double xi = S.x[i] + S.dv[i];
+      S.x[i] = xi;
+      mdv = fmax(mdv, fabs(S.dv[i]));
+      mx = fmax(mx, fabs(xi));
+    }
+    mdv = cta_max(mdv, red);
+    mx = cta_max(mx, red);
+    if (!(mdv * fmin(1.0, mdv / prev) > kRefineTol * mx)) break;  // also stops on 0/0
+    prev = mdv;
   }
   return true;
 }
 
-// FP32 factor (one warp per simulation): a simulation whose FP32
+// FP32 factor (one CTA per simulation): a simulation whose FP32
 // factorisation meets a non-positive pivot is marked for the FP64 kernel.
 constexpr int kStRetry64 = 1;
 
-__global__ void __launch_bounds__(32) k_wsolve32(const SimDev* __restrict__ sims, const int* __restrict__ active,
-                                                 int n_active, int iters) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kThreads, 4) k_csolve32(const SimDev* __restrict__ sims,
+                                                       const int* __restrict__ active, int n_active, int iters) {
   const int a = blockIdx.x;
   if (a >= n_active) return;
   const SimDev& S = sims[active[a]];
@@ -803,35 +949,35 @@ __global__ void __launch_bounds__(32) k_wsolve32(const SimDev* __restrict__ sims
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   float* Lf = reinterpret_cast<float*>(S.L);
   float* Lif = reinterpret_cast<float*>(S.Linv);
-  WarpSmem<float> m = warp_carve_and_load<float>(S, b, lane);
-  const int f = wfactor<float>(S, Lf, Lif, m, lane);
+  CtaSmem<float> m = cta_carve_and_load<float>(S, b);
+  const int f = cfactor<float>(S, Lf, Lif, m);
   if (f == kFacOk) {
-    if (!wsolve_refine<float>(S, Lf, Lif, iters, m, lane) && lane == 0) S.status[0] = kStTimeout;
-  } else if (lane == 0) {
+    if (!csolve_refine<float>(S, Lf, Lif, iters, m) && threadIdx.x == 0) S.status[0] = kStTimeout;
+  } else if (threadIdx.x == 0) {
     S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
   }
 }
 
 // FP64 factor. only_retry: process only the simulations marked by the FP32 kernel.
-__global__ void __launch_bounds__(32) k_wsolve64(const SimDev* __restrict__ sims, const int* __restrict__ active,
-                                                 int n_active, int iters, int only_retry) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kThreads) k_csolve64(const SimDev* __restrict__ sims,
+                                                       const int* __restrict__ active, int n_active, int iters,
+                                                       int only_retry) {
   const int a = blockIdx.x;
   if (a >= n_active) return;
   const SimDev& S = sims[active[a]];
   const int st = S.status[0];
   if (only_retry ? st != kStRetry64 : st != kStOk) return;
-  __syncwarp();
-  if (lane == 0) S.status[0] = kStOk;
+  __syncthreads();
+  if (threadIdx.x == 0) S.status[0] = kStOk;
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
-  WarpSmem<double> m = warp_carve_and_load<double>(S, b, lane);
-  const int f = wfactor<double>(S, S.L, S.Linv, m, lane);
+  CtaSmem<double> m = cta_carve_and_load<double>(S, b);
+  const int f = cfactor<double>(S, S.L, S.Linv, m);
   if (f != kFacOk) {
-    if (lane == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
+    if (threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  if (!wsolve_refine<double>(S, S.L, S.Linv, iters, m, lane) && lane == 0) S.status[0] = kStTimeout;
+  if (!csolve_refine<double>(S, S.L, S.Linv, iters, m) && threadIdx.x == 0) S.status[0] = kStTimeout;
 }
 
 // ---------------------------------------------------------------- static scratch
@@ -864,32 +1010,31 @@ __global__ void k_noalloc_tables(SimDev S) {
   S.status[0] = kStOk;
 }
 
-__global__ void __launch_bounds__(32) k_wsolve_static(SimDev S, int mode, int iters) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, int iters) {
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   if (mode == 1) {
     float* Lf = reinterpret_cast<float*>(S.L);
     float* Lif = reinterpret_cast<float*>(S.Linv);
-    WarpSmem<float> mf = warp_carve_and_load<float>(S, b, lane);
-    const int f = wfactor<float>(S, Lf, Lif, mf, lane);
+    CtaSmem<float> mf = cta_carve_and_load<float>(S, b);
+    const int f = cfactor<float>(S, Lf, Lif, mf);
     if (f == kFacOk) {
-      if (!wsolve_refine<float>(S, Lf, Lif, iters, mf, lane) && lane == 0) S.status[0] = kStTimeout;
+      if (!csolve_refine<float>(S, Lf, Lif, iters, mf) && threadIdx.x == 0) S.status[0] = kStTimeout;
       return;
     }
     if (f == kFacTimeout) {
-      if (lane == 0) S.status[0] = kStTimeout;
+      if (threadIdx.x == 0) S.status[0] = kStTimeout;
       return;
     }
-    warp_release_barriers(mf.bar, lane);
+    cta_release_barriers(mf.full);
   }
-  WarpSmem<double> md = warp_carve_and_load<double>(S, b, lane);
-  const int f = wfactor<double>(S, S.L, S.Linv, md, lane);
+  CtaSmem<double> md = cta_carve_and_load<double>(S, b);
+  const int f = cfactor<double>(S, S.L, S.Linv, md);
   if (f != kFacOk) {
-    if (lane == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
+    if (threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  if (!wsolve_refine<double>(S, S.L, S.Linv, iters, md, lane) && lane == 0) S.status[0] = kStTimeout;
+  if (!csolve_refine<double>(S, S.L, S.Linv, iters, md) && threadIdx.x == 0) S.status[0] = kStTimeout;
 }
 
 }  // namespace
@@ -912,7 +1057,7 @@ static cudaError_t set_smem(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// One warp (one CTA) per simulation; the CTAs spread over the SMs, as many
+// One CTA of kNW warps per simulation; the CTAs spread over the SMs, as many
 // per SM as their shared memory allows.
 cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
                               const SolveShape& sh, cudaStream_t st) {
@@ -920,12 +1065,12 @@ cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_activ
   if (n_active <= 0) return cudaSuccess;
   if (mode == 1) {
     const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
-    if ((e = set_smem((const void*)k_wsolve32, s32)) != cudaSuccess) return e;
-    k_wsolve32<<<n_active, 32, s32, st>>>(sims, active, n_active, iters);
+    if ((e = set_smem((const void*)k_csolve32, s32)) != cudaSuccess) return e;
+    k_csolve32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
   }
   const size_t s64 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(double));
-  if ((e = set_smem((const void*)k_wsolve64, s64)) != cudaSuccess) return e;
-  k_wsolve64<<<n_active, 32, s64, st>>>(sims, active, n_active, iters, mode == 1 ? 1 : 0);
+  if ((e = set_smem((const void*)k_csolve64, s64)) != cudaSuccess) return e;
+  k_csolve64<<<n_active, kThreads, s64, st>>>(sims, active, n_active, iters, mode == 1 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1002,12 +1147,12 @@ extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double*
     return LRBMS_E_CUDA;
   k_noalloc_tables<<<1, 1, 0, st>>>(S);
   const int mode = solver == LRBMS_SOLVE_MIXED ? 1 : 0;
-  const int iters = refine_iters > 0 ? refine_iters : (mode == 1 ? 4 : 1);
+  const int iters = refine_iters > 0 ? refine_iters : (mode == 1 ? 6 : 1);
   const size_t smem = solve_smem_bytes(n_sub, panel_words, max_w, (int)N, sizeof(double));
   if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_wsolve_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      cudaFuncSetAttribute(k_csolve_static, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return LRBMS_E_BUDGET;
-  k_wsolve_static<<<1, 32, smem, st>>>(S, mode, iters);
+  k_csolve_static<<<1, kThreads, smem, st>>>(S, mode, iters);
   if (cudaGetLastError() != cudaSuccess) return LRBMS_E_CUDA;
   int status = 0;
   if (cudaMemcpyAsync(&status, base + o_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

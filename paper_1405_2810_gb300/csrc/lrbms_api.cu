@@ -150,7 +150,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   ctx->device = cfg->device;
   ctx->precision = cfg->precision;
   ctx->solver = cfg->solver;
-  ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 4 : 1);
+  ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 6 : 1);
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete ctx;
