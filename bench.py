@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 
 METRIC = "Batched LRBMS online steps/s and p99 step latency vs plain FP64 GPU path"
 FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA loop: 1.19)
+FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop/clk x 2.07 GHz
 
 
 def parse_args():
@@ -192,9 +193,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ algorithmic work
-def solve_flops(N_E, Sx: int, refine: int = 1) -> float:
-    """FP64 flops of the envelope block Cholesky, the two substitutions and the
-    refinement, as implemented (per simulation)."""
+def solve_flops(N_E, Sx: int) -> tuple:
+    """Flops of the reduced solve per simulation, as implemented: the envelope
+    block Cholesky (with the products by the diagonal inverses), one forward
+    and backward substitution pair, and one FP64 residual b - A x."""
     n = len(N_E)
     xoff = [0]
     for v in N_E:
@@ -216,13 +218,12 @@ def solve_flops(N_E, Sx: int, refine: int = 1) -> float:
         W = xoff[k + 1] - xoff[jl]
         subst += 2.0 * 2.0 * N_E[k] * (W - N_E[k]) + 2.0 * N_E[k] * (N_E[k] + 1)
     nnz = sum(int(v) ** 2 for v in N_E)
-    I = lambda e: e % Sx  # noqa: E731
     for e in range(n):
-        if I(e) < Sx - 1 and e + 1 < n:
+        if e % Sx < Sx - 1 and e + 1 < n:
             nnz += 2 * N_E[e] * N_E[e + 1]
         if e + Sx < n:
             nnz += 2 * N_E[e] * N_E[e + Sx]
-    return fl + subst * (1 + refine) + refine * 2.0 * nnz
+    return fl, subst, 2.0 * nnz
 
 
 def stream_bytes(N_E, Sx: int, cells: int, M: int, elem: int) -> dict:
@@ -389,6 +390,11 @@ def main():
     plain = n1 / (time.perf_counter() - t0)
     L.lrbms_destroy(ctx1)
 
+    # ---- refinement steps actually taken (last step of every simulation)
+    info = np.array([L.lrbms_get_field(ctx, i, L.FIELD_SOLVE_INFO, dtype=np.int32) for i in ids])
+    refine_mean = float(info[:, 0].mean())
+    fp64_redos = int(info[:, 1].sum())
+
     # ---- roofline of the dominant phase
     names = L.PHASES
     dom = int(np.argmax(phase_ms))
@@ -396,11 +402,26 @@ def main():
     cells = (a.n // a.S) ** 2
     elem = 8 if a.precision == "fp64" else 4
     if names[dom] == "solve":
-        work = sum(solve_flops(list(sz), Sx) for sz in sizes) * n_copies * 1e-12
-        achieved = work / (phase_ms[dom] / 1000.0)
-        roof = {"bound": "alu", "kernel": "k_chol_solve", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit counts and clock)"}
+        # factor + (1 + refine) substitution pairs in the factor's type, refine FP64 residuals
+        f_lo = f_hi = 0.0
+        for sz in sizes:
+            fac, sub, res = solve_flops(list(sz), Sx)
+            lo = fac + (1.0 + refine_mean) * sub
+            if a.solver == "mixed":
+                f_lo += lo * n_copies
+            else:
+                f_hi += lo * n_copies
+            f_hi += refine_mean * res * n_copies
+        t_solve = phase_ms[dom] / 1000.0
+        t_min = f_lo / (FP32_PEAK_TFLOPS * 1e12) + f_hi / (FP64_PEAK_TFLOPS * 1e12)
+        work = (f_lo + f_hi) * 1e-12
+        roof = {"bound": "alu", "kernel": "k_csolve32" if a.solver == "mixed" else "k_csolve64",
+                "achieved": work / t_solve, "peak": work / t_min, "unit": "TFLOP/s", "frac": t_min / t_solve,
+                "traffic": None,
+                "peak_source": ("time-weighted ALU peak of the solve's FP32 and FP64 flops: "
+                                "FP32 152 SMs x 256 flop/clk, FP64 152 SMs x 4 flop/clk, at 2.07 GHz "
+                                "(recipe unit counts and clock)"),
+                "flops_fp32": f_lo, "flops_fp64": f_hi}
     else:
         sb = [stream_bytes(list(sz), Sx, cells, 8, elem) for sz in sizes]
         key = names[dom] if names[dom] in sb[0] else None
@@ -433,7 +454,8 @@ def main():
                        "basis_sizes_mean_N": N_mean, "precision": a.precision, "solver": a.solver,
                        "l2": f"inputs larger than L2: {used / 2**30:.1f} GiB resident",
                        "p50_step_ms": p50, "p99_step_ms": p99, "sims_ok": n_ok,
-                       "offline_build_s": t_build, "parallelism": f"replicas x{world}"},
+                       "offline_build_s": t_build, "parallelism": f"replicas x{world}",
+                       "refine_steps_mean": refine_mean, "fp64_redos": fp64_redos},
             "phases_ms": {n: float(v) for n, v in zip(names, phase_ms)},
             "roofline": roof,
             "plain_fp64_single_sim_steps_per_s": plain,

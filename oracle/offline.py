@@ -15,7 +15,7 @@ the offline/online decomposition.
   subdomain's basis by the Gram-Schmidt orthonormalised restriction of the
   worst-approximated snapshot (L2(E) inner product, two passes, rejection below
   1e-10 of the snapshot's local norm; reading R14). The constant function of
-  every subdomain is the first basis function (reading R12). A plain
+  every subdomain is the first basis function (reading R16). A plain
   snapshot variant (fixed random parameters, then truncation to given local
   sizes) serves the batched workloads.
 * Components (Section 4.4): b_q = Phi^T K_vc(Lambda^q) Phi (volume and

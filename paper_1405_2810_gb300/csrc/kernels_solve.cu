@@ -903,22 +903,32 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
 }
 
 // x = (L L^T)^-1 b, then up to `iters` refinement steps x += (L L^T)^-1 (b - A x)
-// with the residual in FP64. The refinement stops once the next correction,
-// predicted from the contraction of the last two, ||dv_k|| min(1,
-// ||dv_k|| / ||dv_{k-1}||), is below kRefineTol ||x|| (max norms; ||dv_0|| :=
-// ||x_0||). Returns false if a copy did not complete.
+// with the residual in FP64 (max norms throughout; ||dv_0|| := ||x_0||). The
+// refinement stops
+//  - converged: once the next correction, predicted from the contraction of
+//    the last two, ||dv_k|| min(1, ||dv_k|| / ||dv_{k-1}||), is below
+//    kRefineTol ||x||;
+//  - at the rounding floor: once a correction no longer halves and is below
+//    kFloorTol ||x||;
+//  - stalled: a correction that no longer halves above that level (the
+//    factor is too inexact for this matrix; the FP32 kernel then hands the
+//    simulation to the FP64 one).
+// Returns kRefOk, kRefStalled or kRefTimeout (a copy did not complete).
 constexpr double kRefineTol = 1e-12;
+constexpr double kFloorTol = 1e-8;
+constexpr int kRefOk = 0, kRefStalled = 1, kRefTimeout = 2;
 
 template <typename T>
-__device__ bool csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
-  if (!csubstitute<T>(S, Lst, Linv, S.b, S.x, m)) return false;
+__device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
+  if (!csubstitute<T>(S, Lst, Linv, S.b, S.x, m)) return kRefTimeout;
   double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
   double mx = 0.0;
   for (int i = threadIdx.x; i < S.N; i += kThreads) mx = fmax(mx, fabs(S.x[i]));
   double prev = cta_max(mx, red);
+  int steps = 0, rc = kRefOk;
   for (int it = 0; it < iters; ++it) {
     cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
-    if (!csubstitute<T>(S, Lst, Linv, S.rv, S.dv, m)) return false;
+    if (!csubstitute<T>(S, Lst, Linv, S.rv, S.dv, m)) return kRefTimeout;
     double mdv = 0.0;
     mx = 0.0;
     for (int i = threadIdx.x; i < S.N; i += kThreads) {
@@ -929,10 +939,16 @@ __device__ bool csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int 
     }
     mdv = cta_max(mdv, red);
     mx = cta_max(mx, red);
-    if (!(mdv * fmin(1.0, mdv / prev) > kRefineTol * mx)) break;  // also stops on 0/0
+    steps = it + 1;
+    if (!(mdv * fmin(1.0, mdv / prev) > kRefineTol * mx)) break;  // converged (also on 0/0)
+    if (mdv > 0.5 * prev) {
+      if (mdv > kFloorTol * mx) rc = kRefStalled;
+      break;
+    }
     prev = mdv;
   }
-  return true;
+  if (threadIdx.x == 0 && S.info) S.info[0] = steps;
+  return rc;
 }
 
 // FP32 factor (one CTA per simulation): a simulation whose FP32
@@ -952,7 +968,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_csolve32(const SimDev* __restri
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
   const int f = cfactor<float>(S, Lf, Lif, m);
   if (f == kFacOk) {
-    if (!csolve_refine<float>(S, Lf, Lif, iters, m) && threadIdx.x == 0) S.status[0] = kStTimeout;
+    const int r = csolve_refine<float>(S, Lf, Lif, iters, m);
+    if (threadIdx.x == 0 && r != kRefOk) S.status[0] = r == kRefStalled ? kStRetry64 : kStTimeout;
   } else if (threadIdx.x == 0) {
     S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
   }
@@ -968,7 +985,10 @@ __global__ void __launch_bounds__(kThreads) k_csolve64(const SimDev* __restrict_
   const int st = S.status[0];
   if (only_retry ? st != kStRetry64 : st != kStOk) return;
   __syncthreads();
-  if (threadIdx.x == 0) S.status[0] = kStOk;
+  if (threadIdx.x == 0) {
+    S.status[0] = kStOk;
+    if (only_retry && S.info) S.info[1] += 1;
+  }
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<double> m = cta_carve_and_load<double>(S, b);
@@ -977,7 +997,7 @@ __global__ void __launch_bounds__(kThreads) k_csolve64(const SimDev* __restrict_
     if (threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  if (!csolve_refine<double>(S, S.L, S.Linv, iters, m) && threadIdx.x == 0) S.status[0] = kStTimeout;
+  if (csolve_refine<double>(S, S.L, S.Linv, iters, m) == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
 }
 
 // ---------------------------------------------------------------- static scratch
@@ -1019,8 +1039,9 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
     CtaSmem<float> mf = cta_carve_and_load<float>(S, b);
     const int f = cfactor<float>(S, Lf, Lif, mf);
     if (f == kFacOk) {
-      if (!csolve_refine<float>(S, Lf, Lif, iters, mf) && threadIdx.x == 0) S.status[0] = kStTimeout;
-      return;
+      const int r = csolve_refine<float>(S, Lf, Lif, iters, mf);
+      if (r == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
+      if (r != kRefStalled) return;
     }
     if (f == kFacTimeout) {
       if (threadIdx.x == 0) S.status[0] = kStTimeout;
@@ -1034,7 +1055,7 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
     if (threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  if (!csolve_refine<double>(S, S.L, S.Linv, iters, md) && threadIdx.x == 0) S.status[0] = kStTimeout;
+  if (csolve_refine<double>(S, S.L, S.Linv, iters, md) == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
 }
 
 }  // namespace

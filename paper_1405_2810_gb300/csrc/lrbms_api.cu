@@ -317,7 +317,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
   const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
   const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
-  const size_t o_status = L.add(4), o_steps = L.add(4);
+  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(8);
   (void)d_tot;
 
   const size_t aoffset = ctx->arena.alloc(L.total);
@@ -358,7 +358,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.A = (double*)P(o_A); d.L = (double*)P(o_L); d.Linv = (double*)P(o_Li);
   d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
   d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);
-  d.status = (int*)P(o_status); d.steps = (int*)P(o_steps);
+  d.status = (int*)P(o_status); d.steps = (int*)P(o_steps); d.info = (int*)P(o_info);
 
   cudaStream_t st = ctx->stream;
   auto cp = [&](void* dst, const void* src, size_t bytes) {
@@ -390,6 +390,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_theta), 0, 8 * lrbms::kMaxM, st));
   CK(cudaMemsetAsync(P(o_status), 0, 4, st));
   CK(cudaMemsetAsync(P(o_steps), 0, 4, st));
+  CK(cudaMemsetAsync(P(o_info), 0, 8, st));
   CK(cudaMemsetAsync(P(o_p), 0, 24 * (size_t)n_cells, st));
   CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
   CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
@@ -577,6 +578,7 @@ size_t lrbms_field_bytes(lrbms_ctx* ctx, int id, int field) {
     case LRBMS_FIELD_S: return 8 * (size_t)d.n_cells;
     case LRBMS_FIELD_DT: return 8;
     case LRBMS_FIELD_STATUS: return 4;
+    case LRBMS_FIELD_SOLVE_INFO: return 8;
     default: return 0;
   }
 }
@@ -602,6 +604,7 @@ int lrbms_get_field(lrbms_ctx* ctx, int id, int field, void* dst, size_t bytes) 
       break;
     case LRBMS_FIELD_DT: src = d.scal + 1; break;
     case LRBMS_FIELD_STATUS: src = d.status; break;
+    case LRBMS_FIELD_SOLVE_INFO: src = d.info; break;
     default: return fail(ctx, LRBMS_E_ARG, "unknown field");
   }
   CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));

@@ -33,7 +33,7 @@ LRBMS_DT_CFL = 0
 LRBMS_DT_FIXED = 1
 LRBMS_SOLVE_FP64 = 0
 LRBMS_SOLVE_MIXED = 1
-FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS = range(9)
+FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS, FIELD_SOLVE_INFO = range(10)
 
 EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offline_build",
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
