@@ -1,8 +1,10 @@
 // Per-cell and per-face kernels of the LRBMS online step:
-//   fit        partial sums of the normal equations of Eq. leastSquaresFit
+//   prepare    (at load) per-face coefficients of Definition 2 and 1/(phi|e|)
+//   fit        lambda(s^n) and f_w(s^n) per cell, and the partial sums of the
+//              normal equations of Eq. leastSquaresFit
 //   reconstruct p_E = Phi_E x_E (Algorithm 3, step 5(b))
 //   flux       face fluxes of Definition 2 (Eq. velocityDG), mobility lambda(s^n)
-//   cfl        per-tile minimum of the CFL bound phi|e| / (L_f * outflow_e)
+//   cfl        per-tile maximum of outflow_e / (phi|e|) (the CFL bound's inverse)
 //   transport  explicit upwind update of Definition 3 with P0 saturation
 //   finalize   time, cumulative boundary outflow and step counter
 // Every reduction uses a fixed tile partition and a fixed order, so a
@@ -33,11 +35,6 @@ __device__ __forceinline__ void phase_mob(const SimDev& S, double s, double& lw,
     lo = (1.0 - s) * S.inv_eta_o;
   }
 }
-__device__ __forceinline__ double total_mob(const SimDev& S, double s) {
-  double lw, lo;
-  phase_mob(S, s, lw, lo);
-  return lw + lo;
-}
 // Eq. frationalFlow.
 __device__ __forceinline__ double frac_flow(const SimDev& S, double s) {
   double lw, lo;
@@ -49,8 +46,8 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_min(double v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -66,22 +63,85 @@ __device__ double block_sum(double v, double* red) {
     for (int i = 0; i < nw; ++i) r += red[i];
   return r;
 }
-__device__ double block_min(double v, double* red) {
+__device__ double block_max(double v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_min(v);
+  v = warp_max(v);
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double r = DBL_MAX;
+  double r = 0.0;
   if (threadIdx.x == 0)
-    for (int i = 0; i < nw; ++i) r = fmin(r, red[i]);
+    for (int i = 0; i < nw; ++i) r = fmax(r, red[i]);
   return r;
 }
 
+// ------------------------------------------------------------------ prepare
+// Per-face coefficients of Definition 2 (they depend on the permeability
+// only): interior faces F = -(c0 lambda_1 dp_1 + c1 lambda_2 dp_2) + c2 [p],
+// with c0 = |f| (2/h_n) tau_1 kappa_1, c1 = |f| (2/h_n) tau_2 kappa_2 (mean
+// weights of reading R3) and c2 = sigma_f (|f| sigma_f / h_f = sigma_f in 2D);
+// Dirichlet faces: c0 = |f| (2/h_n) kappa_e, c2 = c_pen kappa_e, c1 = p_D;
+// Neumann faces: c0 = c2 = 0, c1 = |f| v_N. Per cell: 1/(phi_e |e|).
+__global__ void k_prepare(const SimDev* __restrict__ sp) {
+  const SimDev& S = *sp;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = i0; e < S.n_cells; e += stride) S.inv_pv[e] = 1.0 / (S.poro[e] * S.vol);
+  const int nx = S.nx, ny = S.ny, nf = S.n_faces;
+  for (int f = i0; f < nf; f += stride) {
+    int e1 = -1, e2 = -1, bidx = -1;
+    double flen, dscale;
+    if (f < S.nxf) {
+      const int j = f / (nx + 1), i = f - j * (nx + 1);
+      if (i > 0) e1 = j * nx + i - 1;
+      if (i < nx) e2 = j * nx + i;
+      if (i == 0) bidx = j;
+      if (i == nx) bidx = ny + j;
+      flen = S.hy;
+      dscale = 2.0 / S.hx;
+    } else {
+      const int g = f - S.nxf;
+      const int j = g / nx, i = g - j * nx;
+      if (j > 0) e1 = (j - 1) * nx + i;
+      if (j < ny) e2 = j * nx + i;
+      if (j == 0) bidx = 2 * ny + i;
+      if (j == ny) bidx = 2 * ny + nx + i;
+      flen = S.hx;
+      dscale = 2.0 / S.hy;
+    }
+    double c0, c1, c2;
+    if (e1 >= 0 && e2 >= 0) {
+      const double k1 = S.perm[e1], k2 = S.perm[e2];
+      const double ks = k1 + k2;
+      const double t1 = (S.swapped ? k2 : k1) / ks;
+      const double t2 = (S.swapped ? k1 : k2) / ks;
+      c0 = flen * dscale * t1 * k1;
+      c1 = flen * dscale * t2 * k2;
+      c2 = S.c_pen * 2.0 * k1 * k2 / ks;
+    } else {
+      const int e = (e1 >= 0) ? e1 : e2;
+      if (S.bc_type[bidx] == 1) {
+        const double ke = S.perm[e];
+        c0 = flen * dscale * ke;
+        c1 = S.p_D[bidx];
+        c2 = S.c_pen * ke;
+      } else {
+        c0 = 0.0;
+        c1 = flen * S.v_N[bidx];
+        c2 = 0.0;
+      }
+    }
+    S.fcoef[f] = c0;
+    S.fcoef[(size_t)nf + f] = c1;
+    S.fcoef[2 * (size_t)nf + f] = c2;
+  }
+}
+
 // ------------------------------------------------------------------ fit
-// r_q = sum_e Lambda^q_e lambda(s_e) per tile. With the threshold profiles of
-// Algorithm 2 (Lambda^q_e = lambda(1) if q >= k_e else lambda(0)) the cells are
-// binned by k_e and r follows from the bin sums.
+// lambda(s_e) and f_w(s_e) for the step (stored for the flux and transport
+// kernels) and r_q = sum_e Lambda^q_e lambda(s_e) per tile. With the threshold
+// profiles of Algorithm 2 (Lambda^q_e = lambda(1) if q >= k_e else
+// lambda(0)) the cells are binned by k_e and r follows from the bin sums.
 __global__ void k_fit(const SimDev* __restrict__ sims, const int* __restrict__ active) {
   const SimDev& S = sims[active[blockIdx.y]];
   const int tile = blockIdx.x;
@@ -94,11 +154,23 @@ __global__ void k_fit(const SimDev* __restrict__ sims, const int* __restrict__ a
   const int e0 = tile * kCellTile;
   const int e1 = min(e0 + kCellTile, S.n_cells);
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const double lam = total_mob(S, s[e]);
+    double lw, lo;
+    phase_mob(S, s[e], lw, lo);
+    const double lam = lw + lo;
+    S.lam[e] = lam;
+    S.fw[e] = lw / lam;  // Eq. frationalFlow
     if (S.prof_mode == 0) {
-      const int k = S.prof_idx[e];  // 1-based profile index in 2..M
-#pragma unroll
-      for (int q = 0; q < kMaxM; ++q) acc[q] += (q == k - 1) ? lam : 0.0;
+      switch (S.prof_idx[e] - 1) {  // one add: the cell's bin
+#define LRBMS_BIN(q) \
+  case q:            \
+    acc[q] += lam;   \
+    break;
+        LRBMS_BIN(0) LRBMS_BIN(1) LRBMS_BIN(2) LRBMS_BIN(3) LRBMS_BIN(4) LRBMS_BIN(5) LRBMS_BIN(6)
+        LRBMS_BIN(7) LRBMS_BIN(8) LRBMS_BIN(9) LRBMS_BIN(10) LRBMS_BIN(11) LRBMS_BIN(12) LRBMS_BIN(13)
+        LRBMS_BIN(14) LRBMS_BIN(15)
+#undef LRBMS_BIN
+        default: break;
+      }
     } else {
 #pragma unroll
       for (int q = 0; q < kMaxM; ++q)
@@ -176,21 +248,19 @@ __global__ void k_reconstruct32(const SimDev* __restrict__ sims, const int* __re
 
 // ------------------------------------------------------------------ flux
 // Definition 2 for P1 pressure and P0 coefficients: the normal gradient is
-// constant per cell and the jump is linear along the face, so
-//   F = |f| ( -(tau1 l1 k1 dn p1 + tau2 l2 k2 dn p2) ) + sigma_f [p](midpoint)
-// with sigma_f/h_f * |f| = sigma_f in 2D (h_f = |f|).
+// constant per cell and the jump is linear along the face, so with the
+// coefficients of k_prepare
+//   F = -(c0 lambda_1 dp_1 + c1 lambda_2 dp_2) + c2 [p](midpoint),
+// dp the normal-direction dof of each cell (the gradient times h_n / 2).
 __global__ void k_flux(const SimDev* __restrict__ sims, const int* __restrict__ active) {
   const SimDev& S = sims[active[blockIdx.y]];
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= S.n_faces || S.status[0] != kStOk) return;
-  const double* s = cur_s(S);
+  const double* lam = S.lam;
   const double* p0 = S.p;
-  const double* p1 = S.p + S.n_cells;
-  const double* p2 = S.p + 2 * (size_t)S.n_cells;
-  const int nx = S.nx, ny = S.ny;
+  const int nx = S.nx, ny = S.ny, nf = S.n_faces;
   int e1 = -1, e2 = -1, bidx = -1;
   bool xface;
-  double flen, dscale;
   if (f < S.nxf) {
     xface = true;
     const int j = f / (nx + 1), i = f - j * (nx + 1);
@@ -198,8 +268,6 @@ __global__ void k_flux(const SimDev* __restrict__ sims, const int* __restrict__ 
     if (i < nx) e2 = j * nx + i;
     if (i == 0) bidx = j;
     if (i == nx) bidx = ny + j;
-    flen = S.hy;
-    dscale = 2.0 / S.hx;
   } else {
     xface = false;
     const int g = f - S.nxf;
@@ -208,34 +276,22 @@ __global__ void k_flux(const SimDev* __restrict__ sims, const int* __restrict__ 
     if (j < ny) e2 = j * nx + i;
     if (j == 0) bidx = 2 * ny + i;
     if (j == ny) bidx = 2 * ny + nx + i;
-    flen = S.hx;
-    dscale = 2.0 / S.hy;
   }
-  const double* pt = xface ? p1 : p2;  // tangential-free coefficient along the normal
+  const double* pt = S.p + (xface ? 1 : 2) * (size_t)S.n_cells;  // normal-direction dof
+  const double c0 = S.fcoef[f], c1 = S.fcoef[(size_t)nf + f], c2 = S.fcoef[2 * (size_t)nf + f];
   double F;
   if (e1 >= 0 && e2 >= 0) {
-    const double k1 = S.perm[e1], k2 = S.perm[e2];
-    const double ks = k1 + k2;
-    const double t1 = (S.swapped ? k2 : k1) / ks;
-    const double t2 = (S.swapped ? k1 : k2) / ks;
-    const double l1 = total_mob(S, s[e1]), l2 = total_mob(S, s[e2]);
-    const double g1 = dscale * pt[e1], g2 = dscale * pt[e2];
-    const double mean = t1 * l1 * k1 * g1 + t2 * l2 * k2 * g2;
     const double jump = (p0[e1] + pt[e1]) - (p0[e2] - pt[e2]);
-    const double sig = S.c_pen * 2.0 * k1 * k2 / ks;
-    F = -flen * mean + sig * jump;
+    F = -(c0 * lam[e1] * pt[e1] + c1 * lam[e2] * pt[e2]) + c2 * jump;
   } else {
     const int e = (e1 >= 0) ? e1 : e2;
     const double sgn = (e1 >= 0) ? 1.0 : -1.0;  // outward normal along +axis?
     double Fout;
     if (S.bc_type[bidx] == 1) {
-      const double ke = S.perm[e];
-      const double le = total_mob(S, s[e]);
-      const double gn = sgn * dscale * pt[e];
       const double pmid = p0[e] + sgn * pt[e];
-      Fout = -flen * le * ke * gn + S.c_pen * ke * (pmid - S.p_D[bidx]);
+      Fout = -c0 * lam[e] * (sgn * pt[e]) + c2 * (pmid - c1);
     } else {
-      Fout = flen * S.v_N[bidx];
+      Fout = c1;
     }
     F = sgn * Fout;
   }
@@ -260,24 +316,25 @@ __global__ void k_cfl(const SimDev* __restrict__ sims, const int* __restrict__ a
   if (tile >= S.n_tiles || S.status[0] != kStOk) return;
   const int e0 = tile * kCellTile;
   const int e1 = min(e0 + kCellTile, S.n_cells);
-  double m = DBL_MAX;
+  double m = 0.0;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     int fl, fr, fb, ft;
     cell_faces(S, e, fl, fr, fb, ft);
     const double out = fmax(-S.F[fl], 0.0) + fmax(S.F[fr], 0.0) + fmax(-S.F[fb], 0.0) +
                        fmax(S.F[ft], 0.0);
-    if (out > 0.0) m = fmin(m, S.poro[e] * S.vol / (S.Lf * out));
+    m = fmax(m, out * S.inv_pv[e]);
   }
   __shared__ double red[32];
-  const double r = block_min(m, red);
+  const double r = block_max(m, red);
   if (threadIdx.x == 0) S.cfl_part[tile] = r;
 }
 
+// Reading R12: dt = cfl min_e phi_e|e| / (L_f outflow_e) = cfl / (L_f max_e outflow_e / (phi_e|e|)).
 __device__ __forceinline__ double step_dt(const SimDev& S) {
   if (S.dt_mode == 1) return S.dt_fixed;
-  double m = DBL_MAX;
-  for (int t = 0; t < S.n_tiles; ++t) m = fmin(m, S.cfl_part[t]);
-  double dt = (m == DBL_MAX) ? DBL_MAX : S.cfl * m;
+  double m = 0.0;
+  for (int t = 0; t < S.n_tiles; ++t) m = fmax(m, S.cfl_part[t]);
+  double dt = (m > 0.0) ? S.cfl / (S.Lf * m) : DBL_MAX;
   if (S.dt_max > 0.0) dt = fmin(dt, S.dt_max);
   return dt;
 }
@@ -287,10 +344,13 @@ __device__ __forceinline__ double step_dt(const SimDev& S) {
 // (s|e1 if F >= 0, else s|e2; s_D on boundary inflow). Both cells of an
 // interior face evaluate G_f from identical operands, so it cancels exactly
 // in the total water volume.
-__device__ __forceinline__ double face_term_interior(const SimDev& S, const double* s, double F,
-                                                     int e1, int e2) {
-  const double su = (F >= 0.0) ? s[e1] : s[e2];
-  return F * frac_flow(S, su);
+__device__ __forceinline__ double face_term_interior(const double* fw, double F, int e1, int e2) {
+  return F * ((F >= 0.0) ? fw[e1] : fw[e2]);
+}
+// Boundary face with outward flux Fo: the cell's own f_w on outflow, f_w(s_D) on inflow.
+__device__ __forceinline__ double face_term_boundary(const SimDev& S, const double* fw, double Fo, int e,
+                                                     double sD) {
+  return Fo * ((Fo >= 0.0) ? fw[e] : frac_flow(S, sD));
 }
 
 __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restrict__ active) {
@@ -308,49 +368,42 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
   const int e1 = min(e0 + kCellTile, S.n_cells);
   double bout = 0.0;
   bool bad = !(dt > 0.0 && dt < DBL_MAX);
+  const double* fw = S.fw;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int j = e / nx, i = e - j * nx;
     int fl, fr, fb, ft;
     cell_faces(S, e, fl, fr, fb, ft);
-    double net = 0.0;
+    double net = 0.0, g;
     // left face: this cell is e2; outward flux -F
     if (i > 0) {
-      net -= face_term_interior(S, s, S.F[fl], e - 1, e);
+      net -= face_term_interior(fw, S.F[fl], e - 1, e);
     } else {
-      const double Fo = -S.F[fl];
-      const double su = (Fo >= 0.0) ? s[e] : S.s_D[j];
-      const double g = Fo * frac_flow(S, su);
+      g = face_term_boundary(S, fw, -S.F[fl], e, S.s_D[j]);
       net += g;
       bout += g;
     }
     if (i < nx - 1) {
-      net += face_term_interior(S, s, S.F[fr], e, e + 1);
+      net += face_term_interior(fw, S.F[fr], e, e + 1);
     } else {
-      const double Fo = S.F[fr];
-      const double su = (Fo >= 0.0) ? s[e] : S.s_D[ny + j];
-      const double g = Fo * frac_flow(S, su);
+      g = face_term_boundary(S, fw, S.F[fr], e, S.s_D[ny + j]);
       net += g;
       bout += g;
     }
     if (j > 0) {
-      net -= face_term_interior(S, s, S.F[fb], e - nx, e);
+      net -= face_term_interior(fw, S.F[fb], e - nx, e);
     } else {
-      const double Fo = -S.F[fb];
-      const double su = (Fo >= 0.0) ? s[e] : S.s_D[2 * ny + i];
-      const double g = Fo * frac_flow(S, su);
+      g = face_term_boundary(S, fw, -S.F[fb], e, S.s_D[2 * ny + i]);
       net += g;
       bout += g;
     }
     if (j < ny - 1) {
-      net += face_term_interior(S, s, S.F[ft], e, e + nx);
+      net += face_term_interior(fw, S.F[ft], e, e + nx);
     } else {
-      const double Fo = S.F[ft];
-      const double su = (Fo >= 0.0) ? s[e] : S.s_D[2 * ny + nx + i];
-      const double g = Fo * frac_flow(S, su);
+      g = face_term_boundary(S, fw, S.F[ft], e, S.s_D[2 * ny + nx + i]);
       net += g;
       bout += g;
     }
-    const double v = s[e] - dt / (S.poro[e] * S.vol) * net;
+    const double v = s[e] - dt * S.inv_pv[e] * net;
     if (!isfinite(v)) bad = true;
     sn[e] = v;
   }
@@ -421,6 +474,11 @@ void launch_sat_io(const SimDev* sims, const int* active, int n_active, const do
   if (dst) k_sat_out<<<dim3(16, n_active), 256, 0, st>>>(sims, active, dst);
 }
 
+void launch_prepare(const SimDev* sim, int n_items, cudaStream_t st) {
+  int blocks = (n_items + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_prepare<<<blocks, 256, 0, st>>>(sim);
+}
 void launch_fit(const SimDev* sims, const int* active, int n_active, int max_tiles,
                 cudaStream_t st) {
   k_fit<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);

@@ -310,6 +310,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_comp32 = mixed ? L.add(4 * Q * (size_t)a_tot) : 0;
   const size_t o_s = L.add(16 * (size_t)n_cells), o_p = L.add(24 * (size_t)n_cells);
   const size_t o_F = L.add(8 * (size_t)n_faces);
+  const size_t o_lam = L.add(8 * (size_t)n_cells), o_fw = L.add(8 * (size_t)n_cells),
+               o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces);
   const size_t o_x = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N), o_y = L.add(16 * (size_t)N),
                o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N);
   const size_t o_A = L.add(8 * (size_t)a_tot);
@@ -359,6 +361,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
   d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);
   d.status = (int*)P(o_status); d.steps = (int*)P(o_steps); d.info = (int*)P(o_info);
+  d.lam = (double*)P(o_lam); d.fw = (double*)P(o_fw); d.inv_pv = (double*)P(o_ipv); d.fcoef = (double*)P(o_fc);
 
   cudaStream_t st = ctx->stream;
   auto cp = [&](void* dst, const void* src, size_t bytes) {
@@ -400,6 +403,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
     ctx->launches += 2;
   }
   CK(cp(ctx->d_sims + slot, &d, sizeof(SimDev)));
+  lrbms::launch_prepare(ctx->d_sims + slot, std::max(n_cells, n_faces), st);
+  ctx->launches += 1;
   CK(cudaStreamSynchronize(st));  // caller buffers may be freed on return
   CK(cudaGetLastError());
   Slot& s = ctx->slots[slot];

@@ -61,6 +61,12 @@ struct SimDev {
   const long long* ioff;    // [n_sub+1] inverse of diagonal block k, [N_k][N_k], then its transpose;
                             // same alignment
 
+  // per-step cell data and load-time coefficients
+  double* lam;      // [n_cells] lambda(s^n) of the current step
+  double* fw;       // [n_cells] f_w(s^n) of the current step
+  double* inv_pv;   // [n_cells] 1 / (phi_e |e|)
+  double* fcoef;    // [3][n_faces] per-face coefficients of the flux (k_prepare)
+
   // state and work arrays
   double* s;        // [2][n_cells] ping-pong; current = steps & 1
   double* p;        // [3][n_cells]
@@ -87,6 +93,8 @@ struct SimDev {
 __host__ __device__ inline int jlo_of(int k, int Sx) { return k - Sx > 0 ? k - Sx : 0; }
 
 // Launchers (all enqueue on `st`; `active` lists slot indices, device array).
+// Load-time coefficients of one simulation (device pointer to its SimDev).
+void launch_prepare(const SimDev* sim, int n_items, cudaStream_t st);
 void launch_fit(const SimDev* sims, const int* active, int n_active, int max_tiles,
                 cudaStream_t st);
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
