@@ -252,8 +252,8 @@ __host__ __device__ inline size_t meta_bytes(int n_sub) {
   return ((size_t)4 * (2 * n_sub + 1) + 15) / 16 * 16 + (size_t)16 * (n_sub + 1);
 }
 __host__ __device__ inline size_t round4(size_t v) { return (v + 3) & ~(size_t)3; }
-constexpr size_t kBarBytes = 8 * kMaxSlots * 2 + 4 * kMaxSlots + 16;  // full, empty, dl, flags
-// Offset tables, barriers, slot offsets and flags, per-warp partial vectors
+constexpr size_t kBarBytes = 8 * kMaxSlots * 2 + 8 * kMaxSlots + 16;  // full, empty, dl, epos, flags
+// Offset tables, barriers, slot offsets, FIFO entry starts and flags, per-warp partial vectors
 // [kNW][32], the panel R of the current block row (padded columns), the
 // factorisation ring, the substitution vectors [2N] and [32].
 __host__ __device__ inline size_t warp_smem_bytes(int n_sub, int panel_words, int N, size_t elem) {
@@ -267,6 +267,7 @@ struct CtaSmem {
   uint64_t* full;   // [kMaxSlots]
   uint64_t* empty;  // [kMaxSlots]
   int* dl;          // [kMaxSlots]
+  int* epos;        // [kMaxSlots] entry starts of the substitution FIFOs
   int* flag;        // [0] non-positive pivot, [1] copy timeout
   T* part;          // [kNW][32]
   T* R;             // [panel_words]
@@ -291,7 +292,8 @@ __device__ CtaSmem<T> cta_carve_and_load(const SimDev& S, unsigned char* b) {
   m.full = reinterpret_cast<uint64_t*>(bb);
   m.empty = m.full + kMaxSlots;
   m.dl = reinterpret_cast<int*>(m.empty + kMaxSlots);
-  m.flag = m.dl + kMaxSlots;
+  m.epos = m.dl + kMaxSlots;
+  m.flag = m.epos + kMaxSlots;
   T* t = reinterpret_cast<T*>(bb + kBarBytes);
   const size_t rw = round4((size_t)S.panel_words);
   m.part = t;
@@ -648,58 +650,160 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
   return kFacOk;
 }
 
-// Chunk sequence of the substitutions. Forward, block row k ascending: the
-// rows of panel k at the columns of each j in [jlo_k, k), then (L_kk^-1)^T.
-// Backward, k descending: L_kk^-1 first, then the same panel chunks. The
-// state advances incrementally (j = -1 marks the inverse).
-struct SubstSeq {
-  int k, j, jl, Nk, dir;
-  long long poff;  // element offset of chunk j within the factor
+// ---------------------------------------------------------------- substitutions
+// Forward and backward substitution, pipelined over the block rows with one
+// CTA barrier per row. Forward, iteration k: the leader applies the
+// contribution of row k-1 to row k and y_k = L_kk^-1 t_k (the critical path);
+// the other warps apply the contributions of row k-1 to rows k+1 ..
+// k-1+Sx (t_k' -= L_{k'k-1} y_{k-1}). Backward, iteration k (descending): the
+// leader applies the contribution of row k+1 to row k and z_k = L_kk^-T (y_k
+// - p_k); the other warps apply the contributions of row k+1 to rows j <
+// k (p_j += L_{k+1 j}^T z_{k+1}). Every warp streams its own chunks through
+// its own region of shared memory (a FIFO of variable-size bulk copies with
+// kEnt full barriers), so no warp waits for another to release a slot.
+constexpr int kEnt = kMaxSlots / kNW;  // chunks in flight per warp
+
+template <typename T>
+struct WRing {
+  T* base;          // the warp's region [cap]
+  int cap;          // elements (multiple of 4)
+  int b0;           // first barrier of the warp
+  uint64_t* full;   // all barriers
+  int* eoff;        // per barrier: element offset of the chunk's data in the region
+  int* epos;        // per barrier: start of the entry in the region
+  int pos, tpos;    // next allocation; start of the oldest live entry
+  unsigned issued, consumed;
+  unsigned ph, used, fpar;
+  bool ok;
 };
 
-__device__ __forceinline__ SubstSeq subst_begin(const SolveMeta& mt, int Sx, int k, int dir) {
-  SubstSeq q;
-  q.k = k;
-  q.dir = dir;
-  q.jl = jlo_of(k, Sx);
-  q.Nk = mt.NE[k];
-  q.poff = mt.loff[k];
-  q.j = dir > 0 ? (q.jl < k ? q.jl : -1) : -1;
-  return q;
+// Issue a chunk if it fits (lane 0 copies); returns false if the region is full.
+template <typename T>
+__device__ __forceinline__ bool wring_try_issue(WRing<T>& r, const T* src, long long off, int count, int lane) {
+  constexpr int kA = 16 / (int)sizeof(T);
+  if ((int)(r.issued - r.consumed) >= kEnt) return false;
+  const int d = (int)(off & (kA - 1));
+  const int need = (d + count + 3) & ~3;  // elements, 16-byte multiple
+  int at;
+  if (r.issued == r.consumed) {
+    at = 0;
+    r.tpos = 0;
+  } else if (r.pos > r.tpos) {
+    if (r.pos + need <= r.cap) at = r.pos;
+    else if (need <= r.tpos) at = 0;
+    else return false;
+  } else {  // wrapped: free space is [pos, tpos)
+    if (r.pos + need <= r.tpos) at = r.pos;
+    else return false;
+  }
+  const int e = (int)(r.issued % (unsigned)kEnt);
+  const int b = r.b0 + e;
+  r.used |= 1u << b;
+  r.fpar ^= 1u << b;
+  if (lane == 0) {
+    r.eoff[b] = at + d;
+    r.epos[b] = at;
+    mbar_expect_tx(&r.full[b], (uint32_t)(need * (int)sizeof(T)));
+    bulk_g2s(r.base + at, src + (off - d), (uint32_t)(need * (int)sizeof(T)), &r.full[b]);
+  }
+  r.pos = at + need;
+  ++r.issued;
+  return true;
 }
 
 template <typename T>
-__device__ __forceinline__ void subst_issue(Ring<T>& r, SubstSeq& q, const SolveMeta& mt, int Sx, int nsub,
-                                            const T* LT, const T* Linv, int lane) {
-  const int Nk = q.Nk;
-  if (q.j < 0) {
-    ring_issue<T>(r, Linv, mt.ioff[q.k] + (q.dir > 0 ? ((Nk * Nk + 3) & ~3) : 0), Nk * Nk, lane);
-    if (q.dir > 0) {
-      if (q.k + 1 < nsub) q = subst_begin(mt, Sx, q.k + 1, 1);
-      else q.k = nsub;
-    } else {
-      q.j = q.jl < q.k ? q.jl : -2;  // -2: row done
+__device__ __forceinline__ const T* wring_wait(WRing<T>& r) {
+  const int b = r.b0 + (int)(r.consumed % (unsigned)kEnt);
+  if (r.ok && !mbar_wait(&r.full[b], (r.ph >> b) & 1u)) r.ok = false;  // fail fast after a timeout
+  r.ph ^= 1u << b;
+  return r.base + r.eoff[b];
+}
+
+template <typename T>
+__device__ __forceinline__ void wring_release(WRing<T>& r) {
+  __syncwarp();
+  ++r.consumed;
+  if (r.consumed == r.issued) r.tpos = r.pos;
+  else r.tpos = r.epos[r.b0 + (int)(r.consumed % (unsigned)kEnt)];
+}
+
+// The warp's own chunks, in consumption order. Iteration k owns, for the
+// leader: (a) the previous (forward) / next (backward) row's chunk at row k,
+// (b) the diagonal inverse of row k; for warp w > 0: the c-items i = w-1,
+// w-1+(kNW-1), ... (forward: rows k' = k+1+i at block k-1; backward: row k+1
+// at block j = jlo_{k+1}+i).
+struct SCursor {
+  int dir, k, sub;
+};
+
+__device__ __forceinline__ int n_citems(const SolveMeta& mt, int Sx, int nsub, int dir, int k) {
+  (void)mt;
+  if (dir > 0) return k >= 1 ? max(0, min(k - 1 + Sx, nsub - 1) - k) : 0;
+  return k <= nsub - 2 ? k - jlo_of(k + 1, Sx) : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool scursor_item(const SolveMeta& mt, int Sx, int nsub, int w, const SCursor& c,
+                                             const T* LT, const T* Linv, const T** src, long long* off, int* cnt) {
+  const int k = c.k;
+  if (w == 0) {
+    const bool has_a = c.dir > 0 ? k >= 1 : k <= nsub - 2;
+    const int ia = has_a ? 0 : -1;
+    if (c.sub == ia) {
+      if (c.dir > 0) {  // panel k at block k-1: [g][c]
+        *off = mt.loff[k] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(k, Sx)]) * mt.NE[k];
+        *cnt = mt.NE[k - 1] * mt.NE[k];
+      } else {  // panel k+1 at block k
+        *off = mt.loff[k + 1] + (long long)(mt.xoff[k] - mt.xoff[jlo_of(k + 1, Sx)]) * mt.NE[k + 1];
+        *cnt = mt.NE[k] * mt.NE[k + 1];
+      }
+      *src = LT;
+      return true;
     }
-  } else {
-    const int Nj = mt.NE[q.j];
-    ring_issue<T>(r, LT, q.poff, Nj * Nk, lane);
-    q.poff += (long long)Nj * Nk;
-    if (++q.j == q.k) q.j = q.dir > 0 ? -1 : -2;
+    if (c.sub == ia + 1) {
+      const int Nk = mt.NE[k];
+      *off = mt.ioff[k] + (c.dir > 0 ? ((Nk * Nk + 3) & ~3) : 0);
+      *cnt = Nk * Nk;
+      *src = Linv;
+      return true;
+    }
+    return false;
   }
-  if (q.dir < 0 && q.j == -2) {
-    if (q.k > 0) q = subst_begin(mt, Sx, q.k - 1, -1);
-    else q.k = -1;
+  const int i = (w - 1) + c.sub * (kNW - 1);
+  if (i >= n_citems(mt, Sx, nsub, c.dir, k)) return false;
+  if (c.dir > 0) {
+    const int kk = k + 1 + i;
+    *off = mt.loff[kk] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(kk, Sx)]) * mt.NE[kk];
+    *cnt = mt.NE[k - 1] * mt.NE[kk];
+  } else {
+    const int jl1 = jlo_of(k + 1, Sx), j = jl1 + i;
+    *off = mt.loff[k + 1] + (long long)(mt.xoff[j] - mt.xoff[jl1]) * mt.NE[k + 1];
+    *cnt = mt.NE[j] * mt.NE[k + 1];
+  }
+  *src = LT;
+  return true;
+}
+
+// Issue the warp's next chunks while they fit.
+template <typename T>
+__device__ __forceinline__ void srefill(WRing<T>& r, SCursor& c, const SolveMeta& mt, int Sx, int nsub, int w,
+                                        const T* LT, const T* Linv, int lane) {
+  while (c.dir > 0 ? c.k < nsub : c.k >= 0) {
+    const T* src;
+    long long off;
+    int cnt;
+    if (!scursor_item<T>(mt, Sx, nsub, w, c, LT, Linv, &src, &off, &cnt)) {
+      c.k += c.dir;
+      c.sub = 0;
+      continue;
+    }
+    if (!wring_try_issue<T>(r, src, off, cnt, lane)) return;
+    ++c.sub;
   }
 }
-__device__ __forceinline__ bool subst_done(const SubstSeq& q, int nsub) { return q.dir > 0 ? q.k >= nsub : q.k < 0; }
 
 // Solve L L^T out = in with the transposed panels (arithmetic in T) by the
-// CTA; y and z live in shared memory. The chunks of a block row are shared
-// out over the warps (chunk i of the row to warp i mod kNW, the inverse to
-// warp 0). Warp 0 produces: after every chunk it passes it tops the ring up,
-// each refill of a slot waiting for the release of the slot's previous chunk
-// (a chunk that warp 0 has passed and whose owner reaches it without crossing
-// a CTA barrier). Returns false if a copy did not complete.
+// CTA; y and z live in shared memory. Returns false if a copy did not complete.
 template <typename T>
 __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const double* in, double* out,
                             CtaSmem<T>& m) {
@@ -709,127 +813,147 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   T* y = m.yz;
   T* z = y + N;
   T* tv = m.tv;
-  T* part = m.part;
-  Ring<T> rg{m.R, m.full, m.empty, m.dl, m.n_sub_slots, 0u, 0u, m.ph, m.eph, m.used, m.fpar, true};
-  SubstSeq q = subst_begin(mt, Sx, 0, 1);
-  auto refill = [&]() {
-    if (w == 0)
-      while (!subst_done(q, nsub) && (int)(rg.issued - rg.consumed) < rg.nslot)
-        subst_issue<T>(rg, q, mt, Sx, nsub, LT, Linv, lane);
-  };
+  const int area = (int)(round4((size_t)S.panel_words) + (size_t)kRing * kSlot);
+  const int cap = (area / kNW) & ~3;
+  WRing<T> rg{m.R + (size_t)w * cap, cap, w * kEnt, m.full, m.dl, m.epos, 0, 0, 0u, 0u, m.ph, m.used, m.fpar, true};
   for (int i = threadIdx.x; i < N; i += kThreads) {
     y[i] = (T)in[i];
     z[i] = T(0);
   }
-  refill();
+  SCursor cur{1, 0, 0};
+  srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
   __syncthreads();
-  // forward: y_k = L_kk^-1 (in_k - sum_j L_kj y_j)
+  // forward
   for (int k = 0; k < nsub; ++k) {
-    const int jl = jlo_of(k, Sx);
     const int Nk = mt.NE[k], xk = mt.xoff[k];
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    for (int j = jl; j < k; ++j) {
-      if (((j - jl) % kNW) != w) {
-        ring_skip<T>(rg);
-      } else {
-        const int Nj = mt.NE[j];
-        const T* P = ring_wait<T>(rg);  // [g][c]
-        const T* yj = y + mt.xoff[j];
+    if (w == 0) {
+      T t = (lane < Nk) ? y[xk + lane] : T(0);
+      if (k >= 1) {  // t_k -= L_{k,k-1} y_{k-1}
+        const int Nj = mt.NE[k - 1];
+        const T* P = wring_wait<T>(rg);  // [g][c]
+        const T* yj = y + mt.xoff[k - 1];
         if (lane < Nk) {
+          T a1 = T(0), a2 = T(0), a3 = T(0);
           int g = 0;
           for (; g + 3 < Nj; g += 4) {
-            a0 = fma(-P[g * Nk + lane], yj[g], a0);
+            t = fma(-P[g * Nk + lane], yj[g], t);
             a1 = fma(-P[(g + 1) * Nk + lane], yj[g + 1], a1);
             a2 = fma(-P[(g + 2) * Nk + lane], yj[g + 2], a2);
             a3 = fma(-P[(g + 3) * Nk + lane], yj[g + 3], a3);
           }
-          for (; g < Nj; ++g) a0 = fma(-P[g * Nk + lane], yj[g], a0);
+          for (; g < Nj; ++g) t = fma(-P[g * Nk + lane], yj[g], t);
+          t += (a1 + a2) + a3;
         }
-        ring_release<T>(rg, lane, kNW);
+        wring_release<T>(rg);
+        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
-      refill();
-    }
-    part[w * 32 + lane] = (a0 + a1) + (a2 + a3);
-    __syncthreads();
-    if (w == 0) {
-      const T* LiT = ring_wait<T>(rg);
-      if (lane < Nk) {
-        T t = y[xk + lane];
-#pragma unroll
-        for (int u = 0; u < kNW; ++u) t += part[u * 32 + lane];
-        tv[lane] = t;
-      }
+      if (lane < Nk) tv[lane] = t;
       __syncwarp();
+      const T* LiT = wring_wait<T>(rg);
       T yk = T(0), yk1 = T(0);
       if (lane < Nk) {  // y_k[c] = sum_{t <= c} Linv[c][t] tv[t]
-        int t = 0;
-        for (; t + 1 <= lane; t += 2) {
-          yk = fma(LiT[t * Nk + lane], tv[t], yk);
-          yk1 = fma(LiT[(t + 1) * Nk + lane], tv[t + 1], yk1);
+        int u = 0;
+        for (; u + 1 <= lane; u += 2) {
+          yk = fma(LiT[u * Nk + lane], tv[u], yk);
+          yk1 = fma(LiT[(u + 1) * Nk + lane], tv[u + 1], yk1);
         }
-        if (t <= lane) yk = fma(LiT[t * Nk + lane], tv[t], yk);
+        if (u <= lane) yk = fma(LiT[u * Nk + lane], tv[u], yk);
         yk += yk1;
       }
-      ring_release<T>(rg, lane, kNW);
+      wring_release<T>(rg);
+        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       if (lane < Nk) y[xk + lane] = yk;
-    } else {
-      ring_skip<T>(rg);
+    } else if (k >= 1) {  // t_k' -= L_{k',k-1} y_{k-1} for the warp's rows k'
+      const int Nj = mt.NE[k - 1];
+      const T* yj = y + mt.xoff[k - 1];
+      const int nc = n_citems(mt, Sx, nsub, 1, k);
+      for (int i = w - 1; i < nc; i += kNW - 1) {
+        const int kk = k + 1 + i, N2 = mt.NE[kk];
+        const T* P = wring_wait<T>(rg);  // [g][c]
+        if (lane < N2) {
+          T a0 = T(0), a1 = T(0);
+          int g = 0;
+          for (; g + 1 < Nj; g += 2) {
+            a0 = fma(P[g * N2 + lane], yj[g], a0);
+            a1 = fma(P[(g + 1) * N2 + lane], yj[g + 1], a1);
+          }
+          if (g < Nj) a0 = fma(P[g * N2 + lane], yj[g], a0);
+          y[mt.xoff[kk] + lane] -= a0 + a1;
+        }
+        wring_release<T>(rg);
+        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+      }
     }
-    refill();
+    srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
     __syncthreads();
   }
-  // backward: z_k = L_kk^-T (y_k - p_k), then p_j += L_kj^T z_k for j < k
-  q = subst_begin(mt, Sx, nsub - 1, -1);
-  refill();
+  // backward
+  cur = SCursor{-1, nsub - 1, 0};
+  srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
   for (int k = nsub - 1; k >= 0; --k) {
-    const int jl = jlo_of(k, Sx);
     const int Nk = mt.NE[k], xk = mt.xoff[k];
     if (w == 0) {
-      const T* Li = ring_wait<T>(rg);
+      if (k <= nsub - 2) {  // p_k += L_{k+1,k}^T z_{k+1}
+        const int N2 = mt.NE[k + 1];
+        const T* P = wring_wait<T>(rg);  // [g][c]: g in block k, c in block k+1
+        const T* zn = z + mt.xoff[k + 1];
+        if (lane < Nk) {
+          const int g = lane;
+          int c = (N2 & 1) ? 0 : g % N2;
+          T a0 = T(0);
+          for (int u = 0; u < N2; ++u) {
+            a0 = fma(P[g * N2 + c], zn[c], a0);
+            if (++c == N2) c = 0;
+          }
+          z[xk + g] += a0;
+        }
+        wring_release<T>(rg);
+        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+      }
+      const T* Li = wring_wait<T>(rg);
       if (lane < Nk) tv[lane] = y[xk + lane] - z[xk + lane];
       __syncwarp();
       T zc = T(0);
       if (lane < Nk)
         for (int r = lane; r < Nk; ++r) zc = fma(Li[r * Nk + lane], tv[r], zc);
-      ring_release<T>(rg, lane, kNW);
+      wring_release<T>(rg);
+        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       if (lane < Nk) z[xk + lane] = zc;
-    } else {
-      ring_skip<T>(rg);
-    }
-    refill();
-    __syncthreads();
-    const T* zk = z + xk;
-    for (int j = jl; j < k; ++j) {
-      if (((j - jl) % kNW) != w) {
-        ring_skip<T>(rg);
-      } else {
-        const int Nj = mt.NE[j];
-        const T* P = ring_wait<T>(rg);  // [g][c]
-        if (lane < Nj) {  // lane = g; rotated for even N_k
+    } else if (k <= nsub - 2) {  // p_j += L_{k+1,j}^T z_{k+1} for the warp's j < k
+      const int N2 = mt.NE[k + 1];
+      const T* zn = z + mt.xoff[k + 1];
+      const int jl1 = jlo_of(k + 1, Sx);
+      const int nc = n_citems(mt, Sx, nsub, -1, k);
+      for (int i = w - 1; i < nc; i += kNW - 1) {
+        const int j = jl1 + i, Nj = mt.NE[j];
+        const T* P = wring_wait<T>(rg);  // [g][c]: g in block j, c in block k+1
+        if (lane < Nj) {
           const int g = lane;
-          int c = (Nk & 1) ? 0 : g % Nk;
+          int c = (N2 & 1) ? 0 : g % N2;
           T a0 = T(0);
-          for (int u = 0; u < Nk; ++u) {
-            a0 = fma(P[g * Nk + c], zk[c], a0);
-            if (++c == Nk) c = 0;
+          for (int u = 0; u < N2; ++u) {
+            a0 = fma(P[g * N2 + c], zn[c], a0);
+            if (++c == N2) c = 0;
           }
           z[mt.xoff[j] + g] += a0;
         }
-        ring_release<T>(rg, lane, kNW);
+        wring_release<T>(rg);
+        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
-      refill();
     }
+    srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < N; i += kThreads) out[i] = (double)z[i];
   if (!rg.ok) m.flag[1] = 1;
   m.ph = rg.ph;
-  m.eph = rg.eph;
   m.used = rg.used;
   m.fpar = rg.fpar;
   __syncthreads();
   if (m.flag[1]) {
-    ring_drain<T>(rg);
+    if (lane == 0)  // bounded wait for the warp's copies still in flight
+      for (int b = rg.b0; b < rg.b0 + kEnt; ++b)
+        if (rg.used & (1u << b)) mbar_wait(&rg.full[b], ((~rg.fpar) >> b) & 1u);
     __syncthreads();
     return false;
   }
