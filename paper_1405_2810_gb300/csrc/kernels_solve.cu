@@ -157,6 +157,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
+  #pragma unroll 1
   for (int it = 0; it < (1 << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (clock64() - t0 > kWaitCycles) break;
@@ -236,6 +237,7 @@ __device__ __forceinline__ int vwarp();
 template <typename T>
 __device__ void ring_drain(const Ring<T>& r) {
   if ((threadIdx.x & 31) == 0 && vwarp() == 0)
+    #pragma unroll 1
     for (int s = 0; s < kMaxSlots; ++s)
       if (r.used & (1u << s)) mbar_wait(&r.full[s], ((~r.fpar) >> s) & 1u);
 }
@@ -304,13 +306,16 @@ __device__ CtaSmem<T> cta_carve_and_load(const SimDev& S, unsigned char* b) {
   const size_t nss = (rw + (size_t)kRing * kSlot) / kSlot;
   m.n_sub_slots = nss > (size_t)kMaxSlots ? kMaxSlots : (int)nss;
   m.ph = m.eph = m.used = m.fpar = 0;
+  #pragma unroll 1
   for (int i = threadIdx.x; i < ns; i += kThreads) m.mt.NE[i] = S.NE[i];
+  #pragma unroll 1
   for (int i = threadIdx.x; i <= ns; i += kThreads) {
     m.mt.xoff[i] = S.xoff[i];
     m.mt.loff[i] = S.loff[i];
     m.mt.ioff[i] = S.ioff[i];
   }
   if (threadIdx.x == 0) {
+    #pragma unroll 1
     for (int i = 0; i < kMaxSlots; ++i) {
       mbar_init(&m.full[i], 1);
       mbar_init(&m.empty[i], kNW);
@@ -334,6 +339,7 @@ __device__ __forceinline__ int vwarp() {
 __device__ void cta_release_barriers(uint64_t* full) {
   __syncthreads();
   if (threadIdx.x == 0)
+    #pragma unroll 1
     for (int i = 0; i < 2 * kMaxSlots; ++i) mbar_inval(&full[i]);
   __syncthreads();
 }
@@ -348,6 +354,7 @@ __device__ __forceinline__ double vget(const double2& v, int i) { return i == 0 
 // Padded width of block row k in R: sum over its envelope of round4(N_i).
 __device__ __forceinline__ int padded_width(const SolveMeta& mt, int jl, int k) {
   int w = 0;
+  #pragma unroll 1
   for (int i = jl; i <= k; ++i) w += (mt.NE[i] + 3) & ~3;
   return w;
 }
@@ -360,14 +367,16 @@ __device__ __forceinline__ int row_stride(int Wc) {
 }
 
 // Row-GEMM on one warp, lane = output column c (< ncols):
-//   C[r][c] (SET: =, else -=) sum_{t < 4 NV} A[r][t] B[t][c],  r < nrows,
+//   C[r][c] (set: =, else -=) sum_{t < 4 NV} A[r][t] B[t][c],  r < nrows,
 // A rows in shared memory (16-byte aligned, zero beyond the true inner size),
 // B element (t, c) at Bp[t * bst + c * bsc] for t < nt (zero for t >= nt).
-// Four rows per pass for independent accumulation chains; in SET mode C may
-// alias A (every row is read by all lanes before it is written).
-template <typename T, int NV, bool SET>
-__device__ __forceinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* C, int ldc, int nrows, const T* Bp,
-                                           int bst, int bsc, int nt, int ncols, int lane) {
+// Four rows per pass for independent accumulation chains; with `set` C may
+// alias A (every row is read by all lanes before it is written). Not inlined:
+// one copy per unroll depth keeps the kernel's instruction footprint small
+// when several CTAs share an SM.
+template <typename T, int NV>
+__device__ __noinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* C, int ldc, int nrows, const T* Bp,
+                                        int bst, int bsc, int nt, int ncols, int lane, bool set) {
   using V = typename Vec16<T>::type;
   constexpr int kV = Vec16<T>::n;
   constexpr int NT = 4 * NV;
@@ -376,6 +385,7 @@ __device__ __forceinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* 
 #pragma unroll
   for (int t = 0; t < NT; ++t) b[t] = (act && t < nt) ? Bp[t * bst + lane * bsc] : T(0);
   int r = 0;
+  #pragma unroll 1
   for (; r + 3 < nrows; r += 4) {
     T acc[4][2];
 #pragma unroll
@@ -389,15 +399,16 @@ __device__ __forceinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* 
         for (int e = 0; e < kV; ++e) acc[i][e & 1] = fma(vget(x, e), b[v * kV + e], acc[i][e & 1]);
       }
     }
-    if (SET) __syncwarp();
+    if (set) __syncwarp();
     if (act) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (SET) C[(r + i) * ldc + lane] = acc[i][0] + acc[i][1];
-        else C[(r + i) * ldc + lane] -= acc[i][0] + acc[i][1];
+        T* c = C + (r + i) * ldc + lane;
+        *c = (set ? T(0) : *c) - (acc[i][0] + acc[i][1]) * (set ? T(-1) : T(1));
       }
     }
   }
+  #pragma unroll 1
   for (; r < nrows; ++r) {
     T a0 = T(0), a1 = T(0);
 #pragma unroll
@@ -409,28 +420,28 @@ __device__ __forceinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* 
         else a0 = fma(vget(x, e), b[v * kV + e], a0);
       }
     }
-    if (SET) __syncwarp();
+    if (set) __syncwarp();
     if (act) {
-      if (SET) C[r * ldc + lane] = a0 + a1;
-      else C[r * ldc + lane] -= a0 + a1;
+      T* c = C + r * ldc + lane;
+      *c = (set ? T(0) : *c) - (a0 + a1) * (set ? T(-1) : T(1));
     }
   }
   __syncwarp();
 }
 
-template <typename T, bool SET>
+template <typename T>
 __device__ __forceinline__ void rowgemm(const T* A, int lda, T* C, int ldc, int nrows, const T* Bp, int bst,
-                                        int bsc, int nt, int ncols, int lane) {
+                                        int bsc, int nt, int ncols, int lane, bool set) {
   if (nrows <= 0) return;
   switch ((nt + 3) >> 2) {
-    case 1: rowgemm_nv<T, 1, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    case 2: rowgemm_nv<T, 2, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    case 3: rowgemm_nv<T, 3, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    case 4: rowgemm_nv<T, 4, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    case 5: rowgemm_nv<T, 5, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    case 6: rowgemm_nv<T, 6, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    case 7: rowgemm_nv<T, 7, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
-    default: rowgemm_nv<T, 8, SET>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane); break;
+    case 1: rowgemm_nv<T, 1>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    case 2: rowgemm_nv<T, 2>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    case 3: rowgemm_nv<T, 3>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    case 4: rowgemm_nv<T, 4>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    case 5: rowgemm_nv<T, 5>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    case 6: rowgemm_nv<T, 6>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    case 7: rowgemm_nv<T, 7>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
+    default: rowgemm_nv<T, 8>(A, lda, C, ldc, nrows, Bp, bst, bsc, nt, ncols, lane, set); break;
   }
 }
 
@@ -462,6 +473,76 @@ __device__ __forceinline__ void factor_issue(Ring<T>& r, FactorSeq& q, const Sol
   q.next();
 }
 
+// Cholesky factor and inverse of the N x N diagonal block D (shared memory,
+// row stride ld; overwritten by L) by one warp, with runtime loops (a small
+// instruction footprint). Left-looking, lane = row r: L[r][c] = (D[r][c] -
+// sum_{t<c} L[r][t] L[c][t]) / L[c][c]. Inverse, lane = column j (work area
+// Y [N][N] in shared memory): Linv[r][j] = (delta_rj - sum_{t<r} L[r][t]
+// Linv[t][j]) / L[r][r]. Writes L to the transposed panel rows LTd ([c][r],
+// zero above the diagonal), L^-1 to Li [N][N] and its transpose after it.
+// Returns true on a non-positive or non-finite pivot (the warp's vote).
+template <typename T>
+__device__ __noinline__ bool diag_block(T* D, int ld, int N, T* Y, T* LTd, T* Li, int lane) {
+  bool bad = false;
+#pragma unroll 1
+  for (int c = 0; c < N; ++c) {
+    T sr = T(0), sr1 = T(0);
+    if (lane >= c && lane < N) {
+      const T* Lr = D + lane * ld;
+      const T* Lc = D + c * ld;
+      int t = 0;
+#pragma unroll 1
+      for (; t + 1 < c; t += 2) {
+        sr = fma(Lr[t], Lc[t], sr);
+        sr1 = fma(Lr[t + 1], Lc[t + 1], sr1);
+      }
+      if (t < c) sr = fma(Lr[t], Lc[t], sr);
+      sr = Lr[c] - (sr + sr1);
+    }
+    T piv = __shfl_sync(0xffffffffu, sr, c);
+    if (!(piv > T(0)) || !isfinite((double)piv)) {
+      bad = true;
+      piv = T(1);
+    }
+    const T d = sqrt(piv);
+    __syncwarp();
+    if (lane == c) D[c * ld + c] = d;
+    else if (lane > c && lane < N) D[lane * ld + c] = sr / d;
+    __syncwarp();
+  }
+  // inverse, lane = column j
+#pragma unroll 1
+  for (int r = 0; r < N; ++r) {
+    T y = T(0);
+    if (lane < N && lane <= r) {
+      const T* Lr = D + r * ld;
+      T s = (r == lane) ? T(1) : T(0), s1 = T(0);
+      int t = lane;
+#pragma unroll 1
+      for (; t + 1 < r; t += 2) {
+        s = fma(-Lr[t], Y[t * N + lane], s);
+        s1 = fma(-Lr[t + 1], Y[(t + 1) * N + lane], s1);
+      }
+      if (t < r) s = fma(-Lr[t], Y[t * N + lane], s);
+      y = (s + s1) / Lr[r];
+      Y[r * N + lane] = y;
+    }
+    __syncwarp();
+  }
+  T* LiT = Li + ((N * N + 3) & ~3);
+  if (lane < N) {
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) LTd[(size_t)c * N + lane] = (c <= lane) ? D[lane * ld + c] : T(0);
+#pragma unroll 1
+    for (int r = 0; r < N; ++r) {
+      const T y = (r >= lane) ? Y[r * N + lane] : T(0);
+      Li[r * N + lane] = y;
+      LiT[lane * N + r] = y;
+    }
+  }
+  return __any_sync(0xffffffffu, bad);
+}
+
 // Envelope block Cholesky of the assembled A (FP64) with factor storage T, by
 // the kNW warps of one CTA, each owning a contiguous range of the rows of the
 // current block row. Block row k is formed in R and processed right-looking:
@@ -479,10 +560,10 @@ template <typename T>
 __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
   const SolveMeta& mt = m.mt;
   const int nsub = S.n_sub, Sx = S.Sx;
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, w = vwarp();
   T* R = m.R;
   Ring<T> rg{m.ring, m.full, m.empty, m.dl, kRing, 0u, 0u, m.ph, m.eph, m.used, m.fpar, true};
+  #pragma unroll 1
   for (int k = 0; k < nsub; ++k) {
     const int jl = jlo_of(k, Sx);
     const int base = mt.xoff[jl];
@@ -498,6 +579,7 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
     {  // own rows of R <- assembled blocks of A (diagonal, left, lower), zero elsewhere and in the padding
       const int I = k % Sx, J = k / Sx;
       int pc = 0;
+      #pragma unroll 1
       for (int i = jl; i <= k; ++i) {
         const int Ni = mt.NE[i], Np = (Ni + 3) & ~3;
         const double* blk = nullptr;
@@ -512,6 +594,7 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
           for (int u = 0; u < 8; ++u)
             if (u < nr && lane < Np) R[(r0 + u) * Wp + pc + lane] = (T)v[u];
         } else if (blk) {  // A_{k,i}[r][c] = blk[c][r]: lanes over own rows read coalesced
+          #pragma unroll 1
           for (int c0 = 0; c0 < Np; c0 += 8) {
             double v[8];
 #pragma unroll
@@ -521,6 +604,7 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
               if (c0 + u < Np && lane < nr) R[(r0 + lane) * Wp + pc + c0 + u] = (T)v[u];
           }
         } else {
+          #pragma unroll 1
           for (int r = r0; r < r1; ++r)
             if (lane < Np) R[r * Wp + pc + lane] = T(0);
         }
@@ -531,21 +615,23 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
     T* LTk = LT + mt.loff[k];
     T* Rw = R + r0 * Wp;
     int pcj = 0;
+    #pragma unroll 1
     for (int j = jl; j < k; ++j) {
       const int Nj = mt.NE[j];
       const int Njp4 = (Nj + 3) & ~3;
       {  // X_j = R_j L_jj^-T on own rows (in place); B = (L_jj^-1)^T
         const T* LiT = ring_wait<T>(rg);
-        rowgemm<T, true>(Rw + pcj, Wp, Rw + pcj, Wp, nr, LiT, Nj, 1, Nj, Nj, lane);
+        rowgemm<T>(Rw + pcj, Wp, Rw + pcj, Wp, nr, LiT, Nj, 1, Nj, Nj, lane, true);
         ring_release<T>(rg, lane, 1);
         if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
       }
       // R_j' -= X_j L_{j'j}^T for j' in (j, k), own rows
       int pcjp = pcj + Njp4;
+      #pragma unroll 1
       for (int jp = j + 1; jp < k; ++jp) {
         const int Njp = mt.NE[jp];
         const T* Lc = ring_wait<T>(rg);  // [t][c'] = L_{j'j}[c'][t]
-        rowgemm<T, false>(Rw + pcj, Wp, Rw + pcjp, Wp, nr, Lc, Njp, 1, Nj, Njp, lane);
+        rowgemm<T>(Rw + pcj, Wp, Rw + pcjp, Wp, nr, Lc, Njp, 1, Nj, Njp, lane, false);
         ring_release<T>(rg, lane, 1);
         if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
         pcjp += (Njp + 3) & ~3;
@@ -555,79 +641,29 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
     __syncthreads();  // every X_j of the row is final
     {  // L_kj = X_j into the transposed panel (lanes over rows: coalesced), all warps
       int pc = 0;
+      #pragma unroll 1
       for (int j = jl; j < k; ++j) {
         const int Nj = mt.NE[j], gj = mt.xoff[j] - base;
         if (lane < Nk)
+          #pragma unroll 1
           for (int c = w; c < Nj; c += kNW) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
         pc += (Nj + 3) & ~3;
       }
     }
     {  // R_kk -= sum_j X_j X_j^T on own rows; B[t][c] = X_j[c][t]
       int pc = 0;
+      #pragma unroll 1
       for (int j = jl; j < k; ++j) {
         const int Nj = mt.NE[j];
-        rowgemm<T, false>(Rw + pc, Wp, Rw + pck, Wp, nr, R + pc, 1, Wp, Nj, Nk, lane);
+        rowgemm<T>(Rw + pc, Wp, Rw + pck, Wp, nr, R + pc, 1, Wp, Nj, Nk, lane, false);
         pc += (Nj + 3) & ~3;
       }
     }
     __syncthreads();
-    if (w == 0) {  // diagonal block: Cholesky in registers, lane i holds row i
-      bool badp = false;
-      T v[32];
-#pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        if (t >= Nk) break;
-        v[t] = (lane < Nk && t <= lane) ? R[lane * Wp + pck + t] : T(0);
-      }
-      T mydinv = T(1);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        if (c >= Nk) break;
-        T piv = __shfl_sync(full, v[c], c);
-        if (!(piv > T(0)) || !isfinite((double)piv)) {
-          badp = true;
-          piv = T(1);
-        }
-        const T d = sqrt(piv);
-        const T inv = T(1) / d;
-        if (lane == c) mydinv = inv;
-        const T lc = (lane == c) ? d : ((lane > c) ? v[c] * inv : v[c]);
-        v[c] = lc;
-#pragma unroll
-        for (int t = c + 1; t < 32; ++t) {
-          if (t >= Nk) break;
-          const T ltc = __shfl_sync(full, lc, t);
-          if (lane >= t) v[t] = fma(-lc, ltc, v[t]);
-        }
-      }
-      // inverse, lane = column: y[r] = Linv[r][lane]
-      T y[32];
-#pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        if (r >= Nk) break;
-        T s = (r == lane) ? T(1) : T(0);
-#pragma unroll
-        for (int t = 0; t < r; ++t) s = fma(-__shfl_sync(full, v[t], r), y[t], s);
-        const T dinv = __shfl_sync(full, mydinv, r);
-        y[r] = (r >= lane) ? s * dinv : T(0);
-      }
-      T* Li = Linv + mt.ioff[k];
-      T* LiT = Li + ((Nk * Nk + 3) & ~3);
-      const int gk = mt.xoff[k] - base;
-      if (lane < Nk) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          if (c >= Nk) break;
-          LTk[(size_t)(gk + c) * Nk + lane] = (c <= lane) ? v[c] : T(0);
-        }
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          if (r >= Nk) break;
-          Li[r * Nk + lane] = y[r];
-          LiT[lane * Nk + r] = y[r];
-        }
-      }
-      if (__any_sync(full, badp) && lane == 0) m.flag[0] = 1;
+    if (w == 0) {  // diagonal block by the leader warp
+      const bool badp = diag_block<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
+                                      Linv + mt.ioff[k], lane);
+      if (badp && lane == 0) m.flag[0] = 1;
     }
     if (!rg.ok) m.flag[1] = 1;
     fence_proxy_async();  // the next rows copy these panels with the async proxy
@@ -816,6 +852,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   const int area = (int)(round4((size_t)S.panel_words) + (size_t)kRing * kSlot);
   const int cap = (area / kNW) & ~3;
   WRing<T> rg{m.R + (size_t)w * cap, cap, w * kEnt, m.full, m.dl, m.epos, 0, 0, 0u, 0u, m.ph, m.used, m.fpar, true};
+  #pragma unroll 1
   for (int i = threadIdx.x; i < N; i += kThreads) {
     y[i] = (T)in[i];
     z[i] = T(0);
@@ -824,6 +861,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
   __syncthreads();
   // forward
+  #pragma unroll 1
   for (int k = 0; k < nsub; ++k) {
     const int Nk = mt.NE[k], xk = mt.xoff[k];
     if (w == 0) {
@@ -835,12 +873,14 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
         if (lane < Nk) {
           T a1 = T(0), a2 = T(0), a3 = T(0);
           int g = 0;
+          #pragma unroll 1
           for (; g + 3 < Nj; g += 4) {
             t = fma(-P[g * Nk + lane], yj[g], t);
             a1 = fma(-P[(g + 1) * Nk + lane], yj[g + 1], a1);
             a2 = fma(-P[(g + 2) * Nk + lane], yj[g + 2], a2);
             a3 = fma(-P[(g + 3) * Nk + lane], yj[g + 3], a3);
           }
+          #pragma unroll 1
           for (; g < Nj; ++g) t = fma(-P[g * Nk + lane], yj[g], t);
           t += (a1 + a2) + a3;
         }
@@ -853,6 +893,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       T yk = T(0), yk1 = T(0);
       if (lane < Nk) {  // y_k[c] = sum_{t <= c} Linv[c][t] tv[t]
         int u = 0;
+        #pragma unroll 1
         for (; u + 1 <= lane; u += 2) {
           yk = fma(LiT[u * Nk + lane], tv[u], yk);
           yk1 = fma(LiT[(u + 1) * Nk + lane], tv[u + 1], yk1);
@@ -867,12 +908,14 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       const int Nj = mt.NE[k - 1];
       const T* yj = y + mt.xoff[k - 1];
       const int nc = n_citems(mt, Sx, nsub, 1, k);
+      #pragma unroll 1
       for (int i = w - 1; i < nc; i += kNW - 1) {
         const int kk = k + 1 + i, N2 = mt.NE[kk];
         const T* P = wring_wait<T>(rg);  // [g][c]
         if (lane < N2) {
           T a0 = T(0), a1 = T(0);
           int g = 0;
+          #pragma unroll 1
           for (; g + 1 < Nj; g += 2) {
             a0 = fma(P[g * N2 + lane], yj[g], a0);
             a1 = fma(P[(g + 1) * N2 + lane], yj[g + 1], a1);
@@ -890,6 +933,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   // backward
   cur = SCursor{-1, nsub - 1, 0};
   srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
+  #pragma unroll 1
   for (int k = nsub - 1; k >= 0; --k) {
     const int Nk = mt.NE[k], xk = mt.xoff[k];
     if (w == 0) {
@@ -901,6 +945,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
           const int g = lane;
           int c = (N2 & 1) ? 0 : g % N2;
           T a0 = T(0);
+          #pragma unroll 1
           for (int u = 0; u < N2; ++u) {
             a0 = fma(P[g * N2 + c], zn[c], a0);
             if (++c == N2) c = 0;
@@ -915,6 +960,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       __syncwarp();
       T zc = T(0);
       if (lane < Nk)
+        #pragma unroll 1
         for (int r = lane; r < Nk; ++r) zc = fma(Li[r * Nk + lane], tv[r], zc);
       wring_release<T>(rg);
         srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
@@ -924,6 +970,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       const T* zn = z + mt.xoff[k + 1];
       const int jl1 = jlo_of(k + 1, Sx);
       const int nc = n_citems(mt, Sx, nsub, -1, k);
+      #pragma unroll 1
       for (int i = w - 1; i < nc; i += kNW - 1) {
         const int j = jl1 + i, Nj = mt.NE[j];
         const T* P = wring_wait<T>(rg);  // [g][c]: g in block j, c in block k+1
@@ -931,6 +978,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
           const int g = lane;
           int c = (N2 & 1) ? 0 : g % N2;
           T a0 = T(0);
+          #pragma unroll 1
           for (int u = 0; u < N2; ++u) {
             a0 = fma(P[g * N2 + c], zn[c], a0);
             if (++c == N2) c = 0;
@@ -944,6 +992,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
     srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
     __syncthreads();
   }
+  #pragma unroll 1
   for (int i = threadIdx.x; i < N; i += kThreads) out[i] = (double)z[i];
   if (!rg.ok) m.flag[1] = 1;
   m.ph = rg.ph;
@@ -952,6 +1001,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   __syncthreads();
   if (m.flag[1]) {
     if (lane == 0)  // bounded wait for the warp's copies still in flight
+      #pragma unroll 1
       for (int b = rg.b0; b < rg.b0 + kEnt; ++b)
         if (rg.used & (1u << b)) mbar_wait(&rg.full[b], ((~rg.fpar) >> b) & 1u);
     __syncthreads();
@@ -965,12 +1015,14 @@ __device__ __forceinline__ double dot_strided(const double* __restrict__ a, int 
                                               double acc) {
   double a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int c = 0;
+  #pragma unroll 1
   for (; c + 3 < n; c += 4) {
     acc = fma(a[c * sa], xs[c], acc);
     a1 = fma(a[(c + 1) * sa], xs[c + 1], a1);
     a2 = fma(a[(c + 2) * sa], xs[c + 2], a2);
     a3 = fma(a[(c + 3) * sa], xs[c + 3], a3);
   }
+  #pragma unroll 1
   for (; c < n; ++c) acc = fma(a[c * sa], xs[c], acc);
   return (acc + a1) + (a2 + a3);
 }
@@ -981,8 +1033,10 @@ __device__ void cresidual(const SimDev& S, const SolveMeta& mt, const double* x,
                           double* xs) {
   const int Sx = S.Sx, Sy = S.Sy, nsub = S.n_sub;
   const int lane = threadIdx.x & 31, w = vwarp();
+  #pragma unroll 1
   for (int i = threadIdx.x; i < S.N; i += kThreads) xs[i] = x[i];
   __syncthreads();
+  #pragma unroll 1
   for (int E = w; E < nsub; E += kNW) {
     const int NE = mt.NE[E], x0 = mt.xoff[E];
     const int I = E % Sx, J = E / Sx;
@@ -1047,14 +1101,17 @@ __device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int i
   if (!csubstitute<T>(S, Lst, Linv, S.b, S.x, m)) return kRefTimeout;
   double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
   double mx = 0.0;
+  #pragma unroll 1
   for (int i = threadIdx.x; i < S.N; i += kThreads) mx = fmax(mx, fabs(S.x[i]));
   double prev = cta_max(mx, red);
   int steps = 0, rc = kRefOk;
+  #pragma unroll 1
   for (int it = 0; it < iters; ++it) {
     cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
     if (!csubstitute<T>(S, Lst, Linv, S.rv, S.dv, m)) return kRefTimeout;
     double mdv = 0.0;
     mx = 0.0;
+    #pragma unroll 1
     for (int i = threadIdx.x; i < S.N; i += kThreads) {
       const double xi = S.x[i] + S.dv[i];
       S.x[i] = xi;
@@ -1140,13 +1197,19 @@ __global__ void k_noalloc_tables(SimDev S) {
   long long* loff = const_cast<long long*>(S.loff);
   long long* ioff = const_cast<long long*>(S.ioff);
   xoff[0] = 0;
+  #pragma unroll 1
   for (int E = 0; E < S.n_sub; ++E) xoff[E + 1] = xoff[E] + NE[E];
   aoff[0] = 0;
+  #pragma unroll 1
   for (int E = 0; E < S.n_sub; ++E) aoff[E + 1] = aoff[E] + (long long)NE[E] * NE[E];
   int b = S.n_sub;
+  #pragma unroll 1
   for (int J = 0; J < S.Sy; ++J)
+    #pragma unroll 1
     for (int I = 0; I + 1 < S.Sx; ++I, ++b) aoff[b + 1] = aoff[b] + (long long)NE[J * S.Sx + I] * NE[J * S.Sx + I + 1];
+  #pragma unroll 1
   for (int J = 0; J + 1 < S.Sy; ++J)
+    #pragma unroll 1
     for (int I = 0; I < S.Sx; ++I, ++b) aoff[b + 1] = aoff[b] + (long long)NE[J * S.Sx + I] * NE[(J + 1) * S.Sx + I];
   loff[0] = 0;
   ioff[0] = 0;
