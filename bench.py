@@ -415,7 +415,7 @@ def main():
         t_solve = phase_ms[dom] / 1000.0
         t_min = f_lo / (FP32_PEAK_TFLOPS * 1e12) + f_hi / (FP64_PEAK_TFLOPS * 1e12)
         work = (f_lo + f_hi) * 1e-12
-        roof = {"bound": "alu", "kernel": "k_csolve32" if a.solver == "mixed" else "k_csolve64",
+        roof = {"bound": "alu", "kernel": "k_factor32 + k_refine32" if a.solver == "mixed" else "k_csolve64",
                 "achieved": work / t_solve, "peak": work / t_min, "unit": "TFLOP/s", "frac": t_min / t_solve,
                 "traffic": None,
                 "peak_source": ("time-weighted ALU peak of the solve's FP32 and FP64 flops: "

@@ -154,8 +154,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity) {
   const long long t0 = clock64();
   #pragma unroll 1
   for (int it = 0; it < (1 << 26); ++it) {
@@ -163,6 +162,9 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) break;
   }
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
 // Ring state (all threads walk the same chunk stream): chunk n lives in slot
@@ -384,17 +386,20 @@ __device__ __noinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* C, 
   const bool act = lane < ncols;
 #pragma unroll
   for (int t = 0; t < NT; ++t) b[t] = (act && t < nt) ? Bp[t * bst + lane * bsc] : T(0);
-  int r = 0;
-  #pragma unroll 1
-  for (; r + 3 < nrows; r += 4) {
+#pragma unroll 1
+  for (int r = 0; r < nrows; r += 4) {  // rows past nrows repeat the last row and are not written
     T acc[4][2];
+    int ri[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = T(0);
+    for (int i = 0; i < 4; ++i) {
+      acc[i][0] = acc[i][1] = T(0);
+      ri[i] = min(r + i, nrows - 1);
+    }
 #pragma unroll
     for (int v = 0; v < NT / kV; ++v) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const V x = reinterpret_cast<const V*>(A + (r + i) * lda)[v];
+        const V x = reinterpret_cast<const V*>(A + ri[i] * lda)[v];
 #pragma unroll
         for (int e = 0; e < kV; ++e) acc[i][e & 1] = fma(vget(x, e), b[v * kV + e], acc[i][e & 1]);
       }
@@ -403,27 +408,11 @@ __device__ __noinline__ void rowgemm_nv(const T* __restrict__ A, int lda, T* C, 
     if (act) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        T* c = C + (r + i) * ldc + lane;
-        *c = (set ? T(0) : *c) - (acc[i][0] + acc[i][1]) * (set ? T(-1) : T(1));
+        if (r + i < nrows) {
+          T* c = C + (r + i) * ldc + lane;
+          *c = (set ? T(0) : *c) - (acc[i][0] + acc[i][1]) * (set ? T(-1) : T(1));
+        }
       }
-    }
-  }
-  #pragma unroll 1
-  for (; r < nrows; ++r) {
-    T a0 = T(0), a1 = T(0);
-#pragma unroll
-    for (int v = 0; v < NT / kV; ++v) {
-      const V x = reinterpret_cast<const V*>(A + r * lda)[v];
-#pragma unroll
-      for (int e = 0; e < kV; ++e) {
-        if (e & 1) a1 = fma(vget(x, e), b[v * kV + e], a1);
-        else a0 = fma(vget(x, e), b[v * kV + e], a0);
-      }
-    }
-    if (set) __syncwarp();
-    if (act) {
-      T* c = C + r * ldc + lane;
-      *c = (set ? T(0) : *c) - (a0 + a1) * (set ? T(-1) : T(1));
     }
   }
   __syncwarp();
@@ -1011,7 +1000,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
 }
 
 // acc += sum_{c < n} a[c * sa] xs[c] with four chains (FP64).
-__device__ __forceinline__ double dot_strided(const double* __restrict__ a, int sa, const double* xs, int n,
+__device__ __noinline__ double dot_strided(const double* __restrict__ a, int sa, const double* xs, int n,
                                               double acc) {
   double a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int c = 0;
@@ -1098,29 +1087,33 @@ constexpr int kRefOk = 0, kRefStalled = 1, kRefTimeout = 2;
 
 template <typename T>
 __device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
-  if (!csubstitute<T>(S, Lst, Linv, S.b, S.x, m)) return kRefTimeout;
   double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
-  double mx = 0.0;
-  #pragma unroll 1
-  for (int i = threadIdx.x; i < S.N; i += kThreads) mx = fmax(mx, fabs(S.x[i]));
-  double prev = cta_max(mx, red);
+  double prev = 0.0;
   int steps = 0, rc = kRefOk;
-  #pragma unroll 1
-  for (int it = 0; it < iters; ++it) {
-    cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
-    if (!csubstitute<T>(S, Lst, Linv, S.rv, S.dv, m)) return kRefTimeout;
-    double mdv = 0.0;
-    mx = 0.0;
-    #pragma unroll 1
+  // pass 0 solves for x, pass it >= 1 for the correction dv of refinement step it
+  // (one substitution call site keeps the kernel's code small)
+#pragma unroll 1
+  for (int it = 0; it <= iters; ++it) {
+    if (it > 0) cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
+    if (!csubstitute<T>(S, Lst, Linv, it == 0 ? S.b : S.rv, it == 0 ? S.x : S.dv, m)) return kRefTimeout;
+    double mdv = 0.0, mx = 0.0;
+#pragma unroll 1
     for (int i = threadIdx.x; i < S.N; i += kThreads) {
-      const double xi = S.x[i] + S.dv[i];
-      S.x[i] = xi;
-      mdv = fmax(mdv, fabs(S.dv[i]));
+      double xi = S.x[i];
+      if (it > 0) {
+        xi += S.dv[i];
+        S.x[i] = xi;
+        mdv = fmax(mdv, fabs(S.dv[i]));
+      }
       mx = fmax(mx, fabs(xi));
     }
     mdv = cta_max(mdv, red);
     mx = cta_max(mx, red);
-    steps = it + 1;
+    if (it == 0) {
+      prev = mx;
+      continue;
+    }
+    steps = it;
     if (!(mdv * fmin(1.0, mdv / prev) > kRefineTol * mx)) break;  // converged (also on 0/0)
     if (mdv > 0.5 * prev) {
       if (mdv > kFloorTol * mx) rc = kRefStalled;
@@ -1132,28 +1125,38 @@ __device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int i
   return rc;
 }
 
-// FP32 factor (one CTA per simulation): a simulation whose FP32
-// factorisation meets a non-positive pivot is marked for the FP64 kernel.
-constexpr int kStRetry64 = 1;
+constexpr int kStRetry64 = 1;  // transient status: redo this simulation's solve in FP64
 
-__global__ void __launch_bounds__(kThreads, 4) k_csolve32(const SimDev* __restrict__ sims,
-                                                       const int* __restrict__ active, int n_active, int iters) {
+// The FP32 path runs as two kernels, factorisation then substitutions and
+// refinement, so that the CTAs sharing an SM execute the same code (a smaller
+// instruction working set than one kernel whose CTAs are in different phases).
+// A simulation whose FP32 factorisation meets a non-positive pivot, or whose
+// refinement stalls, is marked for the FP64 kernel.
+__global__ void __launch_bounds__(kThreads, 4) k_factor32(const SimDev* __restrict__ sims,
+                                                          const int* __restrict__ active, int n_active) {
   const int a = blockIdx.x;
   if (a >= n_active) return;
   const SimDev& S = sims[active[a]];
   if (S.status[0] != kStOk) return;
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
-  float* Lf = reinterpret_cast<float*>(S.L);
-  float* Lif = reinterpret_cast<float*>(S.Linv);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
-  const int f = cfactor<float>(S, Lf, Lif, m);
-  if (f == kFacOk) {
-    const int r = csolve_refine<float>(S, Lf, Lif, iters, m);
-    if (threadIdx.x == 0 && r != kRefOk) S.status[0] = r == kRefStalled ? kStRetry64 : kStTimeout;
-  } else if (threadIdx.x == 0) {
-    S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
-  }
+  const int f = cfactor<float>(S, reinterpret_cast<float*>(S.L), reinterpret_cast<float*>(S.Linv), m);
+  if (f != kFacOk && threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restrict__ sims,
+                                                          const int* __restrict__ active, int n_active, int iters) {
+  const int a = blockIdx.x;
+  if (a >= n_active) return;
+  const SimDev& S = sims[active[a]];
+  if (S.status[0] != kStOk) return;
+  extern __shared__ double sm[];
+  unsigned char* b = reinterpret_cast<unsigned char*>(sm);
+  CtaSmem<float> m = cta_carve_and_load<float>(S, b);
+  const int r = csolve_refine<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
+                                     iters, m);
+  if (threadIdx.x == 0 && r != kRefOk) S.status[0] = r == kRefStalled ? kStRetry64 : kStTimeout;
 }
 
 // FP64 factor. only_retry: process only the simulations marked by the FP32 kernel.
@@ -1273,8 +1276,10 @@ cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_activ
   if (n_active <= 0) return cudaSuccess;
   if (mode == 1) {
     const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
-    if ((e = set_smem((const void*)k_csolve32, s32)) != cudaSuccess) return e;
-    k_csolve32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
+    if ((e = set_smem((const void*)k_factor32, s32)) != cudaSuccess) return e;
+    if ((e = set_smem((const void*)k_refine32, s32)) != cudaSuccess) return e;
+    k_factor32<<<n_active, kThreads, s32, st>>>(sims, active, n_active);
+    k_refine32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
   }
   const size_t s64 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(double));
   if ((e = set_smem((const void*)k_csolve64, s64)) != cudaSuccess) return e;

@@ -475,7 +475,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(7);
     lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
     mark(8);
-    ctx->launches += 8;
+    ctx->launches += 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 3 : 1);  // mixed: factor, refine, FP64 redo
   }
   CK(cudaGetLastError());
   if (status) {
