@@ -462,74 +462,83 @@ __device__ __forceinline__ void factor_issue(Ring<T>& r, FactorSeq& q, const Sol
   q.next();
 }
 
-// Cholesky factor and inverse of the N x N diagonal block D (shared memory,
-// row stride ld; overwritten by L) by one warp, with runtime loops (a small
-// instruction footprint). Left-looking, lane = row r: L[r][c] = (D[r][c] -
-// sum_{t<c} L[r][t] L[c][t]) / L[c][c]. Inverse, lane = column j (work area
-// Y [N][N] in shared memory): Linv[r][j] = (delta_rj - sum_{t<r} L[r][t]
-// Linv[t][j]) / L[r][r]. Writes L to the transposed panel rows LTd ([c][r],
-// zero above the diagonal), L^-1 to Li [N][N] and its transpose after it.
-// Returns true on a non-positive or non-finite pivot (the warp's vote).
+// Cholesky factor and inverse of the N x N diagonal block Rd (shared memory,
+// row stride ld) by the whole CTA. The lower triangle is copied to the work
+// area W with the odd row stride N | 1. Right-looking factorisation, one CTA
+// barrier per column c: D[i][t] -= D[i][c] D[t][c] / D[c][c] for c < t <= i,
+// with column c scaled by 1/sqrt(D[c][c]) one step later (nothing reads it in
+// between). Right-looking inverse of L, one barrier per row r: Y[i][j] -=
+// L[i][r] Y[r][j] / L[r][r] for i > r, j <= r, with row r scaled one step
+// later. Writes L to the transposed panel rows LTd ([c][r], zero above the
+// diagonal), L^-1 to Li [N][N] and its transpose after it. Returns true on a
+// non-positive or non-finite pivot.
 template <typename T>
-__device__ __noinline__ bool diag_block(T* D, int ld, int N, T* Y, T* LTd, T* Li, int lane) {
+__device__ __noinline__ bool diag_block(const T* Rd, int ld, int N, T* W, T* LTd, T* Li) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ldd = N | 1;
+  T* D = W;
+  T* Y = W + ((N * ldd + 3) & ~3);
+  T* dinv = Y + ((N * N + 3) & ~3);  // [32] 1 / L[c][c]
+  T* dg = dinv + 32;                 // [32] L[c][c]
+#pragma unroll 1
+  for (int i = w; i < N; i += kNW) {
+    if (lane <= i) D[i * ldd + lane] = Rd[i * ld + lane];
+    if (lane < N) Y[i * N + lane] = (lane == i) ? T(1) : T(0);
+  }
+  __syncthreads();
   bool bad = false;
 #pragma unroll 1
   for (int c = 0; c < N; ++c) {
-    T sr = T(0), sr1 = T(0);
-    if (lane >= c && lane < N) {
-      const T* Lr = D + lane * ld;
-      const T* Lc = D + c * ld;
-      int t = 0;
-#pragma unroll 1
-      for (; t + 1 < c; t += 2) {
-        sr = fma(Lr[t], Lc[t], sr);
-        sr1 = fma(Lr[t + 1], Lc[t + 1], sr1);
-      }
-      if (t < c) sr = fma(Lr[t], Lc[t], sr);
-      sr = Lr[c] - (sr + sr1);
-    }
-    T piv = __shfl_sync(0xffffffffu, sr, c);
-    if (!(piv > T(0)) || !isfinite((double)piv)) {
+    T piv = D[c * ldd + c];
+    if (!(piv > T(0)) || !isfinite(piv)) {
       bad = true;
       piv = T(1);
     }
     const T d = sqrt(piv);
-    __syncwarp();
-    if (lane == c) D[c * ld + c] = d;
-    else if (lane > c && lane < N) D[lane * ld + c] = sr / d;
-    __syncwarp();
+    const T inv = T(1) / d;
+    const T inv2 = inv * inv;
+#pragma unroll 1
+    for (int i = c + 1 + w; i < N; i += kNW)
+      if (lane > c && lane <= i) D[i * ldd + lane] -= D[i * ldd + c] * D[lane * ldd + c] * inv2;
+    if (c > 0) {  // column c-1, final since the last barrier
+      const int cp = c - 1;
+      if (threadIdx.x == 0) D[cp * ldd + cp] = dg[cp];
+      else if (threadIdx.x > cp && threadIdx.x < N) D[threadIdx.x * ldd + cp] *= dinv[cp];
+    }
+    if (threadIdx.x == 0) {
+      dinv[c] = inv;
+      dg[c] = d;
+    }
+    __syncthreads();
   }
-  // inverse, lane = column j
+  {
+    const int cp = N - 1;
+    if (threadIdx.x == 0) D[cp * ldd + cp] = dg[cp];
+  }
+  __syncthreads();
+  // inverse of L
 #pragma unroll 1
   for (int r = 0; r < N; ++r) {
-    T y = T(0);
-    if (lane < N && lane <= r) {
-      const T* Lr = D + r * ld;
-      T s = (r == lane) ? T(1) : T(0), s1 = T(0);
-      int t = lane;
+    const T f = dinv[r];
 #pragma unroll 1
-      for (; t + 1 < r; t += 2) {
-        s = fma(-Lr[t], Y[t * N + lane], s);
-        s1 = fma(-Lr[t + 1], Y[(t + 1) * N + lane], s1);
-      }
-      if (t < r) s = fma(-Lr[t], Y[t * N + lane], s);
-      y = (s + s1) / Lr[r];
-      Y[r * N + lane] = y;
-    }
-    __syncwarp();
+    for (int i = r + 1 + w; i < N; i += kNW)
+      if (lane <= r) Y[i * N + lane] -= D[i * ldd + r] * (Y[r * N + lane] * f);
+    if (r > 0 && threadIdx.x < r) Y[(r - 1) * N + threadIdx.x] *= dinv[r - 1];  // row r-1 (j <= r-1)
+    __syncthreads();
   }
+  if (threadIdx.x < N) Y[(N - 1) * N + threadIdx.x] *= dinv[N - 1];
+  __syncthreads();
   T* LiT = Li + ((N * N + 3) & ~3);
-  if (lane < N) {
 #pragma unroll 1
-    for (int c = 0; c < N; ++c) LTd[(size_t)c * N + lane] = (c <= lane) ? D[lane * ld + c] : T(0);
-#pragma unroll 1
-    for (int r = 0; r < N; ++r) {
-      const T y = (r >= lane) ? Y[r * N + lane] : T(0);
-      Li[r * N + lane] = y;
-      LiT[lane * N + r] = y;
+  for (int c = w; c < N; c += kNW) {
+    if (lane < N) {
+      LTd[(size_t)c * N + lane] = (c <= lane) ? D[lane * ldd + c] : T(0);
+      const T y = (lane <= c) ? Y[c * N + lane] : T(0);  // row c of L^-1
+      Li[c * N + lane] = y;
+      LiT[lane * N + c] = y;
     }
   }
-  return __any_sync(0xffffffffu, bad);
+  return __syncthreads_or(bad ? 1 : 0) != 0;
 }
 
 // Envelope block Cholesky of the assembled A (FP64) with factor storage T, by
@@ -649,10 +658,10 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
       }
     }
     __syncthreads();
-    if (w == 0) {  // diagonal block by the leader warp
+    {  // diagonal block by the CTA (its work area: the factor ring, idle between rows)
       const bool badp = diag_block<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
-                                      Linv + mt.ioff[k], lane);
-      if (badp && lane == 0) m.flag[0] = 1;
+                                      Linv + mt.ioff[k]);
+      if (badp && threadIdx.x == 0) m.flag[0] = 1;
     }
     if (!rg.ok) m.flag[1] = 1;
     fence_proxy_async();  // the next rows copy these panels with the async proxy
