@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 METRIC = "Batched LRBMS online steps/s and p99 step latency vs plain FP64 GPU path"
 FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA loop: 1.19)
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop/clk x 2.07 GHz
+# DRAM bytes (read + write) per simulation of k_factor32 + k_refine32, from the
+# ncu capture in profiles/k_factor32_k_refine32_304sims_64x64_full.md
+# (0.334 GB + 2.367 GB for 304 simulations with the same reduced systems)
+SOLVE_DRAM_BYTES_PER_SIM = (0.334e9 + 2.367e9) / 304
 
 
 def parse_args():
@@ -417,7 +421,8 @@ def main():
         work = (f_lo + f_hi) * 1e-12
         roof = {"bound": "alu", "kernel": "k_factor32 + k_refine32" if a.solver == "mixed" else "k_csolve64",
                 "achieved": work / t_solve, "peak": work / t_min, "unit": "TFLOP/s", "frac": t_min / t_solve,
-                "traffic": None,
+                "traffic": SOLVE_DRAM_BYTES_PER_SIM * a.n_sims if a.solver == "mixed" else None,
+                "traffic_source": "ncu dram bytes of the 304-simulation capture, scaled per simulation",
                 "peak_source": ("time-weighted ALU peak of the solve's FP32 and FP64 flops: "
                                 "FP32 152 SMs x 256 flop/clk, FP64 152 SMs x 4 flop/clk, at 2.07 GHz "
                                 "(recipe unit counts and clock)"),
