@@ -244,6 +244,23 @@ def stream_bytes(N_E, Sx: int, cells: int, M: int, elem: int) -> dict:
             "reconstruct": sum(3 * cells * int(v) * elem for v in N_E) + 24 * cells * n + 8 * N}
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_sims: int, steps: int, seconds: float, world: int) -> float:
+    """Whole-job sim-steps/s: each of `world` ranks advances its own n_sims
+    simulations `steps` times (weak scaling, no data-path collective)."""
+    return world * n_sims * steps / seconds
+
+
 # ------------------------------------------------------------------ main arms
 def run_reference(a, rank: int, world: int):
     if rank != 0:
@@ -356,13 +373,10 @@ def main():
     launches = L.lrbms_launch_count(ctx) - launches0
     phase_ms, step_ms = L.lrbms_profile_read(ctx, K)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     status = L.lrbms_step(ctx, ids, 0)
     n_ok = int(np.sum(status == 0))
-    value = world * a.n_sims * K / (elapsed_ms / 1000.0)
+    value = job_throughput(a.n_sims, K, elapsed_ms / 1000.0, world)
 
     # ---- end to end through lrbms_step_io with pinned host buffers
     n_cells = a.n * a.n
@@ -373,13 +387,15 @@ def main():
     for i in range(len(ids)):
         s_in[i].copy_(s_out[i])
     L.lrbms_step_io(ctx, ids, 1, s_in, s_out)  # warm-up of the io path
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(Ke):
         for i in range(len(ids)):
             s_in[i], s_out[i] = s_out[i], s_in[i]
         L.lrbms_step_io(ctx, ids, 1, s_in, s_out)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * a.n_sims * Ke / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_throughput(a.n_sims, Ke, e2e_s, world)
 
     # ---- plain FP64 single-simulation path: one simulation, one step per call
     ctx1 = L.lrbms_create(precision=L.LRBMS_FP64, max_slots=2, hbm_budget=1 << 30, device=local)
