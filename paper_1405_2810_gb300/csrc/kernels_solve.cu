@@ -541,6 +541,48 @@ __device__ __noinline__ bool diag_block(const T* Rd, int ld, int N, T* W, T* LTd
   return __syncthreads_or(bad ? 1 : 0) != 0;
 }
 
+// Own rows [r0, r0 + nr) of the block-row panel R (row stride Wp) <- the
+// assembled blocks of A in block row k (diagonal, left and lower neighbours;
+// FP64 rounded to T), zero elsewhere and in the padding columns.
+template <typename T>
+__device__ void fill_rows(const SimDev& S, const SolveMeta& mt, T* R, int k, int jl, int Wp, int r0, int nr, int lane) {
+  const int nsub = S.n_sub, Sx = S.Sx, Nk = mt.NE[k], r1 = r0 + nr;
+  const int I = k % Sx, J = k / Sx;
+  int pc = 0;
+  #pragma unroll 1
+  for (int i = jl; i <= k; ++i) {
+    const int Ni = mt.NE[i], Np = (Ni + 3) & ~3;
+    const double* blk = nullptr;
+    if (i == k) blk = S.A + S.aoff[k];
+    else if (I > 0 && i == k - 1) blk = S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)];        // [N_i][N_k]
+    else if (J > 0 && i == k - Sx) blk = S.A + S.aoff[nsub + S.Sy * (Sx - 1) + (J - 1) * Sx + I];  // [N_i][N_k]
+    if (i == k) {  // lanes over columns
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (u < nr && lane < Nk) ? blk[(r0 + u) * Nk + lane] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < nr && lane < Np) R[(r0 + u) * Wp + pc + lane] = (T)v[u];
+    } else if (blk) {  // A_{k,i}[r][c] = blk[c][r]: lanes over own rows read coalesced
+      #pragma unroll 1
+      for (int c0 = 0; c0 < Np; c0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (c0 + u < Ni && lane < nr) ? blk[(c0 + u) * Nk + r0 + lane] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (c0 + u < Np && lane < nr) R[(r0 + lane) * Wp + pc + c0 + u] = (T)v[u];
+      }
+    } else {
+      #pragma unroll 1
+      for (int r = r0; r < r1; ++r)
+        if (lane < Np) R[r * Wp + pc + lane] = T(0);
+    }
+    pc += Np;
+  }
+  __syncwarp();
+}
+
 // Envelope block Cholesky of the assembled A (FP64) with factor storage T, by
 // the kNW warps of one CTA, each owning a contiguous range of the rows of the
 // current block row. Block row k is formed in R and processed right-looking:
@@ -574,41 +616,7 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
     FactorSeq q{k, jl, jl};
     if (w == 0)
       while (!q.done() && (int)(rg.issued - rg.consumed) < rg.nslot) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
-    {  // own rows of R <- assembled blocks of A (diagonal, left, lower), zero elsewhere and in the padding
-      const int I = k % Sx, J = k / Sx;
-      int pc = 0;
-      #pragma unroll 1
-      for (int i = jl; i <= k; ++i) {
-        const int Ni = mt.NE[i], Np = (Ni + 3) & ~3;
-        const double* blk = nullptr;
-        if (i == k) blk = S.A + S.aoff[k];
-        else if (I > 0 && i == k - 1) blk = S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)];        // [N_i][N_k]
-        else if (J > 0 && i == k - Sx) blk = S.A + S.aoff[nsub + S.Sy * (Sx - 1) + (J - 1) * Sx + I];  // [N_i][N_k]
-        if (i == k) {  // lanes over columns
-          double v[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (u < nr && lane < Nk) ? blk[(r0 + u) * Nk + lane] : 0.0;
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (u < nr && lane < Np) R[(r0 + u) * Wp + pc + lane] = (T)v[u];
-        } else if (blk) {  // A_{k,i}[r][c] = blk[c][r]: lanes over own rows read coalesced
-          #pragma unroll 1
-          for (int c0 = 0; c0 < Np; c0 += 8) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (c0 + u < Ni && lane < nr) ? blk[(c0 + u) * Nk + r0 + lane] : 0.0;
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (c0 + u < Np && lane < nr) R[(r0 + lane) * Wp + pc + c0 + u] = (T)v[u];
-          }
-        } else {
-          #pragma unroll 1
-          for (int r = r0; r < r1; ++r)
-            if (lane < Np) R[r * Wp + pc + lane] = T(0);
-        }
-        pc += Np;
-      }
-    }
+    fill_rows<T>(S, mt, R, k, jl, Wp, r0, nr, lane);
     __syncwarp();
     T* LTk = LT + mt.loff[k];
     T* Rw = R + r0 * Wp;
@@ -658,6 +666,178 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
       }
     }
     __syncthreads();
+    {  // diagonal block by the CTA (its work area: the factor ring, idle between rows)
+      const bool badp = diag_block<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
+                                      Linv + mt.ioff[k]);
+      if (badp && threadIdx.x == 0) m.flag[0] = 1;
+    }
+    if (!rg.ok) m.flag[1] = 1;
+    fence_proxy_async();  // the next rows copy these panels with the async proxy
+    __syncthreads();
+    if (m.flag[0] | m.flag[1]) {
+      const int code = m.flag[1] ? kFacTimeout : kFacPivot;
+      ring_drain<T>(rg);
+      m.ph = rg.ph;
+      m.eph = rg.eph;
+      m.used = rg.used;
+      m.fpar = rg.fpar;
+      __syncthreads();
+      return code;
+    }
+  }
+  m.ph = rg.ph;
+  m.eph = rg.eph;
+  m.used = rg.used;
+  m.fpar = rg.fpar;
+  return kFacOk;
+}
+
+// ---------------------------------------------------------------- tensor-core block products
+// FP32 block products of the factorisation on the tensor cores: mma.sync
+// m16n8k8 with TF32 operands split into high and low parts, three products
+// per term (a_lo b_hi + a_hi b_lo + a_hi b_hi, FP32 accumulation), which
+// keeps the products at FP32 accuracy.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One warp: C[r][c] (set: =, else -=) sum_{t < K} A[r][t] B(t, c) for the
+// 16-row tiles [m0, m1) of r < M and all c < N (N, K <= 32); A row-major
+// (lda), B(t, c) at B[t * ldbk + c * ldbn], C row-major (ldc). With `set`, C
+// may alias A (a tile's rows are read for all t before they are written).
+__device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ldc, int M, int N, int K,
+                                       const float* B, int ldbk, int ldbn, int m0, int m1, bool set) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+#pragma unroll 1
+  for (int mt = m0; mt < m1 && mt * 16 < M; ++mt) {
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    const int r0 = mt * 16 + g, r1 = r0 + 8;
+#pragma unroll 1
+    for (int kt = 0; kt * 8 < K; ++kt) {
+      const int k0 = kt * 8 + tq, k1 = k0 + 4;
+      float av[4];
+      av[0] = (r0 < M && k0 < K) ? A[r0 * lda + k0] : 0.f;
+      av[1] = (r1 < M && k0 < K) ? A[r1 * lda + k0] : 0.f;
+      av[2] = (r0 < M && k1 < K) ? A[r0 * lda + k1] : 0.f;
+      av[3] = (r1 < M && k1 < K) ? A[r1 * lda + k1] : 0.f;
+      uint32_t ah[4], al[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) split_tf32(av[i], ah[i], al[i]);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        if (nt * 8 < N) {
+          const int n = nt * 8 + g;
+          const float b0 = (k0 < K && n < N) ? B[k0 * ldbk + n * ldbn] : 0.f;
+          const float b1 = (k1 < K && n < N) ? B[k1 * ldbk + n * ldbn] : 0.f;
+          uint32_t bh[2], bl[2];
+          split_tf32(b0, bh[0], bl[0]);
+          split_tf32(b1, bh[1], bl[1]);
+          mma_tf32(acc[nt], al, bh);
+          mma_tf32(acc[nt], ah, bl);
+          mma_tf32(acc[nt], ah, bh);
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      if (nt * 8 < N) {
+        const int c0 = nt * 8 + 2 * tq, c1 = c0 + 1;
+        if (r0 < M && c0 < N) C[r0 * ldc + c0] = set ? acc[nt][0] : C[r0 * ldc + c0] - acc[nt][0];
+        if (r0 < M && c1 < N) C[r0 * ldc + c1] = set ? acc[nt][1] : C[r0 * ldc + c1] - acc[nt][1];
+        if (r1 < M && c0 < N) C[r1 * ldc + c0] = set ? acc[nt][2] : C[r1 * ldc + c0] - acc[nt][2];
+        if (r1 < M && c1 < N) C[r1 * ldc + c1] = set ? acc[nt][3] : C[r1 * ldc + c1] - acc[nt][3];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// FP32 envelope block Cholesky with the block products on the tensor cores,
+// by the CTA. Block row k is formed in R and processed right-looking in
+// barrier-separated phases per block j of the envelope: (1) X_j = R_j
+// L_jj^-T (L_kj = X_j), its 16-row tiles on different warps; (2) R_j' -= X_j
+// L_{j'j}^T for j' in (j, k) and R_kk -= X_j X_j^T, each block product by one
+// warp in turn. Every warp waits for every chunk of the ring before it
+// releases it (whether it used it or not), so no warp releases a slot ahead
+// of the chunk's user. The diagonal block is factored by the CTA as in
+// cfactor. Same results contract as cfactor.
+__device__ int cfactor_mma(const SimDev& S, float* LT, float* Linv, CtaSmem<float>& m) {
+  using T = float;
+  const SolveMeta& mt = m.mt;
+  const int nsub = S.n_sub, Sx = S.Sx;
+  const int lane = threadIdx.x & 31, w = vwarp();
+  T* R = m.R;
+  Ring<T> rg{m.ring, m.full, m.empty, m.dl, kRing, 0u, 0u, m.ph, m.eph, m.used, m.fpar, true};
+#pragma unroll 1
+  for (int k = 0; k < nsub; ++k) {
+    const int jl = jlo_of(k, Sx);
+    const int base = mt.xoff[jl];
+    const int Nk = mt.NE[k];
+    const int Wc = padded_width(mt, jl, k);
+    const int Wp = row_stride<T>(Wc);
+    const int pck = Wc - ((Nk + 3) & ~3);
+    const int r0 = (w * Nk) / kNW, r1 = ((w + 1) * Nk) / kNW, nr = r1 - r0;
+    const int mtn = (Nk + 15) >> 4;
+    FactorSeq q{k, jl, jl};
+    if (w == 0)
+      while (!q.done() && (int)(rg.issued - rg.consumed) < rg.nslot) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+    fill_rows<T>(S, mt, R, k, jl, Wp, r0, nr, lane);
+    __syncthreads();
+    T* LTk = LT + mt.loff[k];
+    int pcj = 0, pair = 0;
+#pragma unroll 1
+    for (int j = jl; j < k; ++j) {
+      const int Nj = mt.NE[j];
+      const int Njp4 = (Nj + 3) & ~3;
+      {  // X_j = R_j L_jj^-T; B(t, c) = (L_jj^-1)^T[t][c]
+        const T* LiT = ring_wait<T>(rg);
+        if (w < mtn) mma_block(R + pcj, Wp, R + pcj, Wp, Nk, Nj, Nj, LiT, Nj, 1, w, w + 1, true);
+        ring_release<T>(rg, lane, 1);
+        if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+      }
+      __syncthreads();
+      int pcjp = pcj + Njp4;
+#pragma unroll 1
+      for (int jp = j + 1; jp < k; ++jp) {  // R_j' -= X_j L_{j'j}^T; B(t, c') = chunk[t][c']
+        const int Njp = mt.NE[jp];
+        const T* Lc = ring_wait<T>(rg);
+        if ((pair++ % kNW) == w) mma_block(R + pcj, Wp, R + pcjp, Wp, Nk, Njp, Nj, Lc, Njp, 1, 0, 2, false);
+        ring_release<T>(rg, lane, 1);
+        if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+        pcjp += (Njp + 3) & ~3;
+      }
+      // R_kk -= X_j X_j^T; B(t, c) = X_j[c][t]
+      if ((pair++ % kNW) == w) mma_block(R + pcj, Wp, R + pck, Wp, Nk, Nk, Nj, R + pcj, 1, Wp, 0, 2, false);
+      __syncthreads();
+      pcj += Njp4;
+    }
+    {  // L_kj = X_j into the transposed panel (lanes over rows: coalesced), all warps
+      int pc = 0;
+#pragma unroll 1
+      for (int j = jl; j < k; ++j) {
+        const int Nj = mt.NE[j], gj = mt.xoff[j] - base;
+        if (lane < Nk)
+#pragma unroll 1
+          for (int c = w; c < Nj; c += kNW) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
+        pc += (Nj + 3) & ~3;
+      }
+    }
     {  // diagonal block by the CTA (its work area: the factor ring, idle between rows)
       const bool badp = diag_block<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
                                       Linv + mt.ioff[k]);
@@ -1150,7 +1330,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_factor32(const SimDev* __restri
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
-  const int f = cfactor<float>(S, reinterpret_cast<float*>(S.L), reinterpret_cast<float*>(S.Linv), m);
+  const int f = cfactor_mma(S, reinterpret_cast<float*>(S.L), reinterpret_cast<float*>(S.Linv), m);
   if (f != kFacOk && threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
 }
 
@@ -1236,7 +1416,7 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
     float* Lf = reinterpret_cast<float*>(S.L);
     float* Lif = reinterpret_cast<float*>(S.Linv);
     CtaSmem<float> mf = cta_carve_and_load<float>(S, b);
-    const int f = cfactor<float>(S, Lf, Lif, mf);
+    const int f = cfactor_mma(S, Lf, Lif, mf);
     if (f == kFacOk) {
       const int r = csolve_refine<float>(S, Lf, Lif, iters, mf);
       if (r == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
