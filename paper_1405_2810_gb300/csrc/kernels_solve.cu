@@ -769,11 +769,11 @@ __device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ld
 }
 
 // FP32 envelope block Cholesky with the block products on the tensor cores,
-// by the CTA. Block row k is formed in R and processed right-looking in
-// barrier-separated phases per block j of the envelope: (1) X_j = R_j
-// L_jj^-T (L_kj = X_j), its 16-row tiles on different warps; (2) R_j' -= X_j
-// L_{j'j}^T for j' in (j, k) and R_kk -= X_j X_j^T, each block product by one
-// warp in turn. Every warp waits for every chunk of the ring before it
+// by the CTA. Block row k is formed in R and processed right-looking in one
+// barrier-separated phase per block j of the envelope (X_j = R_j L_jj^-T =
+// L_kj final at its start): R_j' -= X_j L_{j'j}^T for j' in (j, k), each
+// block product by one warp in turn; X_{j+1} by the warp that applied the
+// update into block j+1; R_kk -= X_j X_j^T. Every warp waits for every chunk of the ring before it
 // releases it (whether it used it or not), so no warp releases a slot ahead
 // of the chunk's user. The diagonal block is factored by the CTA as in
 // cfactor. Same results contract as cfactor.
@@ -800,30 +800,43 @@ __device__ int cfactor_mma(const SimDev& S, float* LT, float* Linv, CtaSmem<floa
     fill_rows<T>(S, mt, R, k, jl, Wp, r0, nr, lane);
     __syncthreads();
     T* LTk = LT + mt.loff[k];
-    int pcj = 0, pair = 0;
+    if (jl < k) {  // X_jl = R_jl L_jl,jl^-T, its 16-row tiles on different warps
+      const int N0 = mt.NE[jl];
+      const T* LiT = ring_wait<T>(rg);
+      if (w < mtn) mma_block(R, Wp, R, Wp, Nk, N0, N0, LiT, N0, 1, w, w + 1, true);
+      ring_release<T>(rg, lane, 1);
+      if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+      __syncthreads();
+    }
+    int pcj = 0;
 #pragma unroll 1
     for (int j = jl; j < k; ++j) {
+      // phase j: X_j is final. Tasks in chunk order: R_j' -= X_j L_{j'j}^T for
+      // j' = j+1 .. k-1, then X_{j+1} = R_{j+1} L^-T (by the warp that applied
+      // the update into block j+1), then R_kk -= X_j X_j^T. One barrier per phase.
       const int Nj = mt.NE[j];
       const int Njp4 = (Nj + 3) & ~3;
-      {  // X_j = R_j L_jj^-T; B(t, c) = (L_jj^-1)^T[t][c]
-        const T* LiT = ring_wait<T>(rg);
-        if (w < mtn) mma_block(R + pcj, Wp, R + pcj, Wp, Nk, Nj, Nj, LiT, Nj, 1, w, w + 1, true);
-        ring_release<T>(rg, lane, 1);
-        if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
-      }
-      __syncthreads();
+      const int crit = (j - jl) % kNW;  // owner of block j+1's update and of X_{j+1}
+      int task = 0;
       int pcjp = pcj + Njp4;
 #pragma unroll 1
-      for (int jp = j + 1; jp < k; ++jp) {  // R_j' -= X_j L_{j'j}^T; B(t, c') = chunk[t][c']
+      for (int jp = j + 1; jp < k; ++jp) {
         const int Njp = mt.NE[jp];
         const T* Lc = ring_wait<T>(rg);
-        if ((pair++ % kNW) == w) mma_block(R + pcj, Wp, R + pcjp, Wp, Nk, Njp, Nj, Lc, Njp, 1, 0, 2, false);
+        if ((crit + task++) % kNW == w) mma_block(R + pcj, Wp, R + pcjp, Wp, Nk, Njp, Nj, Lc, Njp, 1, 0, 2, false);
         ring_release<T>(rg, lane, 1);
         if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
         pcjp += (Njp + 3) & ~3;
       }
+      if (j + 1 < k) {  // X_{j+1}
+        const int N1 = mt.NE[j + 1];
+        const T* LiT = ring_wait<T>(rg);
+        if (w == crit) mma_block(R + pcj + Njp4, Wp, R + pcj + Njp4, Wp, Nk, N1, N1, LiT, N1, 1, 0, 2, true);
+        ring_release<T>(rg, lane, 1);
+        if (w == 0 && !q.done()) factor_issue<T>(rg, q, mt, Sx, LT, Linv, lane);
+      }
       // R_kk -= X_j X_j^T; B(t, c) = X_j[c][t]
-      if ((pair++ % kNW) == w) mma_block(R + pcj, Wp, R + pck, Wp, Nk, Nk, Nj, R + pcj, 1, Wp, 0, 2, false);
+      if ((crit + task++) % kNW == w) mma_block(R + pcj, Wp, R + pck, Wp, Nk, Nk, Nj, R + pcj, 1, Wp, 0, 2, false);
       __syncthreads();
       pcj += Njp4;
     }
