@@ -1,0 +1,116 @@
+"""Continuous batching of LRBMS simulations over the C ABI.
+
+Requests (a problem, its offline data and a number of online steps) arrive
+at any tick. A request is admitted as soon as the context's HBM budget and
+slots allow (lrbms_offline_load succeeds; LRBMS_E_BUDGET leaves it queued, in
+arrival order), every tick advances all admitted simulations by one online
+step in a single lrbms_step call (Algorithm 3, step 5, batched), and a
+simulation that has taken its steps is read out and released, which frees
+its memory for the queue. All arithmetic runs in the library's kernels; this
+module only schedules. Because the kernels reduce in a fixed order per
+simulation, each result is the same as the simulation run alone.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+
+@dataclass
+class Request:
+    rid: int
+    problem: dict
+    offline: dict
+    n_steps: int
+    arrival_tick: int = 0
+    sim_id: int = -1
+    steps_done: int = 0
+    admitted_tick: int = -1
+    finished_tick: int = -1
+    result: dict = field(default_factory=dict)
+
+
+class Server:
+    """Admission by budget, one batched step per tick, retirement.
+
+    backend: the ctypes binding (paper_1405_2810_gb300.lrbms) or an object
+    with the same functions (lrbms_offline_load, lrbms_step, lrbms_get_state,
+    lrbms_release, LrbmsError, LRBMS_E_BUDGET)."""
+
+    def __init__(self, backend, ctx):
+        self.L = backend
+        self.ctx = ctx
+        self.queue: deque[Request] = deque()
+        self.active: list[Request] = []
+        self.done: list[Request] = []
+        self.tick_ms: list[float] = []
+        self.tick = 0
+        self._next = 0
+
+    def submit(self, problem: dict, offline: dict, n_steps: int) -> int:
+        r = Request(self._next, problem, offline, int(n_steps), arrival_tick=self.tick)
+        self._next += 1
+        self.queue.append(r)
+        return r.rid
+
+    def _admit(self):
+        while self.queue:
+            r = self.queue[0]
+            try:
+                r.sim_id = self.L.lrbms_offline_load(self.ctx, r.problem, r.offline)
+            except self.L.LrbmsError as e:
+                if e.code == self.L.LRBMS_E_BUDGET:
+                    break  # wait for memory to be freed; keep arrival order
+                raise
+            r.admitted_tick = self.tick
+            self.queue.popleft()
+            self.active.append(r)
+
+    def step(self):
+        """One tick: admit, advance every active simulation by one step, retire."""
+        self._admit()
+        if self.active:
+            ids = [r.sim_id for r in self.active]
+            t0 = time.perf_counter()
+            st = self.L.lrbms_step(self.ctx, ids, 1)
+            self.tick_ms.append(1e3 * (time.perf_counter() - t0))
+            still = []
+            for r, code in zip(self.active, st):
+                r.steps_done += 1
+                if code != 0 or r.steps_done >= r.n_steps:
+                    r.result = self._read(r, int(code))
+                    self.L.lrbms_release(self.ctx, r.sim_id)
+                    r.finished_tick = self.tick
+                    self.done.append(r)
+                else:
+                    still.append(r)
+            self.active = still
+        self.tick += 1
+
+    def _read(self, r: Request, code: int) -> dict:
+        import numpy as np
+        s = np.empty(int(r.problem["nx"]) * int(r.problem["ny"]))
+        t, out = self.L.lrbms_get_state(self.ctx, r.sim_id, s)
+        return {"status": code, "s": s, "t": t, "outflow": out, "steps": r.steps_done}
+
+    def run(self, arrivals=(), max_ticks: int = 100000):
+        """arrivals: iterable of (tick, problem, offline, n_steps); runs until
+        every request has finished."""
+        pending = sorted(arrivals, key=lambda a: a[0])
+        i = 0
+        while (i < len(pending) or self.queue or self.active) and self.tick < max_ticks:
+            while i < len(pending) and pending[i][0] <= self.tick:
+                _, p, o, n = pending[i]
+                self.submit(p, o, n)
+                i += 1
+            self.step()
+        return sorted(self.done, key=lambda r: r.rid)
+
+    def latency_ms(self):
+        """p50 and p99 of the per-tick step latency (host-measured, ms)."""
+        import numpy as np
+        if not self.tick_ms:
+            return None, None
+        a = np.sort(np.array(self.tick_ms))
+        return float(np.percentile(a, 50)), float(np.percentile(a, 99))

@@ -1,0 +1,67 @@
+"""Serving loop logic (admission by budget in arrival order, one batched step
+per tick, retirement) against a fake backend on CPU."""
+import numpy as np
+import pytest
+
+from paper_1405_2810_gb300.serving import Server
+
+
+class FakeLib:
+    LRBMS_E_BUDGET = -2
+
+    class LrbmsError(Exception):
+        def __init__(self, code, msg=""):
+            super().__init__(msg)
+            self.code = code
+
+    def __init__(self, capacity):
+        self.capacity = capacity  # simultaneous simulations
+        self.live = {}
+        self.next_id = 0
+        self.calls = []
+
+    def lrbms_offline_load(self, ctx, problem, offline):
+        if len(self.live) >= self.capacity:
+            raise self.LrbmsError(self.LRBMS_E_BUDGET, "budget")
+        sid = self.next_id
+        self.next_id += 1
+        self.live[sid] = {"steps": 0, "nx": problem["nx"], "ny": problem["ny"]}
+        return sid
+
+    def lrbms_step(self, ctx, ids, n):
+        self.calls.append(list(ids))
+        for i in ids:
+            self.live[i]["steps"] += n
+        return np.zeros(len(ids), dtype=np.int32)
+
+    def lrbms_get_state(self, ctx, sid, s):
+        s[:] = self.live[sid]["steps"]
+        return float(self.live[sid]["steps"]), 0.0
+
+    def lrbms_release(self, ctx, sid):
+        del self.live[sid]
+
+
+def test_admission_in_arrival_order_and_retirement():
+    lib = FakeLib(capacity=2)
+    srv = Server(lib, ctx=None)
+    prob = {"nx": 2, "ny": 2}
+    arrivals = [(0, prob, None, 3), (0, prob, None, 1), (0, prob, None, 2), (4, prob, None, 2)]
+    done = srv.run(arrivals)
+    assert [r.rid for r in done] == [0, 1, 2, 3]
+    assert all(r.result["steps"] == r.n_steps for r in done)
+    assert all(np.all(r.result["s"] == r.n_steps) for r in done)
+    # at most two simulations live at once; request 2 waits for request 1 to retire
+    assert max(len(c) for c in lib.calls) == 2
+    assert done[2].admitted_tick == done[1].finished_tick + 1
+    assert not lib.live  # every slot released
+
+
+def test_budget_error_other_than_budget_is_raised():
+    class Broken(FakeLib):
+        def lrbms_offline_load(self, ctx, problem, offline):
+            raise self.LrbmsError(-7, "format")
+    srv = Server(Broken(1), ctx=None)
+    srv.submit({"nx": 1, "ny": 1}, None, 1)
+    with pytest.raises(Broken.LrbmsError):
+        srv.step()
