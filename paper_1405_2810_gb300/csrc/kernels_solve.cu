@@ -707,7 +707,7 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   lo = to_tf32(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -738,20 +738,25 @@ __device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ld
       uint32_t ah[4], al[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) split_tf32(av[i], ah[i], al[i]);
+      uint32_t bh[4][2], bl[4][2];
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
-        if (nt * 8 < N) {
-          const int n = nt * 8 + g;
-          const float b0 = (k0 < K && n < N) ? B[k0 * ldbk + n * ldbn] : 0.f;
-          const float b1 = (k1 < K && n < N) ? B[k1 * ldbk + n * ldbn] : 0.f;
-          uint32_t bh[2], bl[2];
-          split_tf32(b0, bh[0], bl[0]);
-          split_tf32(b1, bh[1], bl[1]);
-          mma_tf32(acc[nt], al, bh);
-          mma_tf32(acc[nt], ah, bl);
-          mma_tf32(acc[nt], ah, bh);
-        }
+        const int n = nt * 8 + g;
+        const float b0 = (nt * 8 < N && k0 < K && n < N) ? B[k0 * ldbk + n * ldbn] : 0.f;
+        const float b1 = (nt * 8 < N && k1 < K && n < N) ? B[k1 * ldbk + n * ldbn] : 0.f;
+        split_tf32(b0, bh[nt][0], bl[nt][0]);
+        split_tf32(b1, bh[nt][1], bl[nt][1]);
       }
+      // term by term over the independent accumulators (small terms first)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+        if (nt * 8 < N) mma_tf32(acc[nt], al, bh[nt]);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+        if (nt * 8 < N) mma_tf32(acc[nt], ah, bl[nt]);
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+        if (nt * 8 < N) mma_tf32(acc[nt], ah, bh[nt]);
     }
     __syncwarp();
 #pragma unroll
