@@ -111,7 +111,7 @@ __global__ void k_assemble32(const SimDev* __restrict__ sims, const int* __restr
 // mbarrier of its slot; consumers release a slot on its "empty" mbarrier
 // before the producer (lane 0 of warp 0) refills it. The copies of the next
 // chunks run while the CTA computes on the current one. Every wait is bounded.
-constexpr int kNW = 4;                       // warps per simulation
+constexpr int kNW = kSolveWarps;             // warps per simulation
 constexpr int kThreads = 32 * kNW;
 constexpr int kRing = 4;                     // slots of the factorisation ring
 constexpr int kSlot = kMaxNE * kMaxNE + 8;   // elements per slot: one 32 x 32 block + alignment slack
@@ -974,9 +974,9 @@ __device__ __forceinline__ int n_citems(const SolveMeta& mt, int Sx, int nsub, i
   return k <= nsub - 2 ? k - jlo_of(k + 1, Sx) : 0;
 }
 
-template <typename T>
-__device__ __forceinline__ bool scursor_item(const SolveMeta& mt, int Sx, int nsub, int w, const SCursor& c,
-                                             const T* LT, const T* Linv, const T** src, long long* off, int* cnt) {
+constexpr int kChNone = 0, kChPanel = 1, kChInverse = 2;
+__device__ int scursor_item(const SolveMeta& mt, int Sx, int nsub, int w, const SCursor& c, long long* off,
+                            int* cnt) {
   const int k = c.k;
   if (w == 0) {
     const bool has_a = c.dir > 0 ? k >= 1 : k <= nsub - 2;
@@ -989,20 +989,18 @@ __device__ __forceinline__ bool scursor_item(const SolveMeta& mt, int Sx, int ns
         *off = mt.loff[k + 1] + (long long)(mt.xoff[k] - mt.xoff[jlo_of(k + 1, Sx)]) * mt.NE[k + 1];
         *cnt = mt.NE[k] * mt.NE[k + 1];
       }
-      *src = LT;
-      return true;
+      return kChPanel;
     }
     if (c.sub == ia + 1) {
       const int Nk = mt.NE[k];
       *off = mt.ioff[k] + (c.dir > 0 ? ((Nk * Nk + 3) & ~3) : 0);
       *cnt = Nk * Nk;
-      *src = Linv;
-      return true;
+      return kChInverse;
     }
-    return false;
+    return kChNone;
   }
   const int i = (w - 1) + c.sub * (kNW - 1);
-  if (i >= n_citems(mt, Sx, nsub, c.dir, k)) return false;
+  if (i >= n_citems(mt, Sx, nsub, c.dir, k)) return kChNone;
   if (c.dir > 0) {
     const int kk = k + 1 + i;
     *off = mt.loff[kk] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(kk, Sx)]) * mt.NE[kk];
@@ -1012,26 +1010,137 @@ __device__ __forceinline__ bool scursor_item(const SolveMeta& mt, int Sx, int ns
     *off = mt.loff[k + 1] + (long long)(mt.xoff[j] - mt.xoff[jl1]) * mt.NE[k + 1];
     *cnt = mt.NE[j] * mt.NE[k + 1];
   }
-  *src = LT;
-  return true;
+  return kChPanel;
+}
+
+// Chunk descriptor of the copy schedule: element offset (bits 0-39) into the
+// panels, or into the diagonal inverses if bit 63 is set; element count in
+// bits 40-50.
+constexpr unsigned long long kDescOffMask = (1ull << 40) - 1;
+constexpr unsigned long long kDescInverse = 1ull << 63;
+
+// The copy schedule of a simulation, by one thread: the word layout is that
+// of sched_words (list starts relative to the buffer, then the lists); the
+// order is the consumption order of csubstitute, forward then backward. The
+// schedule depends only on the basis sizes, so it is built once at load.
+__device__ void build_sched(const SimDev& S, unsigned long long* out) {
+  const SolveMeta mt{const_cast<int*>(S.NE), const_cast<int*>(S.xoff), const_cast<long long*>(S.loff),
+                     const_cast<long long*>(S.ioff)};
+  const int nsub = S.n_sub, Sx = S.Sx;
+  unsigned long long n = kNW + 1;
+  #pragma unroll 1
+  for (int w = 0; w < kNW; ++w) {
+    out[w] = n;
+    #pragma unroll 1
+    for (int dir = 1; dir >= -1; dir -= 2) {
+      SCursor c{dir, dir > 0 ? 0 : nsub - 1, 0};
+      #pragma unroll 1
+      while (dir > 0 ? c.k < nsub : c.k >= 0) {
+        long long off;
+        int cnt;
+        const int kind = scursor_item(mt, Sx, nsub, w, c, &off, &cnt);
+        if (kind == kChNone) {
+          c.k += dir;
+          c.sub = 0;
+          continue;
+        }
+        out[n++] = (unsigned long long)off | ((unsigned long long)cnt << 40) | (kind == kChInverse ? kDescInverse : 0ull);
+        ++c.sub;
+      }
+    }
+  }
+  out[kNW] = n;
+}
+
+__global__ void k_sched(const SimDev* __restrict__ sp) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) build_sched(*sp, const_cast<unsigned long long*>(sp->sched));
+}
+
+// The warp's copy schedule, 32 descriptors at a time in registers (lane l
+// holds descriptor base + l in cur and base + 32 + l in nxt).
+struct SFeed {
+  const unsigned long long* d;
+  int n, next, base;
+  unsigned long long cur, nxt;
+};
+
+__device__ __forceinline__ SFeed sfeed_open(const unsigned long long* sched, int w, int lane) {
+  SFeed f;
+  const long long s0 = (long long)sched[w], s1 = (long long)sched[w + 1];
+  f.d = sched + s0;
+  f.n = (int)(s1 - s0);
+  f.next = 0;
+  f.base = 0;
+  f.cur = lane < f.n ? f.d[lane] : 0ull;
+  f.nxt = 32 + lane < f.n ? f.d[32 + lane] : 0ull;
+  return f;
 }
 
 // Issue the warp's next chunks while they fit.
 template <typename T>
-__device__ __forceinline__ void srefill(WRing<T>& r, SCursor& c, const SolveMeta& mt, int Sx, int nsub, int w,
-                                        const T* LT, const T* Linv, int lane) {
-  while (c.dir > 0 ? c.k < nsub : c.k >= 0) {
-    const T* src;
-    long long off;
-    int cnt;
-    if (!scursor_item<T>(mt, Sx, nsub, w, c, LT, Linv, &src, &off, &cnt)) {
-      c.k += c.dir;
-      c.sub = 0;
-      continue;
+__device__ __forceinline__ void srefill(WRing<T>& r, SFeed& f, const T* LT, const T* Linv, int lane) {
+  #pragma unroll 1
+  while (f.next < f.n) {
+    if (f.next - f.base == 32) {
+      f.cur = f.nxt;
+      f.base += 32;
+      const int j = f.base + 32 + lane;
+      f.nxt = j < f.n ? f.d[j] : 0ull;
     }
-    if (!wring_try_issue<T>(r, src, off, cnt, lane)) return;
-    ++c.sub;
+    const unsigned long long dsc = __shfl_sync(0xffffffffu, f.cur, f.next - f.base);
+    const T* src = (dsc & kDescInverse) ? Linv : LT;
+    if (!wring_try_issue<T>(r, src, (long long)(dsc & kDescOffMask), (int)((dsc >> 40) & 0x7ff), lane)) return;
+    ++f.next;
   }
+}
+
+// sum_{g < K} P[g ld] v[g] (P already offset to the lane's column), four
+// independent chains so that the shared-memory loads overlap.
+template <typename T>
+__device__ __forceinline__ T dot_col(const T* P, int ld, const T* v, int K) {
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int g = 0;
+#pragma unroll 2
+  for (; g + 3 < K; g += 4) {
+    a0 = fma(P[g * ld], v[g], a0);
+    a1 = fma(P[(g + 1) * ld], v[g + 1], a1);
+    a2 = fma(P[(g + 2) * ld], v[g + 2], a2);
+    a3 = fma(P[(g + 3) * ld], v[g + 3], a3);
+  }
+  if (g < K) {
+    a0 = fma(P[g * ld], v[g], a0);
+    if (g + 1 < K) a1 = fma(P[(g + 1) * ld], v[g + 1], a1);
+    if (g + 2 < K) a2 = fma(P[(g + 2) * ld], v[g + 2], a2);
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+// sum_{c < K} Pr[c] v[c] over the lane's own row Pr, starting at column c0
+// and wrapping (lanes start at different columns: rows of even length K
+// would otherwise fall into the same shared-memory banks); four chains.
+template <typename T>
+__device__ __forceinline__ T dot_row(const T* Pr, const T* v, int K, int c0) {
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int c = c0, u = 0;
+#pragma unroll 2
+  for (; u + 3 < K; u += 4) {
+    const int c1 = c + 1 == K ? 0 : c + 1;
+    const int c2 = c1 + 1 == K ? 0 : c1 + 1;
+    const int c3 = c2 + 1 == K ? 0 : c2 + 1;
+    a0 = fma(Pr[c], v[c], a0);
+    a1 = fma(Pr[c1], v[c1], a1);
+    a2 = fma(Pr[c2], v[c2], a2);
+    a3 = fma(Pr[c3], v[c3], a3);
+    c = c3 + 1 == K ? 0 : c3 + 1;
+  }
+  if (u < K) {
+    const int c1 = c + 1 == K ? 0 : c + 1;
+    const int c2 = c1 + 1 == K ? 0 : c1 + 1;
+    a0 = fma(Pr[c], v[c], a0);
+    if (u + 1 < K) a1 = fma(Pr[c1], v[c1], a1);
+    if (u + 2 < K) a2 = fma(Pr[c2], v[c2], a2);
+  }
+  return (a0 + a1) + (a2 + a3);
 }
 
 // Solve L L^T out = in with the transposed panels (arithmetic in T) by the
@@ -1053,8 +1162,8 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
     y[i] = (T)in[i];
     z[i] = T(0);
   }
-  SCursor cur{1, 0, 0};
-  srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
+  SFeed fd = sfeed_open(S.sched, w, lane);
+  srefill<T>(rg, fd, LT, Linv, lane);
   __syncthreads();
   // forward
   #pragma unroll 1
@@ -1066,39 +1175,17 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
         const int Nj = mt.NE[k - 1];
         const T* P = wring_wait<T>(rg);  // [g][c]
         const T* yj = y + mt.xoff[k - 1];
-        if (lane < Nk) {
-          T a1 = T(0), a2 = T(0), a3 = T(0);
-          int g = 0;
-          #pragma unroll 1
-          for (; g + 3 < Nj; g += 4) {
-            t = fma(-P[g * Nk + lane], yj[g], t);
-            a1 = fma(-P[(g + 1) * Nk + lane], yj[g + 1], a1);
-            a2 = fma(-P[(g + 2) * Nk + lane], yj[g + 2], a2);
-            a3 = fma(-P[(g + 3) * Nk + lane], yj[g + 3], a3);
-          }
-          #pragma unroll 1
-          for (; g < Nj; ++g) t = fma(-P[g * Nk + lane], yj[g], t);
-          t += (a1 + a2) + a3;
-        }
+        if (lane < Nk) t -= dot_col<T>(P + lane, Nk, yj, Nj);
         wring_release<T>(rg);
-        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
       if (lane < Nk) tv[lane] = t;
       __syncwarp();
       const T* LiT = wring_wait<T>(rg);
-      T yk = T(0), yk1 = T(0);
-      if (lane < Nk) {  // y_k[c] = sum_{t <= c} Linv[c][t] tv[t]
-        int u = 0;
-        #pragma unroll 1
-        for (; u + 1 <= lane; u += 2) {
-          yk = fma(LiT[u * Nk + lane], tv[u], yk);
-          yk1 = fma(LiT[(u + 1) * Nk + lane], tv[u + 1], yk1);
-        }
-        if (u <= lane) yk = fma(LiT[u * Nk + lane], tv[u], yk);
-        yk += yk1;
-      }
+      // y_k[c] = sum_{t <= c} Linv[c][t] tv[t] (the stored inverse holds its zeros)
+      const T yk = lane < Nk ? dot_col<T>(LiT + lane, Nk, tv, Nk) : T(0);
       wring_release<T>(rg);
-        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       if (lane < Nk) y[xk + lane] = yk;
     } else if (k >= 1) {  // t_k' -= L_{k',k-1} y_{k-1} for the warp's rows k'
       const int Nj = mt.NE[k - 1];
@@ -1108,27 +1195,16 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       for (int i = w - 1; i < nc; i += kNW - 1) {
         const int kk = k + 1 + i, N2 = mt.NE[kk];
         const T* P = wring_wait<T>(rg);  // [g][c]
-        if (lane < N2) {
-          T a0 = T(0), a1 = T(0);
-          int g = 0;
-          #pragma unroll 1
-          for (; g + 1 < Nj; g += 2) {
-            a0 = fma(P[g * N2 + lane], yj[g], a0);
-            a1 = fma(P[(g + 1) * N2 + lane], yj[g + 1], a1);
-          }
-          if (g < Nj) a0 = fma(P[g * N2 + lane], yj[g], a0);
-          y[mt.xoff[kk] + lane] -= a0 + a1;
-        }
+        if (lane < N2) y[mt.xoff[kk] + lane] -= dot_col<T>(P + lane, N2, yj, Nj);
         wring_release<T>(rg);
-        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
     }
-    srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
+    srefill<T>(rg, fd, LT, Linv, lane);
     __syncthreads();
   }
-  // backward
-  cur = SCursor{-1, nsub - 1, 0};
-  srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
+  // backward (the feed runs on into the backward chunks)
+  srefill<T>(rg, fd, LT, Linv, lane);
   #pragma unroll 1
   for (int k = nsub - 1; k >= 0; --k) {
     const int Nk = mt.NE[k], xk = mt.xoff[k];
@@ -1137,29 +1213,17 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
         const int N2 = mt.NE[k + 1];
         const T* P = wring_wait<T>(rg);  // [g][c]: g in block k, c in block k+1
         const T* zn = z + mt.xoff[k + 1];
-        if (lane < Nk) {
-          const int g = lane;
-          int c = (N2 & 1) ? 0 : g % N2;
-          T a0 = T(0);
-          #pragma unroll 1
-          for (int u = 0; u < N2; ++u) {
-            a0 = fma(P[g * N2 + c], zn[c], a0);
-            if (++c == N2) c = 0;
-          }
-          z[xk + g] += a0;
-        }
+        if (lane < Nk) z[xk + lane] += dot_row<T>(P + lane * N2, zn, N2, (N2 & 1) ? 0 : lane % N2);
         wring_release<T>(rg);
-        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
       const T* Li = wring_wait<T>(rg);
       if (lane < Nk) tv[lane] = y[xk + lane] - z[xk + lane];
       __syncwarp();
-      T zc = T(0);
-      if (lane < Nk)
-        #pragma unroll 1
-        for (int r = lane; r < Nk; ++r) zc = fma(Li[r * Nk + lane], tv[r], zc);
+      // z_k[c] = sum_{r >= c} Linv[r][c] tv[r] (zeros stored above the diagonal)
+      const T zc = lane < Nk ? dot_col<T>(Li + lane, Nk, tv, Nk) : T(0);
       wring_release<T>(rg);
-        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       if (lane < Nk) z[xk + lane] = zc;
     } else if (k <= nsub - 2) {  // p_j += L_{k+1,j}^T z_{k+1} for the warp's j < k
       const int N2 = mt.NE[k + 1];
@@ -1170,22 +1234,12 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       for (int i = w - 1; i < nc; i += kNW - 1) {
         const int j = jl1 + i, Nj = mt.NE[j];
         const T* P = wring_wait<T>(rg);  // [g][c]: g in block j, c in block k+1
-        if (lane < Nj) {
-          const int g = lane;
-          int c = (N2 & 1) ? 0 : g % N2;
-          T a0 = T(0);
-          #pragma unroll 1
-          for (int u = 0; u < N2; ++u) {
-            a0 = fma(P[g * N2 + c], zn[c], a0);
-            if (++c == N2) c = 0;
-          }
-          z[mt.xoff[j] + g] += a0;
-        }
+        if (lane < Nj) z[mt.xoff[j] + lane] += dot_row<T>(P + lane * N2, zn, N2, (N2 & 1) ? 0 : lane % N2);
         wring_release<T>(rg);
-        srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
     }
-    srefill<T>(rg, cur, mt, Sx, nsub, w, LT, Linv, lane);
+    srefill<T>(rg, fd, LT, Linv, lane);
     __syncthreads();
   }
   #pragma unroll 1
@@ -1424,6 +1478,7 @@ __global__ void k_noalloc_tables(SimDev S) {
   loff[0] = 0;
   ioff[0] = 0;
   solve_offsets(S.n_sub, S.Sx, NE, xoff, loff, ioff);
+  build_sched(S, const_cast<unsigned long long*>(S.sched));
   S.status[0] = kStOk;
 }
 
@@ -1464,6 +1519,8 @@ void launch_assemble(const SimDev* sims, const int* active, int n_active, int ma
   else
     k_assemble<<<dim3(max_blocks, n_active), 128, 0, st>>>(sims, active);
 }
+
+void launch_sched(const SimDev* sim, cudaStream_t st) { k_sched<<<1, 32, 0, st>>>(sim); }
 
 size_t solve_smem_bytes(int n_sub, int panel_words, int max_w, int N, size_t elem) {
   (void)max_w;
@@ -1542,6 +1599,7 @@ extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double*
   const size_t o_y = off; off = up(off + 16 * (size_t)N);
   const size_t o_rv = off; off = up(off + 8 * (size_t)N);
   const size_t o_dv = off; off = up(off + 8 * (size_t)N);
+  const size_t o_sched = off; off = up(off + 8 * sched_words(n_sub, Sx));
   if (off > kNoAllocBytes) return LRBMS_E_BUDGET;  // system larger than the static scratch
 
   int dev = 0;
@@ -1560,6 +1618,7 @@ extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double*
   S.ioff = (const long long*)(base + o_ioff); S.status = (int*)(base + o_status);
   S.L = (double*)(base + o_L); S.Linv = (double*)(base + o_Li); S.y = (double*)(base + o_y);
   S.rv = (double*)(base + o_rv); S.dv = (double*)(base + o_dv);
+  S.sched = (const unsigned long long*)(base + o_sched);
   S.A = const_cast<double*>(A); S.b = const_cast<double*>(rhs); S.x = x;
   S.panel_words = panel_words;
   S.max_w = max_w;

@@ -320,6 +320,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
   const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
   const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(8);
+  const size_t o_sched = L.add(8 * lrbms::sched_words(n_sub, Sx));
   (void)d_tot;
 
   const size_t aoffset = ctx->arena.alloc(L.total);
@@ -361,6 +362,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
   d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);
   d.status = (int*)P(o_status); d.steps = (int*)P(o_steps); d.info = (int*)P(o_info);
+  d.sched = (const unsigned long long*)P(o_sched);
   d.lam = (double*)P(o_lam); d.fw = (double*)P(o_fw); d.inv_pv = (double*)P(o_ipv); d.fcoef = (double*)P(o_fc);
 
   cudaStream_t st = ctx->stream;
@@ -404,7 +406,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   }
   CK(cp(ctx->d_sims + slot, &d, sizeof(SimDev)));
   lrbms::launch_prepare(ctx->d_sims + slot, std::max(n_cells, n_faces), st);
-  ctx->launches += 1;
+  lrbms::launch_sched(ctx->d_sims + slot, st);
+  ctx->launches += 2;
   CK(cudaStreamSynchronize(st));  // caller buffers may be freed on return
   CK(cudaGetLastError());
   Slot& s = ctx->slots[slot];

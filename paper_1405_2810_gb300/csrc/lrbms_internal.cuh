@@ -60,6 +60,7 @@ struct SimDev {
                             // offsets are multiples of 4 elements (16-byte aligned copies)
   const long long* ioff;    // [n_sub+1] inverse of diagonal block k, [N_k][N_k], then its transpose;
                             // same alignment
+  const unsigned long long* sched;  // copy schedule of the substitutions (launch_sched)
 
   // per-step cell data and load-time coefficients
   double* lam;      // [n_cells] lambda(s^n) of the current step
@@ -91,6 +92,14 @@ struct SimDev {
 };
 
 __host__ __device__ inline int jlo_of(int k, int Sx) { return k - Sx > 0 ? k - Sx : 0; }
+
+constexpr int kSolveWarps = 4;  // warps of the CTA that solves one reduced system
+// 64-bit words of the substitution copy schedule: kSolveWarps + 1 list starts,
+// then the warps' lists, together at most n_sub (2 Sx + 3) chunk descriptors
+// (a block row holds at most Sx + 1 forward and Sx + 2 backward chunks).
+inline size_t sched_words(int n_sub, int Sx) {
+  return kSolveWarps + 1 + (size_t)n_sub * (2 * (size_t)Sx + 3);
+}
 
 // Launchers (all enqueue on `st`; `active` lists slot indices, device array).
 // Load-time coefficients of one simulation (device pointer to its SimDev).
@@ -140,6 +149,9 @@ __host__ __device__ inline void solve_offsets(int n_sub, int Sx, const int* NE, 
 // factorisation meets a non-positive pivot). Both refine with FP64 residuals.
 cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
                               const SolveShape& sh, cudaStream_t st);
+// Substitution copy schedule of one simulation (device pointer to its SimDev,
+// whose NE, xoff, loff, ioff and sched are set).
+void launch_sched(const SimDev* sim, cudaStream_t st);
 // FP64 solve of the fine systems of the offline builder (one-cell blocks).
 cudaError_t launch_fine_solve(const SimDev* sims, const int* active, int n_active, cudaStream_t st);
 void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
