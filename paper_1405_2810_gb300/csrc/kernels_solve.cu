@@ -463,29 +463,30 @@ __device__ __forceinline__ void factor_issue(Ring<T>& r, FactorSeq& q, const Sol
 }
 
 // Cholesky factor and inverse of the N x N diagonal block Rd (shared memory,
-// row stride ld) by the whole CTA. The lower triangle is copied to the work
-// area W with the odd row stride N | 1. Right-looking factorisation, one CTA
-// barrier per column c: D[i][t] -= D[i][c] D[t][c] / D[c][c] for c < t <= i,
-// with column c scaled by 1/sqrt(D[c][c]) one step later (nothing reads it in
-// between). Right-looking inverse of L, one barrier per row r: Y[i][j] -=
-// L[i][r] Y[r][j] / L[r][r] for i > r, j <= r, with row r scaled one step
-// later. Writes L to the transposed panel rows LTd ([c][r], zero above the
-// diagonal), L^-1 to Li [N][N] and its transpose after it. Returns true on a
-// non-positive or non-finite pivot.
+// row stride ld) by one warp, so that no CTA barrier is needed (the other
+// warps write the row's panel back meanwhile). The lower triangle is copied
+// to the work area W with the odd row stride N | 1 (a column is read without
+// bank conflicts). Right-looking factorisation, lane = row: column c is
+// scaled by 1/sqrt(D[c][c]), then D[i][t] -= l_i l_t for c < t <= i (the
+// loop runs over every t > c; the entries above the diagonal it also
+// touches are never read). Inverse Y = L^-1 row by row, lane = column:
+// Y[i][j] = (delta_ij - sum_{t < i} L[i][t] Y[t][j]) / L[i][i], over a
+// zero-filled Y. Writes L to the transposed panel rows LTd ([c][r], zero
+// above the diagonal), L^-1 to Li [N][N] and its transpose after it.
+// Returns true (in every lane) on a non-positive or non-finite pivot.
 template <typename T>
-__device__ __noinline__ bool diag_block(const T* Rd, int ld, int N, T* W, T* LTd, T* Li) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __noinline__ bool diag_block_warp(const T* Rd, int ld, int N, T* W, T* LTd, T* Li) {
+  const int lane = threadIdx.x & 31;
   const int ldd = N | 1;
   T* D = W;
   T* Y = W + ((N * ldd + 3) & ~3);
   T* dinv = Y + ((N * N + 3) & ~3);  // [32] 1 / L[c][c]
-  T* dg = dinv + 32;                 // [32] L[c][c]
 #pragma unroll 1
-  for (int i = w; i < N; i += kNW) {
+  for (int i = 0; i < N; ++i)
     if (lane <= i) D[i * ldd + lane] = Rd[i * ld + lane];
-    if (lane < N) Y[i * N + lane] = (lane == i) ? T(1) : T(0);
-  }
-  __syncthreads();
+#pragma unroll 1
+  for (int e = lane; e < N * N; e += 32) Y[e] = T(0);
+  __syncwarp();
   bool bad = false;
 #pragma unroll 1
   for (int c = 0; c < N; ++c) {
@@ -496,49 +497,59 @@ __device__ __noinline__ bool diag_block(const T* Rd, int ld, int N, T* W, T* LTd
     }
     const T d = sqrt(piv);
     const T inv = T(1) / d;
-    const T inv2 = inv * inv;
-#pragma unroll 1
-    for (int i = c + 1 + w; i < N; i += kNW)
-      if (lane > c && lane <= i) D[i * ldd + lane] -= D[i * ldd + c] * D[lane * ldd + c] * inv2;
-    if (c > 0) {  // column c-1, final since the last barrier
-      const int cp = c - 1;
-      if (threadIdx.x == 0) D[cp * ldd + cp] = dg[cp];
-      else if (threadIdx.x > cp && threadIdx.x < N) D[threadIdx.x * ldd + cp] *= dinv[cp];
+    T li = T(0);
+    if (lane > c && lane < N) {
+      li = D[lane * ldd + c] * inv;
+      D[lane * ldd + c] = li;
     }
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    if (lane == 0) {
+      D[c * ldd + c] = d;
       dinv[c] = inv;
-      dg[c] = d;
     }
-    __syncthreads();
-  }
-  {
-    const int cp = N - 1;
-    if (threadIdx.x == 0) D[cp * ldd + cp] = dg[cp];
-  }
-  __syncthreads();
-  // inverse of L
-#pragma unroll 1
-  for (int r = 0; r < N; ++r) {
-    const T f = dinv[r];
-#pragma unroll 1
-    for (int i = r + 1 + w; i < N; i += kNW)
-      if (lane <= r) Y[i * N + lane] -= D[i * ldd + r] * (Y[r * N + lane] * f);
-    if (r > 0 && threadIdx.x < r) Y[(r - 1) * N + threadIdx.x] *= dinv[r - 1];  // row r-1 (j <= r-1)
-    __syncthreads();
-  }
-  if (threadIdx.x < N) Y[(N - 1) * N + threadIdx.x] *= dinv[N - 1];
-  __syncthreads();
-  T* LiT = Li + ((N * N + 3) & ~3);
-#pragma unroll 1
-  for (int c = w; c < N; c += kNW) {
     if (lane < N) {
+      T* Di = D + lane * ldd;
+      int t = c + 1;
+#pragma unroll 1
+      for (; t + 3 < N; t += 4) {
+        const T l0 = D[t * ldd + c], l1 = D[(t + 1) * ldd + c], l2 = D[(t + 2) * ldd + c], l3 = D[(t + 3) * ldd + c];
+        const T d0 = Di[t], d1 = Di[t + 1], d2 = Di[t + 2], d3 = Di[t + 3];
+        Di[t] = fma(-li, l0, d0);
+        Di[t + 1] = fma(-li, l1, d1);
+        Di[t + 2] = fma(-li, l2, d2);
+        Di[t + 3] = fma(-li, l3, d3);
+      }
+#pragma unroll 1
+      for (; t < N; ++t) Di[t] = fma(-li, D[t * ldd + c], Di[t]);
+    }
+    __syncwarp();
+  }
+  // inverse, lane = column j (Y[t][j] = 0 for t < j)
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    const T* Dr = D + i * ldd;
+    T s0 = (lane == i) ? T(1) : T(0), s1 = T(0);
+    int t = 0;
+#pragma unroll 1
+    for (; t + 1 < i; t += 2) {
+      s0 = fma(-Dr[t], Y[t * N + lane], s0);
+      s1 = fma(-Dr[t + 1], Y[(t + 1) * N + lane], s1);
+    }
+    if (t < i) s0 = fma(-Dr[t], Y[t * N + lane], s0);
+    if (lane <= i) Y[i * N + lane] = (s0 + s1) * dinv[i];
+    __syncwarp();
+  }
+  T* LiT = Li + ((N * N + 3) & ~3);
+  if (lane < N) {
+#pragma unroll 1
+    for (int c = 0; c < N; ++c) {
       LTd[(size_t)c * N + lane] = (c <= lane) ? D[lane * ldd + c] : T(0);
-      const T y = (lane <= c) ? Y[c * N + lane] : T(0);  // row c of L^-1
+      const T y = Y[c * N + lane];  // row c of L^-1 (zero right of the diagonal)
       Li[c * N + lane] = y;
       LiT[lane * N + c] = y;
     }
   }
-  return __syncthreads_or(bad ? 1 : 0) != 0;
+  return __any_sync(0xffffffffu, bad);
 }
 
 // Own rows [r0, r0 + nr) of the block-row panel R (row stride Wp) <- the
@@ -589,8 +600,9 @@ __device__ void fill_rows(const SimDev& S, const SolveMeta& mt, T* R, int k, int
 // for each block j of the envelope, X_j = R_j L_jj^-T is finalised (L_kj =
 // X_j), then the later off-diagonal blocks j' of the row are updated, R_j' -=
 // X_j L_{j'j}^T (lane = column of j'); these steps touch only the warp's own
-// rows. After a CTA barrier the diagonal block is updated with all X_j, and
-// warp 0 computes L_kk = chol(R_kk) and its inverse in registers (lane = row).
+// rows. After a CTA barrier the diagonal block is updated with all X_j; the
+// leader warp computes L_kk = chol(R_kk) and its inverse (diag_block_warp)
+// while the other warps write the row's panel back.
 // Panels are stored transposed, LT_k [W_k][N_k]; block k of the inverses holds
 // L_kk^-1 and its transpose. Returns kFacOk, kFacPivot on a non-positive (or
 // non-finite) pivot, or kFacTimeout if a copy did not complete.
@@ -645,17 +657,6 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
       pcj += Njp4;
     }
     __syncthreads();  // every X_j of the row is final
-    {  // L_kj = X_j into the transposed panel (lanes over rows: coalesced), all warps
-      int pc = 0;
-      #pragma unroll 1
-      for (int j = jl; j < k; ++j) {
-        const int Nj = mt.NE[j], gj = mt.xoff[j] - base;
-        if (lane < Nk)
-          #pragma unroll 1
-          for (int c = w; c < Nj; c += kNW) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
-        pc += (Nj + 3) & ~3;
-      }
-    }
     {  // R_kk -= sum_j X_j X_j^T on own rows; B[t][c] = X_j[c][t]
       int pc = 0;
       #pragma unroll 1
@@ -666,10 +667,20 @@ __device__ int cfactor(const SimDev& S, T* LT, T* Linv, CtaSmem<T>& m) {
       }
     }
     __syncthreads();
-    {  // diagonal block by the CTA (its work area: the factor ring, idle between rows)
-      const bool badp = diag_block<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
-                                      Linv + mt.ioff[k]);
-      if (badp && threadIdx.x == 0) m.flag[0] = 1;
+    if (w == 0) {  // diagonal block by the leader (its work area: the factor ring, idle between rows)
+      const bool badp = diag_block_warp<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
+                                           Linv + mt.ioff[k]);
+      if (badp && lane == 0) m.flag[0] = 1;
+    } else {  // meanwhile L_kj = X_j into the transposed panel (lanes over rows: coalesced)
+      int pc = 0;
+      #pragma unroll 1
+      for (int j = jl; j < k; ++j) {
+        const int Nj = mt.NE[j], gj = mt.xoff[j] - base;
+        if (lane < Nk)
+          #pragma unroll 1
+          for (int c = w - 1; c < Nj; c += kNW - 1) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
+        pc += (Nj + 3) & ~3;
+      }
     }
     if (!rg.ok) m.flag[1] = 1;
     fence_proxy_async();  // the next rows copy these panels with the async proxy
@@ -780,7 +791,7 @@ __device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ld
 // block product by one warp in turn; X_{j+1} by the warp that applied the
 // update into block j+1; R_kk -= X_j X_j^T. Every warp waits for every chunk of the ring before it
 // releases it (whether it used it or not), so no warp releases a slot ahead
-// of the chunk's user. The diagonal block is factored by the CTA as in
+// of the chunk's user. The diagonal block is factored by the leader warp as in
 // cfactor. Same results contract as cfactor.
 __device__ int cfactor_mma(const SimDev& S, float* LT, float* Linv, CtaSmem<float>& m) {
   using T = float;
@@ -845,21 +856,20 @@ __device__ int cfactor_mma(const SimDev& S, float* LT, float* Linv, CtaSmem<floa
       __syncthreads();
       pcj += Njp4;
     }
-    {  // L_kj = X_j into the transposed panel (lanes over rows: coalesced), all warps
+    if (w == 0) {  // diagonal block by the leader (its work area: the factor ring, idle between rows)
+      const bool badp = diag_block_warp<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
+                                           Linv + mt.ioff[k]);
+      if (badp && lane == 0) m.flag[0] = 1;
+    } else {  // meanwhile L_kj = X_j into the transposed panel (lanes over rows: coalesced)
       int pc = 0;
 #pragma unroll 1
       for (int j = jl; j < k; ++j) {
         const int Nj = mt.NE[j], gj = mt.xoff[j] - base;
         if (lane < Nk)
 #pragma unroll 1
-          for (int c = w; c < Nj; c += kNW) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
+          for (int c = w - 1; c < Nj; c += kNW - 1) LTk[(size_t)(gj + c) * Nk + lane] = R[lane * Wp + pc + c];
         pc += (Nj + 3) & ~3;
       }
-    }
-    {  // diagonal block by the CTA (its work area: the factor ring, idle between rows)
-      const bool badp = diag_block<T>(R + pck, Wp, Nk, m.ring, LTk + (size_t)(mt.xoff[k] - base) * Nk,
-                                      Linv + mt.ioff[k]);
-      if (badp && threadIdx.x == 0) m.flag[0] = 1;
     }
     if (!rg.ok) m.flag[1] = 1;
     fence_proxy_async();  // the next rows copy these panels with the async proxy
