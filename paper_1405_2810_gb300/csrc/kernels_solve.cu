@@ -1270,25 +1270,28 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   return true;
 }
 
-// acc += sum_{c < n} a[c * sa] xs[c] with four chains (FP64).
-__device__ __noinline__ double dot_strided(const double* __restrict__ a, int sa, const double* xs, int n,
-                                              double acc) {
+// acc += sum_{c < n} a[c * sa] xs[c * sx] with four chains (FP64).
+__device__ __noinline__ double dot_strided(const double* __restrict__ a, int sa, const double* xs, int sx, int n,
+                                           double acc) {
   double a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int c = 0;
   #pragma unroll 1
   for (; c + 3 < n; c += 4) {
-    acc = fma(a[c * sa], xs[c], acc);
-    a1 = fma(a[(c + 1) * sa], xs[c + 1], a1);
-    a2 = fma(a[(c + 2) * sa], xs[c + 2], a2);
-    a3 = fma(a[(c + 3) * sa], xs[c + 3], a3);
+    acc = fma(a[c * sa], xs[c * sx], acc);
+    a1 = fma(a[(c + 1) * sa], xs[(c + 1) * sx], a1);
+    a2 = fma(a[(c + 2) * sa], xs[(c + 2) * sx], a2);
+    a3 = fma(a[(c + 3) * sa], xs[(c + 3) * sx], a3);
   }
   #pragma unroll 1
-  for (; c < n; ++c) acc = fma(a[c * sa], xs[c], acc);
+  for (; c < n; ++c) acc = fma(a[c * sa], xs[c * sx], acc);
   return (acc + a1) + (a2 + a3);
 }
 
 // r = b - A x with the block-sparse assembled A, in FP64, by the CTA
 // (subdomain E to warp E mod kNW); x is staged in the shared work area xs [N].
+// p = floor(32 / N_E) lanes share a row: lane q N_E + i takes the columns
+// c = q (mod p) of row i and the partial sums meet by shuffles, so that the
+// FP64 pipe sees p N_E of 32 lanes busy instead of N_E.
 __device__ void cresidual(const SimDev& S, const SolveMeta& mt, const double* x, const double* b, double* r,
                           double* xs) {
   const int Sx = S.Sx, Sy = S.Sy, nsub = S.n_sub;
@@ -1300,28 +1303,41 @@ __device__ void cresidual(const SimDev& S, const SolveMeta& mt, const double* x,
   for (int E = w; E < nsub; E += kNW) {
     const int NE = mt.NE[E], x0 = mt.xoff[E];
     const int I = E % Sx, J = E / Sx;
-    if (lane < NE) {
-      const int i = lane;
+    const int p = 32 / NE;
+    const int q = lane / NE, i = lane - q * NE;
+    double acc = 0.0;
+    if (q < p) {
+      // columns c = q + p u of each block: element stride p times the column stride
+      const int d0 = (NE - q + p - 1) / p;
       // diagonal block (symmetric: column i read coalesced)
-      double acc = dot_strided(S.A + S.aoff[E] + i, NE, xs + x0, NE, 0.0);
+      acc = dot_strided(S.A + S.aoff[E] + i + (size_t)q * NE, p * NE, xs + x0 + q, p, d0, 0.0);
       if (I > 0) {  // left neighbour: A_{E,E-1} = blk^T, blk [N_{E-1}][N_E]
-        const int j = E - 1;
-        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)] + i, NE, xs + mt.xoff[j], mt.NE[j], acc);
+        const int j = E - 1, Nj = mt.NE[j];
+        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)] + i + (size_t)q * NE, p * NE,
+                          xs + mt.xoff[j] + q, p, (Nj - q + p - 1) / p, acc);
       }
       if (J > 0) {  // lower neighbour
-        const int j = E - Sx;
-        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + (J - 1) * Sx + I] + i, NE, xs + mt.xoff[j], mt.NE[j], acc);
+        const int j = E - Sx, Nj = mt.NE[j];
+        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + (J - 1) * Sx + I] + i + (size_t)q * NE, p * NE,
+                          xs + mt.xoff[j] + q, p, (Nj - q + p - 1) / p, acc);
       }
       if (I < Sx - 1) {  // right neighbour: A_{E,E+1} = blk [N_E][N_{E+1}]
         const int j = E + 1, Nj = mt.NE[j];
-        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + I] + (size_t)i * Nj, 1, xs + mt.xoff[j], Nj, acc);
+        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + I] + (size_t)i * Nj + q, p, xs + mt.xoff[j] + q, p,
+                          (Nj - q + p - 1) / p, acc);
       }
       if (J < Sy - 1) {  // upper neighbour
         const int j = E + Sx, Nj = mt.NE[j];
-        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + J * Sx + I] + (size_t)i * Nj, 1, xs + mt.xoff[j], Nj, acc);
+        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + J * Sx + I] + (size_t)i * Nj + q, p,
+                          xs + mt.xoff[j] + q, p, (Nj - q + p - 1) / p, acc);
       }
-      r[x0 + i] = b[x0 + i] - acc;
     }
+    #pragma unroll 1
+    for (int u = 1; u < p; ++u) {  // fixed order: q = 0, 1, ..., p-1
+      const double v = __shfl_sync(0xffffffffu, acc, (lane + u * NE) & 31);
+      if (q == 0) acc += v;
+    }
+    if (q == 0) r[x0 + i] = b[x0 + i] - acc;
   }
   __syncthreads();
 }
