@@ -62,6 +62,11 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0)
+    ap.add_argument("--serving", action="store_true",
+                    help="continuous-batching serving run with Poisson arrivals (its own JSON line)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-steps", type=int, default=300, help="online steps per request")
     return ap.parse_args()
 
 
@@ -284,8 +289,76 @@ def run_reference(a, rank: int, world: int):
     _ = mp
 
 
+SERVE_SHAPES = ((64, 4), (64, 8), (64, 16), (128, 8), (128, 16))  # (grid n, subdomains S), n / S >= 4
+
+
+def run_serving(a):
+    """Continuous batching under Poisson arrivals: every request is a
+    simulation of one of SERVE_SHAPES (a seeded physical dataset per shape,
+    built offline on the GPU and kept resident as a pool) admitted as a copy
+    of its pool entry, advanced one online step per tick with every other
+    active simulation, and released after serve_steps steps. Reports the
+    per-tick step latency (p50/p99), the admission time apart from it, the
+    request latency (arrival to finish) and the sustained throughput."""
+    import numpy as np
+    import torch
+    from types import SimpleNamespace
+    from paper_1405_2810_gb300 import build, lrbms as L
+    from paper_1405_2810_gb300.serving import Server
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    free, _tot = torch.cuda.mem_get_info()
+    prec = L.LRBMS_FP64 if a.precision == "fp64" else L.LRBMS_MIXED
+    solver = L.LRBMS_SOLVE_MIXED if a.solver == "mixed" else L.LRBMS_SOLVE_FP64
+    ctx = L.lrbms_create(precision=prec, max_slots=2048, hbm_budget=int(min(free * 0.45, 96 << 30)),
+                         stream=stream.cuda_stream, solver=solver)
+    t0 = time.perf_counter()
+    pool = []  # (sim id, nx, ny, shape)
+    for i, (n, S) in enumerate(SERVE_SHAPES):
+        prob, N_E, mu, _ = problem_inputs(SimpleNamespace(n=n, S=S, n_snap=a.n_snap), 500 + i)
+        (sid,) = L.lrbms_offline_build(ctx, [abi_problem(prob)], [dict(M=prob.M, n_steps_T=prob.n_steps, N_E=N_E,
+                                       mu=mu, c_pen=penalty_scale(prob), allow_fewer=1)], 1)
+        pool.append((sid, prob.nx, prob.ny, f"{n}x{n}/{S}x{S}"))
+    t_pool = time.perf_counter() - t0
+    rng = np.random.default_rng(np.random.PCG64(1405))
+    times = np.cumsum(rng.exponential(1.0 / a.serve_rate, size=a.serve_requests))
+    kinds = rng.integers(0, len(pool), size=a.serve_requests)
+    arrivals = [(float(t), {"nx": pool[k][1], "ny": pool[k][2]}, {"src": pool[k][0], "kind": int(k)},
+                 a.serve_steps) for t, k in zip(times, kinds)]
+    srv = Server(L, ctx, admit=lambda c, r: L.lrbms_clone(c, r.offline["src"], None))
+    t1 = time.perf_counter()
+    done = srv.run_timed(arrivals)
+    wall = time.perf_counter() - t1
+    ok = sum(1 for r in done if r.result.get("status") == 0)
+    p50, p99 = srv.latency_ms()
+    lat = np.array([r.finished_s - r.arrival_s for r in done])
+    wait = np.array([r.admitted_s - r.arrival_s for r in done])
+    adm = np.array([r.admit_ms for r in done])
+    steps = sum(r.steps_done for r in done)
+    print(json.dumps({
+        "metric": "LRBMS serving: per-tick step latency under Poisson arrivals of mixed grids",
+        "value": p99, "unit": "ms (p99 step latency)", "higher_is_better": False,
+        "p50_step_ms": p50, "p99_step_ms": p99, "ticks": len(srv.tick_ms),
+        "throughput_sim_steps_per_s": steps / wall,
+        "request_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "admission_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "admission_ms": {"p50": float(np.percentile(adm, 50)), "p99": float(np.percentile(adm, 99))},
+        "active_sims": {"mean": float(np.mean(srv.tick_n)), "max": int(max(srv.tick_n))},
+        "requests": len(done), "requests_ok": ok, "sim_steps": steps, "wall_s": wall,
+        "dtype": "f64+f32" if a.solver == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"Poisson arrivals at {a.serve_rate:g}/s, {a.serve_requests} requests of "
+                               f"{a.serve_steps} steps, grids/subdomains " + ", ".join(p[3] for p in pool),
+                   "precision": a.precision, "solver": a.solver, "pool_build_s": t_pool},
+    }))
+    L.lrbms_destroy(ctx)
+
+
 def main():
     a = parse_args()
+    if a.serving:
+        run_serving(a)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

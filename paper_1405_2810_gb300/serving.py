@@ -28,6 +28,10 @@ class Request:
     steps_done: int = 0
     admitted_tick: int = -1
     finished_tick: int = -1
+    arrival_s: float = 0.0   # wall-clock times (run_timed), seconds from its start
+    admitted_s: float = -1.0
+    finished_s: float = -1.0
+    admit_ms: float = 0.0    # host time of the admitting call
     result: dict = field(default_factory=dict)
 
 
@@ -36,15 +40,21 @@ class Server:
 
     backend: the ctypes binding (paper_1405_2810_gb300.lrbms) or an object
     with the same functions (lrbms_offline_load, lrbms_step, lrbms_get_state,
-    lrbms_release, LrbmsError, LRBMS_E_BUDGET)."""
+    lrbms_release, LrbmsError, LRBMS_E_BUDGET). admit: optional callable
+    (ctx, request) -> sim_id replacing lrbms_offline_load (for instance a
+    lrbms_clone of a resident simulation); it raises LrbmsError with
+    LRBMS_E_BUDGET when the request does not fit yet."""
 
-    def __init__(self, backend, ctx):
+    def __init__(self, backend, ctx, admit=None):
         self.L = backend
         self.ctx = ctx
+        self.admit = admit
+        self.clock = None  # run_timed: seconds since its start
         self.queue: deque[Request] = deque()
         self.active: list[Request] = []
         self.done: list[Request] = []
         self.tick_ms: list[float] = []
+        self.tick_n: list[int] = []  # simulations stepped per tick
         self.tick = 0
         self._next = 0
 
@@ -57,13 +67,20 @@ class Server:
     def _admit(self):
         while self.queue:
             r = self.queue[0]
+            t0 = time.perf_counter()
             try:
-                r.sim_id = self.L.lrbms_offline_load(self.ctx, r.problem, r.offline)
+                if self.admit is not None:
+                    r.sim_id = self.admit(self.ctx, r)
+                else:
+                    r.sim_id = self.L.lrbms_offline_load(self.ctx, r.problem, r.offline)
             except self.L.LrbmsError as e:
                 if e.code == self.L.LRBMS_E_BUDGET:
                     break  # wait for memory to be freed; keep arrival order
                 raise
+            r.admit_ms = 1e3 * (time.perf_counter() - t0)
             r.admitted_tick = self.tick
+            if self.clock is not None:
+                r.admitted_s = self.clock()
             self.queue.popleft()
             self.active.append(r)
 
@@ -75,6 +92,7 @@ class Server:
             t0 = time.perf_counter()
             st = self.L.lrbms_step(self.ctx, ids, 1)
             self.tick_ms.append(1e3 * (time.perf_counter() - t0))
+            self.tick_n.append(len(ids))
             still = []
             for r, code in zip(self.active, st):
                 r.steps_done += 1
@@ -82,6 +100,8 @@ class Server:
                     r.result = self._read(r, int(code))
                     self.L.lrbms_release(self.ctx, r.sim_id)
                     r.finished_tick = self.tick
+                    if self.clock is not None:
+                        r.finished_s = self.clock()
                     self.done.append(r)
                 else:
                     still.append(r)
@@ -105,6 +125,31 @@ class Server:
                 self.submit(p, o, n)
                 i += 1
             self.step()
+        return sorted(self.done, key=lambda r: r.rid)
+
+    def run_timed(self, arrivals=(), max_seconds: float = 600.0):
+        """arrivals: iterable of (seconds, problem, offline, n_steps) on the wall
+        clock from the call; a request is submitted once its time has come, and
+        the loop sleeps only while nothing is queued or active. Runs until every
+        request has finished (or max_seconds)."""
+        pending = sorted(arrivals, key=lambda a: a[0])
+        t0 = time.perf_counter()
+        self.clock = lambda: time.perf_counter() - t0
+        i = 0
+        while i < len(pending) or self.queue or self.active:
+            now = self.clock()
+            if now > max_seconds:
+                break
+            while i < len(pending) and pending[i][0] <= now:
+                at, p, o, n = pending[i]
+                self.submit(p, o, n)
+                self.queue[-1].arrival_s = at
+                i += 1
+            if not self.queue and not self.active:
+                time.sleep(max(0.0, pending[i][0] - now))
+                continue
+            self.step()
+        self.clock = None
         return sorted(self.done, key=lambda r: r.rid)
 
     def latency_ms(self):

@@ -65,3 +65,26 @@ def test_budget_error_other_than_budget_is_raised():
     srv.submit({"nx": 1, "ny": 1}, None, 1)
     with pytest.raises(Broken.LrbmsError):
         srv.step()
+
+
+def test_admit_hook_and_timed_arrivals():
+    """The admission hook replaces offline loading (clones of a resident pool);
+    wall-clock arrivals are submitted once due and every request finishes."""
+    lib = FakeLib(capacity=3)
+    made = []
+
+    def admit(ctx, r):
+        made.append(r.offline["src"])
+        return lib.lrbms_offline_load(ctx, r.problem, None)
+
+    srv = Server(lib, ctx=None, admit=admit)
+    prob = {"nx": 1, "ny": 2}
+    arrivals = [(0.0, prob, {"src": 7}, 2), (0.0, prob, {"src": 8}, 3), (0.02, prob, {"src": 9}, 1),
+                (0.05, prob, {"src": 7}, 2), (0.05, prob, {"src": 8}, 2)]
+    done = srv.run_timed(arrivals)
+    assert [r.rid for r in done] == [0, 1, 2, 3, 4]
+    assert made == [7, 8, 9, 7, 8]  # admitted in arrival order through the hook
+    assert all(r.result["steps"] == r.n_steps for r in done)
+    assert all(r.arrival_s <= r.admitted_s <= r.finished_s for r in done)
+    assert done[3].arrival_s == 0.05 and done[3].admitted_s >= 0.05
+    assert max(len(c) for c in lib.calls) <= 3 and not lib.live
