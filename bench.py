@@ -38,9 +38,9 @@ FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA lo
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop/clk x 2.07 GHz
 # DRAM bytes (read + write) per simulation of k_factor32 + k_refine32, from the
 # ncu capture in profiles/k_factor32_k_refine32_304sims_64x64_full.md
-# (k_factor32 0.136 GB read + 0.197 GB written, k_refine32 2.969 GB read +
+# (k_factor32 0.137 GB read + 0.197 GB written, k_refine32 2.991 GB read +
 # 0.047 GB written, for 304 simulations with the same reduced systems)
-SOLVE_DRAM_BYTES_PER_SIM = (0.136e9 + 0.197e9 + 2.969e9 + 0.047e9) / 304
+SOLVE_DRAM_BYTES_PER_SIM = (0.137e9 + 0.197e9 + 2.991e9 + 0.047e9) / 304
 
 
 def parse_args():
