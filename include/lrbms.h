@@ -276,7 +276,8 @@ int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n
  * which the synchronisation and possible failure of an allocation are not
  * allowed. No context is needed and nothing is allocated on the host or the
  * device; all working memory (factor panels, diagonal inverses, work vectors,
- * offset tables) is a fixed 32 MiB array in device memory that every GPU
+ * offset tables, the substitutions' copy schedule) is a fixed 32 MiB array in
+ * device memory that every GPU
  * loading the library holds until the process exits.
  *   Sx, Sy  coarse grid; N_E [Sx*Sy] local basis sizes (host memory, 1..32)
  *   A       device, assembled blocks in the layout of LRBMS_FIELD_A
