@@ -67,6 +67,11 @@ typedef enum {
   LRBMS_E_NONFINITE = -5, /* NaN or Inf in the saturation or time step       */
   LRBMS_E_TIMEOUT = -6,   /* a bounded device-side wait gave up              */
   LRBMS_E_FORMAT = -7,    /* offline data inconsistent with the problem      */
+  LRBMS_E_CFL = -8,       /* a fixed time step beyond the CFL bound: some
+                             cell would see dt L_f outflow/(phi|e|) > 1 (the
+                             upwind update of Definition 3 could then leave
+                             [0,1]); the simulation is frozen before its
+                             saturation changes                            */
   LRBMS_E_STATE = -9      /* unknown or released simulation id               */
 } lrbms_status;
 
@@ -117,7 +122,9 @@ typedef struct {
   const double* s0;      /* [nx*ny] initial saturation                       */
   double cfl;            /* CFL number of the time step (dt_mode = CFL)      */
   int dt_mode;           /* LRBMS_DT_CFL or LRBMS_DT_FIXED                   */
-  double dt_fixed;       /* time step for LRBMS_DT_FIXED                     */
+  double dt_fixed;       /* time step for LRBMS_DT_FIXED; a step beyond the
+                            CFL bound with CFL number 1 is refused with
+                            LRBMS_E_CFL (checked every step, needs Lf > 0) */
   double dt_max;         /* upper bound on the CFL step; <= 0: none          */
   int mean_weights;      /* face mean weights: 0 tau_l = a_l/(a1+a2) (as
                             printed, Section 3.1); 1 the swapped weights     */
@@ -286,9 +293,16 @@ int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n
  *   solver  LRBMS_SOLVE_FP64 or LRBMS_SOLVE_MIXED; refine_iters as in
  *           lrbms_config (0: default)
  *   stream  cudaStream_t (NULL: the legacy default stream)
- * Returns LRBMS_E_BUDGET if the system needs more than the 32 MiB array,
- * LRBMS_E_NOT_SPD if a pivot is not positive, LRBMS_E_ARG on bad arguments.
- * The call waits for the stream. The first call on a device looks up the
+ * A, rhs and x must be device (or managed) memory of exactly the sizes the
+ * basis sizes give; pointers the runtime does not report as device memory are
+ * refused with LRBMS_E_ARG (the sizes themselves cannot be checked here).
+ * Returns LRBMS_E_BUDGET if the system needs more than the 32 MiB array or
+ * more shared memory than one CTA has, LRBMS_E_NOT_SPD if a pivot is not
+ * positive, LRBMS_E_NONFINITE if the solution holds a NaN or Inf (for
+ * example from a non-finite right-hand side), LRBMS_E_ARG on bad arguments.
+ * An error left pending by the caller's earlier CUDA work is cleared on entry
+ * and not reported by this call. Every call copies the basis sizes from host
+ * memory and waits for the stream. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. Every call uses the same
  * array: calls that overlap on the GPU (other streams, other host threads)

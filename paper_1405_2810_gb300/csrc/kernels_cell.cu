@@ -353,13 +353,29 @@ __device__ __forceinline__ double face_term_boundary(const SimDev& S, const doub
   return Fo * ((Fo >= 0.0) ? fw[e] : frac_flow(S, sD));
 }
 
+// A fixed step beyond the CFL bound with CFL number 1 (dt L_f outflow_e /
+// (phi_e |e|) > 1 in some cell) is refused: the simulation is frozen with
+// status kStCfl before its saturation changes.
+__device__ __forceinline__ bool fixed_step_breaks_cfl(const SimDev& S) {
+  if (S.dt_mode != 1 || !(S.Lf > 0.0)) return false;
+  double m = 0.0;
+  for (int t = 0; t < S.n_tiles; ++t) m = fmax(m, S.cfl_part[t]);
+  return S.dt_fixed * S.Lf * m > 1.0;
+}
+
 __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restrict__ active) {
   const SimDev& S = sims[active[blockIdx.y]];
   const int tile = blockIdx.x;
   if (tile >= S.n_tiles || S.status[0] != kStOk) return;
   __shared__ double dt_sh;
-  if (threadIdx.x == 0) dt_sh = step_dt(S);
+  __shared__ int cfl_bad;
+  if (threadIdx.x == 0) {
+    dt_sh = step_dt(S);
+    cfl_bad = fixed_step_breaks_cfl(S);
+    if (cfl_bad && tile == 0) S.status[0] = kStCfl;
+  }
   __syncthreads();
+  if (cfl_bad) return;
   const double dt = dt_sh;
   const double* s = cur_s(S);
   double* sn = next_s(S);

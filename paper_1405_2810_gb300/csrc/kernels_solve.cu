@@ -1508,6 +1508,15 @@ __global__ void k_noalloc_tables(SimDev S) {
   S.status[0] = kStOk;
 }
 
+// A solution with a NaN or Inf entry (from a non-finite right-hand side) is
+// reported as such rather than as a converged solve.
+__device__ void mark_nonfinite_solution(const SimDev& S) {
+  bool bad = false;
+  #pragma unroll 1
+  for (int i = threadIdx.x; i < S.N; i += kThreads) bad |= !isfinite(S.x[i]);
+  if (__syncthreads_or(bad ? 1 : 0) && threadIdx.x == 0 && S.status[0] == kStOk) S.status[0] = kStNonFinite;
+}
+
 __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, int iters) {
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
@@ -1519,7 +1528,11 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
     if (f == kFacOk) {
       const int r = csolve_refine<float>(S, Lf, Lif, iters, mf);
       if (r == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
-      if (r != kRefStalled) return;
+      if (r != kRefStalled) {
+        __syncthreads();
+        mark_nonfinite_solution(S);
+        return;
+      }
     }
     if (f == kFacTimeout) {
       if (threadIdx.x == 0) S.status[0] = kStTimeout;
@@ -1534,6 +1547,8 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
     return;
   }
   if (csolve_refine<double>(S, S.L, S.Linv, iters, md) == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
+  __syncthreads();
+  mark_nonfinite_solution(S);
 }
 
 }  // namespace
@@ -1591,9 +1606,19 @@ unsigned char* g_noalloc_dev[kMaxDevices] = {nullptr};
 extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double* A, const double* rhs,
                                    double* x, int solver, int refine_iters, void* stream) {
   using namespace lrbms;
+  (void)cudaGetLastError();  // an error left pending by earlier work is not this call's
   if (Sx < 1 || Sy < 1 || !N_E || !A || !rhs || !x || refine_iters < 0 || refine_iters > 16 ||
       (solver != LRBMS_SOLVE_FP64 && solver != LRBMS_SOLVE_MIXED))
     return LRBMS_E_ARG;
+  // the kernels dereference A, rhs and x on the device: host pointers are refused
+  for (const void* p : {(const void*)A, (const void*)rhs, (const void*)x}) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return LRBMS_E_ARG;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return LRBMS_E_ARG;
+  }
   const int n_sub = Sx * Sy;
   const int n_cf = Sy * (Sx - 1) + (Sy - 1) * Sx;
   // sizes from the caller's (host) basis sizes; no host or device allocation
@@ -1663,5 +1688,8 @@ extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double*
   if (cudaMemcpyAsync(&status, base + o_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return LRBMS_E_CUDA;
-  return status == 0 ? LRBMS_OK : status == kStTimeout ? LRBMS_E_TIMEOUT : LRBMS_E_NOT_SPD;
+  if (status == kStOk) return LRBMS_OK;
+  if (status == kStTimeout) return LRBMS_E_TIMEOUT;
+  if (status == kStNonFinite) return LRBMS_E_NONFINITE;
+  return LRBMS_E_NOT_SPD;
 }

@@ -17,6 +17,7 @@ constexpr int kStOk = 0;
 constexpr int kStNotSpd = -4;
 constexpr int kStNonFinite = -5;
 constexpr int kStTimeout = -6;
+constexpr int kStCfl = -8;
 
 // Everything a kernel needs about one simulation. Lives in device memory,
 // one entry per slot; all pointers point into the context's arena.

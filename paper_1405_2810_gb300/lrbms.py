@@ -24,6 +24,7 @@ LRBMS_E_NOT_SPD = -4
 LRBMS_E_NONFINITE = -5
 LRBMS_E_TIMEOUT = -6
 LRBMS_E_FORMAT = -7
+LRBMS_E_CFL = -8
 LRBMS_E_STATE = -9
 LRBMS_FP64 = 0
 LRBMS_MIXED = 1
@@ -304,11 +305,31 @@ def lrbms_get_field(ctx, sim_id: int, field: int, dtype=np.float64):
     return out
 
 
+def noalloc_sizes(Sx: int, Sy: int, N_E) -> tuple:
+    """Element counts of the assembled blocks (per subdomain N_E^2, then per
+    coarse face N_E- N_E+) and of the reduced vectors, for basis sizes N_E."""
+    ne = np.asarray(N_E, dtype=np.int64).reshape(Sy, Sx)
+    a = int(np.sum(ne * ne)) + int(np.sum(ne[:, :-1] * ne[:, 1:])) + int(np.sum(ne[:-1, :] * ne[1:, :]))
+    return a, int(ne.sum())
+
+
+def _device_f64(t, n: int) -> bool:
+    return (hasattr(t, "data_ptr") and getattr(t, "is_cuda", False) and str(t.dtype) == "torch.float64"
+            and t.is_contiguous() and t.numel() == n)
+
+
 def lrbms_solve_noalloc(Sx: int, Sy: int, N_E, A, rhs, x, solver=LRBMS_SOLVE_FP64, refine_iters=0,
                         stream=None) -> int:
-    """Solve an assembled reduced system with no allocation (A, rhs, x:
-    device arrays with data_ptr(); N_E: host int32). Returns the status code."""
+    """Solve an assembled reduced system with no allocation. A, rhs, x: CUDA
+    float64 contiguous tensors of exactly the sizes the basis sizes give
+    (noalloc_sizes); N_E: host int32 [Sx*Sy]. Returns the status code
+    (LRBMS_E_ARG, without calling the library, for any other argument)."""
     ne = np.ascontiguousarray(N_E, dtype=np.int32)
+    if Sx < 1 or Sy < 1 or ne.size != Sx * Sy:
+        return LRBMS_E_ARG
+    n_a, n = noalloc_sizes(Sx, Sy, ne)
+    if not (_device_f64(A, n_a) and _device_f64(rhs, n) and _device_f64(x, n)):
+        return LRBMS_E_ARG
     return int(library().lrbms_solve_noalloc(Sx, Sy, _ptr(ne), _ptr(A), _ptr(rhs), _ptr(x), solver,
                                              refine_iters, stream))
 

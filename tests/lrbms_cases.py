@@ -9,7 +9,8 @@ import numpy as np
 
 from oracle.grid import Coarse
 from oracle.impes import FineModel
-from oracle.offline import build_offline
+from oracle.offline import (build_offline, initial_profiles, local_mass_rows, orthonormalize,
+                            snapshot_bases)
 from synth import make_problem, simplex_params, basis_sizes
 
 
@@ -79,6 +80,75 @@ def case(name: str, kind: str = "greedy", seed: int | None = None, swapped: bool
         mus = simplex_params(int(NE.max()) + 2, prob.M, prob.seed + 6)
         off = build_offline(m, co, prob.s0, prob.n_steps, prob.M, kind="snapshots", mus=mus, N_E=NE)
     return prob, m, co, off
+
+
+# Cases at the shapes the batched bench and the serving pool run: 8x8
+# subdomains with basis sizes drawn from U{5..30} (both 16-row MMA tiles and
+# all n-tiles of the FP32 factor), the same grid with sizes 17, 24, 30 and 32
+# in neighbouring subdomains (residual rows above 16, the widest blocks), and
+# 16x16 subdomains (the serving pool's widest envelope: 17 blocks per row).
+SHAPES = {
+    "bench-8x8": dict(n=64, S=8, lo=5, hi=30, seed=77),
+    "bench-8x8-wide": dict(n=64, S=8, pattern=(17, 24, 30, 32), seed=78),
+    "serve-16x16": dict(n=128, S=16, lo=5, hi=30, seed=79),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def shape_case(label: str):
+    """(problem, fine model, coarse grid, oracle offline data) for one of
+    SHAPES: the batched workload's physics (seeded log-normal field, Corey,
+    viscosity ratio from U[2, 20]) with snapshot bases of the given sizes."""
+    sp_ = SHAPES[label]
+    prob = make_problem("batch", n=sp_["n"], S=sp_["S"], sim_index=sp_["seed"])
+    m = FineModel.from_problem(prob)
+    co = Coarse(m.grid, prob.Sx, prob.Sy)
+    if "pattern" in sp_:
+        pat = np.array(sp_["pattern"], dtype=np.int32)
+        I = np.arange(co.n_sub) % prob.Sx
+        J = np.arange(co.n_sub) // prob.Sx
+        NE = pat[(I + 2 * J) % len(pat)]  # every x and y neighbour has another size
+    else:
+        NE = basis_sizes(co.n_sub, sp_["lo"], sp_["hi"], sp_["seed"] + 5)
+    mus = simplex_params(int(NE.max()) + 4, prob.M, sp_["seed"] + 6)
+    P = initial_profiles(m, prob.s0, prob.n_steps, prob.M)["P"]
+    Phi = snapshot_bases(m, co, P, mus, NE)
+    # Where the snapshots span fewer functions than asked (their restrictions
+    # become dependent), top the basis up with seeded random P1 functions,
+    # orthonormalised the same way: any local basis is a valid reduced space.
+    rng = np.random.default_rng(np.random.PCG64(sp_["seed"] + 7))
+    mloc = local_mass_rows(m.grid, co.cx * co.cy)
+    for E in range(co.n_sub):
+        cols = [Phi[E][:, i] for i in range(Phi[E].shape[1])]
+        while len(cols) < NE[E]:
+            w = orthonormalize(rng.standard_normal(3 * co.cx * co.cy), cols, mloc)
+            if w is not None:
+                cols.append(w)
+        Phi[E] = np.stack(cols, axis=1)
+    off = build_offline(m, co, prob.s0, prob.n_steps, prob.M, Phi=Phi)
+    assert np.array_equal(off.N_E, NE)
+    return prob, m, co, off
+
+
+@functools.lru_cache(maxsize=None)
+def shape_states(label: str, n_steps: int):
+    """Oracle saturations s^0 .. s^n_steps of a SHAPES case (the reduced
+    trajectory), for per-step parity from identical inputs."""
+    from oracle.reduced import online_step
+    prob, m, co, off = shape_case(label)
+    out = [prob.s0.copy()]
+    for _ in range(n_steps):
+        out.append(online_step(m, off, out[-1])["s"])
+    return tuple(out)
+
+
+def close_elementwise(a, b, tol: float) -> float:
+    """max_i |a_i - b_i| / max_i |b_i| (the element-wise counterpart of rel);
+    callers assert it is at most tol."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    mb = np.abs(b).max() if b.size else 0.0
+    return float(np.abs(a - b).max() / (mb if mb > 0 else 1.0)) if b.size else 0.0
 
 
 def rel(a, b) -> float:

@@ -230,3 +230,46 @@ def test_budget_admission_and_slot_reuse(L):
     again = _load(L, ctx, c)
     assert L.lrbms_step(ctx, [again], 2)[0] == 0
     L.lrbms_destroy(ctx)
+
+
+def test_run_returns_last_step_fields(L):
+    """lrbms_run (n steps, then the saturation, pressure and fluxes of the
+    last step into caller buffers) against the oracle's trajectory."""
+    prob, m, co, off = c = case("small")
+    ctx = _ctx(L, solver=1)
+    sid = _load(L, ctx, c)
+    s = prob.s0.copy()
+    for _ in range(4):
+        ref = online_step(m, off, s)
+        s = ref["s"]
+    s_out = np.empty(prob.n_cells)
+    p_out = np.empty(3 * prob.n_cells)
+    F_out = np.empty(m.grid.n_faces)
+    L.lrbms_run(ctx, sid, 4, s_out, p_out, F_out)
+    assert rel(s_out, s) < TOL
+    assert rel(p_out, _soa(ref["p"])) < TOL
+    assert rel(F_out, ref["F"]) < flux_tolerance(c, ref)
+    L.lrbms_destroy(ctx)
+
+
+def test_fixed_step_beyond_cfl_bound_is_refused(L):
+    """A fixed time step twice the CFL bound with CFL number 1 (reading R12
+    with cfl = 1, from the oracle's fluxes) freezes the simulation with
+    LRBMS_E_CFL and leaves its saturation unchanged; half the bound steps
+    normally and matches the oracle."""
+    from oracle.transport import cfl_dt
+    prob, m, co, off = c = case("small")
+    ref = online_step(m, off, prob.s0)
+    bound = cfl_dt(m.grid, ref["F"], m.poro, m.Lf, 1.0)
+    ctx = _ctx(L)
+    big = _load(L, ctx, c, dt_mode=1, dt_fixed=2.0 * bound)
+    ok = _load(L, ctx, c, dt_mode=1, dt_fixed=0.5 * bound)
+    st = L.lrbms_step(ctx, [big, ok], 1)
+    assert st[0] == L.LRBMS_E_CFL and st[1] == 0
+    assert np.array_equal(L.lrbms_get_field(ctx, big, L.FIELD_S), prob.s0)
+    m.dt_fixed = 0.5 * bound
+    try:
+        _compare_step(L, ctx, ok, c, prob.s0)
+    finally:
+        m.dt_fixed = None
+    L.lrbms_destroy(ctx)

@@ -1,0 +1,108 @@
+"""GPU parity at the shapes the batched bench and the serving pool run
+(Algorithm 3, step 5; Eq. reducedSystem): 8x8 subdomains with basis sizes
+from U{5..30}, 8x8 subdomains with sizes 17, 24, 30 and 32 side by side, and
+16x16 subdomains (17 blocks per envelope row). Every field of a step is
+compared with the FP64 oracle both in relative L2 norm and element by
+element (max |gpu - oracle| / max |oracle|), from the oracle's own states,
+for both reduced solvers."""
+import numpy as np
+import pytest
+
+from lrbms_cases import SHAPES, abi_offline, abi_problem, a_blocks, close_elementwise, rel, shape_case, shape_states
+from oracle.reduced import online_step
+from test_gpu_parity import flux_tolerance
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+LATE = 12  # oracle step whose state starts the second compared step
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_2810_gb300 import build, lrbms
+    build.build()
+    return lrbms
+
+
+def _soa(p):
+    return p.reshape(-1, 3).T.reshape(-1)
+
+
+def _check_fields(L, ctx, sid, c, s):
+    """Every field of the last step against the oracle's step from s."""
+    prob, m, co, off = c
+    ref = online_step(m, off, s)
+    tf = flux_tolerance(c, ref)
+    pairs = [
+        ("fitted mobility", L.lrbms_get_field(ctx, sid, L.FIELD_THETA) @ off.P, ref["theta"] @ off.P, TOL),
+        ("A", L.lrbms_get_field(ctx, sid, L.FIELD_A), a_blocks(co, off, ref["A"]), TOL),
+        ("rhs", L.lrbms_get_field(ctx, sid, L.FIELD_RHS), ref["rhs"], TOL),
+        ("x", L.lrbms_get_field(ctx, sid, L.FIELD_X), ref["x"], TOL),
+        ("p", L.lrbms_get_field(ctx, sid, L.FIELD_P), _soa(ref["p"]), TOL),
+        ("F", L.lrbms_get_field(ctx, sid, L.FIELD_FLUX), ref["F"], tf),
+        ("dt", L.lrbms_get_field(ctx, sid, L.FIELD_DT), np.array([ref["dt"]]), tf),
+        ("s", L.lrbms_get_field(ctx, sid, L.FIELD_S), ref["s"], tf),
+    ]
+    for name, got, want, tol in pairs:
+        r2, re = rel(got, want), close_elementwise(got, want, tol)
+        assert r2 <= tol, (name, "L2", r2, tol)
+        assert re <= tol, (name, "element-wise", re, tol)
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["fp64-solve", "mixed-solve"])
+@pytest.mark.parametrize("label", list(SHAPES))
+def test_bench_shape_steps(L, label, solver):
+    """One step from s^0 and one from the oracle's state after LATE steps."""
+    c = shape_case(label)
+    prob, m, co, off = c
+    states = shape_states(label, LATE)
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=2, solver=solver)
+    sid = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+    for s in (states[0], states[LATE]):
+        L.lrbms_set_saturation(ctx, sid, s)
+        assert L.lrbms_step(ctx, [sid], 1)[0] == 0
+        _check_fields(L, ctx, sid, c, s)
+    L.lrbms_destroy(ctx)
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["fp64-solve", "mixed-solve"])
+def test_bench_shapes_in_one_launch(L, solver):
+    """All shapes stepped together (one launch per phase, the launch shape
+    set by the largest system), two unrotated copies each; every
+    simulation still matches the oracle field by field."""
+    ctx = L.lrbms_create(hbm_budget=2 << 30, max_slots=8, solver=solver)
+    sims = []
+    for label in SHAPES:
+        c = shape_case(label)
+        prob, m, co, off = c
+        s = shape_states(label, LATE)[LATE]
+        for _ in range(2):
+            sid = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+            L.lrbms_set_saturation(ctx, sid, s)
+            sims.append((sid, c, s))
+    st = L.lrbms_step(ctx, [sid for sid, _, _ in sims], 1)
+    assert list(st) == [0] * len(sims)
+    for sid, c, s in sims:
+        _check_fields(L, ctx, sid, c, s)
+    L.lrbms_destroy(ctx)
+
+
+def test_bench_shape_trajectory_mass_balance(L):
+    """LATE steps of the 8x8 bench shape with the mixed solver: the saturation
+    matches the oracle's trajectory, and the water volume changes by the
+    cumulative boundary outflow to FP64 round-off."""
+    c = shape_case("bench-8x8")
+    prob, m, co, off = c
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=2, solver=1)
+    sid = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+    assert L.lrbms_step(ctx, [sid], LATE)[0] == 0
+    s_gpu = np.empty(prob.n_cells)
+    _, mg = L.lrbms_get_state(ctx, sid, s_gpu)
+    s_ref = shape_states("bench-8x8", LATE)[LATE]
+    assert rel(s_gpu, s_ref) < TOL and close_elementwise(s_gpu, s_ref, TOL) <= TOL
+    vol = prob.poro * m.grid.vol
+    assert abs((np.sum(vol * s_gpu) - np.sum(vol * prob.s0)) + mg) <= 1e-13 * abs(mg)
+    L.lrbms_destroy(ctx)

@@ -5,8 +5,6 @@ import json
 import os
 
 import numpy as np
-import pytest
-from scipy.optimize import brentq
 
 from oracle.grid import Grid
 from oracle.impes import FineModel
@@ -72,53 +70,6 @@ def test_mass_balance_and_bounds_fine():
     assert s.min() >= -1e-14 and s.max() <= 1.0 + 1e-14
     for h in hist:
         assert h["s"].min() >= -1e-14 and h["s"].max() <= 1.0 + 1e-14
-
-
-def _bl_profile(x, Q, phi, ew, eo):
-    """Buckley-Leverett solution for injected volume Q per unit area into s = 0
-    (Welge tangent construction)."""
-    fw = lambda s: frac_flow(s, ew, eo, "corey")  # noqa: E731
-    h = 1e-7
-    df = lambda s: (fw(s + h) - fw(s - h)) / (2 * h)  # noqa: E731
-    sstar = brentq(lambda s: df(s) * s - fw(s), 1e-3, 1 - 1e-6)
-    xs = Q * fw(sstar) / (phi * sstar)
-    out = np.zeros_like(x)
-    for k, xx in enumerate(x):
-        if xx >= xs:
-            out[k] = 0.0
-        else:
-            target = xx * phi / Q
-            if target <= df(1 - 1e-9):
-                out[k] = 1.0
-            else:
-                out[k] = brentq(lambda s: df(s) - target, sstar, 1 - 1e-9)
-    return out
-
-
-@pytest.mark.slow
-def test_buckley_leverett_convergence():
-    """T2: 1D strip, Dirichlet pressure at both ends, Corey law; the fine
-    scheme converges in L1 to the Buckley-Leverett profile at equal injected
-    volume."""
-    errs = []
-    for n in (100, 200, 400):
-        prob = make_problem("strip", n=n, S=1)
-        m = FineModel.from_problem(prob)
-        s = prob.s0.copy()
-        Q = 0.0
-        while True:
-            r = m.step(s)
-            Fin = r["F"][0]  # left boundary face, +x orientation = into the domain
-            Q_next = Q + r["dt"] * Fin / m.grid.hy
-            if Q_next > 0.12:
-                break
-            Q = Q_next
-            s = r["s"]
-        exact = _bl_profile(m.grid.xc, Q, 0.2, prob.eta_w, prob.eta_o)
-        errs.append(np.sum(np.abs(s - exact)) * m.grid.hx)
-    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert errs[-1] < 0.02, errs
-    assert np.all(rates > 0.5), (errs, rates)
 
 
 def test_time_of_flight_uniform_flow():
