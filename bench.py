@@ -36,11 +36,6 @@ if ROOT not in sys.path:
 METRIC = "Batched LRBMS online steps/s and p99 step latency vs plain FP64 GPU path"
 FP64_PEAK_TFLOPS = 1.26  # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA loop: 1.19)
 FP32_PEAK_TFLOPS = 80.5  # 152 SMs x 128 FP32 lanes x 2 flop/clk x 2.07 GHz
-# DRAM bytes (read + write) per simulation of k_factor32 + k_refine32, from the
-# ncu capture in profiles/k_factor32_k_refine32_304sims_64x64_full.md
-# (k_factor32 0.137 GB read + 0.197 GB written, k_refine32 2.991 GB read +
-# 0.047 GB written, for 304 simulations with the same reduced systems)
-SOLVE_DRAM_BYTES_PER_SIM = (0.137e9 + 0.197e9 + 2.991e9 + 0.047e9) / 304
 
 
 def parse_args():
@@ -250,6 +245,12 @@ def stream_bytes(N_E, Sx: int, cells: int, M: int, elem: int) -> dict:
             "reconstruct": sum(3 * cells * int(v) * elem for v in N_E) + 24 * cells * n + 8 * N}
 
 
+def solve_info(L, ctx, ids):
+    """Per-simulation reduced-solve counters (LRBMS_FIELD_SOLVE_INFO)."""
+    import numpy as np
+    return np.array([L.lrbms_get_field(ctx, i, L.FIELD_SOLVE_INFO, dtype=np.int32) for i in ids], dtype=np.int64)
+
+
 # ------------------------------------------------------------------ multi-rank aggregation
 def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
     """Largest value of x over all ranks (x itself without a process group)."""
@@ -431,6 +432,7 @@ def main():
         K = min(K, a.horizon - max(a.warmup, 1) - 1)  # stay within the simulated horizon
 
     # ---- timed region: device-resident inputs
+    info0 = solve_info(L, ctx, ids)
     clocks = ClockSampler(local)
     clocks.start()
     L.lrbms_profile_start(ctx, K)
@@ -451,6 +453,12 @@ def main():
     status = L.lrbms_step(ctx, ids, 0)
     n_ok = int(np.sum(status == 0))
     value = job_throughput(a.n_sims, K, elapsed_ms / 1000.0, world)
+    # reduced-solve work of the timed steps (per simulation: substitution
+    # passes, FP32 factorisations, FP64 redos)
+    dinfo = solve_info(L, ctx, ids) - info0
+    solves = np.maximum(dinfo[:, 5], 1)
+    passes_per_solve = dinfo[:, 4] / solves
+    factor_rate = dinfo[:, 2] / solves
 
     # ---- end to end through lrbms_step_io with pinned host buffers
     n_cells = a.n * a.n
@@ -484,10 +492,8 @@ def main():
     plain = n1 / (time.perf_counter() - t0)
     L.lrbms_destroy(ctx1)
 
-    # ---- refinement steps actually taken (last step of every simulation)
-    info = np.array([L.lrbms_get_field(ctx, i, L.FIELD_SOLVE_INFO, dtype=np.int32) for i in ids])
-    refine_mean = float(info[:, 0].mean())
-    fp64_redos = int(info[:, 1].sum())
+    fp64_redos = int(dinfo[:, 1].sum())
+    stale_retries = int(dinfo[:, 3].sum())
 
     # ---- roofline of the dominant phase
     names = L.PHASES
@@ -496,23 +502,25 @@ def main():
     cells = (a.n // a.S) ** 2
     elem = 8 if a.precision == "fp64" else 4
     if names[dom] == "solve":
-        # factor + (1 + refine) substitution pairs in the factor's type, refine FP64 residuals
+        # per simulation and step: FP32 factorisations x factor flops, substitution
+        # passes x (forward + backward) flops in the factor's type, and one FP64
+        # residual per correction pass (mixed; FP64: one residual per refinement)
         f_lo = f_hi = 0.0
-        for sz in sizes:
+        for k, sz in enumerate(sizes):
             fac, sub, res = solve_flops(list(sz), Sx)
-            lo = fac + (1.0 + refine_mean) * sub
+            sl = slice(k * n_copies, (k + 1) * n_copies)  # ids are grouped by physical dataset
             if a.solver == "mixed":
-                f_lo += lo * n_copies
+                f_lo += float(np.sum(factor_rate[sl] * fac + passes_per_solve[sl] * sub))
+                f_hi += float(np.sum(passes_per_solve[sl] * res))
             else:
-                f_hi += lo * n_copies
-            f_hi += refine_mean * res * n_copies
+                f_hi += float(np.sum(fac + passes_per_solve[sl] * sub + (passes_per_solve[sl] - 1) * res))
         t_solve = phase_ms[dom] / 1000.0
         t_min = f_lo / (FP32_PEAK_TFLOPS * 1e12) + f_hi / (FP64_PEAK_TFLOPS * 1e12)
         work = (f_lo + f_hi) * 1e-12
-        roof = {"bound": "alu", "kernel": "k_factor32 + k_refine32" if a.solver == "mixed" else "k_csolve64",
+        roof = {"bound": "alu",
+                "kernel": "k_factor32 + k_refine32 + k_retry32" if a.solver == "mixed" else "k_csolve64",
                 "achieved": work / t_solve, "peak": work / t_min, "unit": "TFLOP/s", "frac": t_min / t_solve,
-                "traffic": SOLVE_DRAM_BYTES_PER_SIM * a.n_sims if a.solver == "mixed" else None,
-                "traffic_source": "ncu dram bytes of the 304-simulation capture, scaled per simulation",
+                "traffic": None,
                 "peak_source": ("time-weighted ALU peak of the solve's FP32 and FP64 flops: "
                                 "FP32 152 SMs x 256 flop/clk, FP64 152 SMs x 4 flop/clk, at 2.07 GHz "
                                 "(recipe unit counts and clock)"),
@@ -550,7 +558,9 @@ def main():
                        "l2": f"inputs larger than L2: {used / 2**30:.1f} GiB resident",
                        "p50_step_ms": p50, "p99_step_ms": p99, "sims_ok": n_ok,
                        "offline_build_s": t_build, "parallelism": f"replicas x{world}",
-                       "refine_steps_mean": refine_mean, "fp64_redos": fp64_redos},
+                       "passes_per_solve": float(passes_per_solve.mean()),
+                       "fp32_factorisations_per_step": float(factor_rate.mean()),
+                       "stale_factor_retries": stale_retries, "fp64_redos": fp64_redos},
             "phases_ms": {n: float(v) for n, v in zip(names, phase_ms)},
             "roofline": roof,
             "plain_fp64_single_sim_steps_per_s": plain,

@@ -90,19 +90,26 @@ typedef struct {
   void* stream;      /* cudaStream_t for all work, or NULL for a stream
                         owned by the context                                */
   int device;        /* CUDA device ordinal                                 */
-  int solver;        /* reduced solve: LRBMS_SOLVE_FP64 (FP64 block Cholesky,
-                        FP64 substitutions) or LRBMS_SOLVE_MIXED (FP32 block
-                        Cholesky and substitutions, iterative refinement with
-                        FP64 residuals and updates; a solve whose FP32
-                        factorisation meets a non-positive pivot, or whose
-                        refinement stops contracting above 1e-8 of the
-                        solution, is redone in FP64)                        */
-  int refine_iters;  /* most refinement steps after the first solve; 0:
-                        default (1 for FP64, 6 for MIXED); at most 16. The
-                        refinement stops early once the next correction,
-                        predicted from the last two, is below 1e-12 of the
-                        solution, or once a correction no longer halves
-                        (max norms)                                         */
+  int solver;        /* reduced solve: LRBMS_SOLVE_FP64 (FP64 block Cholesky
+                        every step, FP64 substitutions) or LRBMS_SOLVE_MIXED
+                        (FP32 block Cholesky and substitutions, iterative
+                        refinement with FP64 residuals and updates, warm-
+                        started from the previous step's solution; the FP32
+                        factor of an earlier step is reused as long as the
+                        refinement converges in at most 8 correction passes,
+                        else the next step refactors; a reused factor that
+                        has not converged after 12 passes is recomputed at
+                        once; a solve whose fresh FP32 factorisation meets a
+                        non-positive pivot, or whose refinement stops
+                        contracting above 1e-8 of the solution, is redone
+                        in FP64)                                            */
+  int refine_iters;  /* FP64: most refinement steps after the first solve;
+                        MIXED: most correction passes with a fresh factor,
+                        minus one. 0: default (1 for FP64, 6 for MIXED); at
+                        most 16. The refinement stops early once the next
+                        correction, predicted from the last two, is below
+                        1e-12 of the solution, or once a correction no
+                        longer halves (max norms)                           */
 } lrbms_config;
 
 /* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with
@@ -201,10 +208,13 @@ enum {
   LRBMS_FIELD_S = 6,     /* [n_cells] saturation                                */
   LRBMS_FIELD_DT = 7,    /* [1] last time step                                  */
   LRBMS_FIELD_STATUS = 8,/* [1] int status word                                 */
-  LRBMS_FIELD_SOLVE_INFO = 9 /* [2] int: refinement steps of the last reduced
-                            solve; reduced solves redone in FP64 after the
-                            FP32 factorisation or refinement failed (count
-                            since load)                                         */
+  LRBMS_FIELD_SOLVE_INFO = 9 /* [6] int: correction passes of the last reduced
+                            solve; then, counted since load: reduced solves
+                            redone in FP64 after the FP32 factorisation or
+                            refinement failed; FP32 factorisations; steps
+                            whose reused (stale) FP32 factor did not converge
+                            and was recomputed at once; substitution passes;
+                            reduced solves                                      */
 };
 /* Wait and copy a field (bytes must equal the field's size). */
 int lrbms_get_field(lrbms_ctx* ctx, int sim_id, int field, void* dst, size_t bytes);

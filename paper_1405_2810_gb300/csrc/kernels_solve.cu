@@ -1367,27 +1367,42 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
 //  - stalled: a correction that no longer halves above that level (the
 //    factor is too inexact for this matrix; the FP32 kernel then hands the
 //    simulation to the FP64 one).
-// Returns kRefOk, kRefStalled or kRefTimeout (a copy did not complete).
+// Warm start (warm = true): x already holds the previous step's solution of
+// a nearby system, and every pass is a correction pass x += (L L^T)^-1 (b - A x);
+// the first correction is accepted only if it is itself below kRefineTol ||x||
+// (its size says nothing about the contraction yet).
+// Returns kRefOk, kRefStalled, kRefTimeout (a copy did not complete) or, warm
+// only, kRefNotConverged (the pass budget ran out before convergence).
+// Per-simulation solve bookkeeping (S.info, ints): [0] correction passes of
+// the last solve, [1] FP64 redos, [2] FP32 factorisations, [3] refactorings
+// forced by a stale factor that did not converge, [4] correction passes,
+// [5] reduced solves (all since load), [6] the FP32 factor's state: 0 none,
+// a >= 1 computed a - 1 steps ago, [7] refactor at the next step.
+constexpr int kInfoPasses = 0, kInfoRedo64 = 1, kInfoFactors = 2, kInfoStaleRetry = 3, kInfoPassSum = 4,
+              kInfoSolves = 5, kInfoAge = 6, kInfoRefactor = 7;
 constexpr double kRefineTol = 1e-12;
 constexpr double kFloorTol = 1e-8;
-constexpr int kRefOk = 0, kRefStalled = 1, kRefTimeout = 2;
+constexpr int kRefOk = 0, kRefStalled = 1, kRefTimeout = 2, kRefNotConverged = 3;
 
 template <typename T>
-__device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
+__device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m,
+                             bool warm = false) {
   double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
   double prev = 0.0;
-  int steps = 0, rc = kRefOk;
-  // pass 0 solves for x, pass it >= 1 for the correction dv of refinement step it
-  // (one substitution call site keeps the kernel's code small)
+  int steps = 0, rc = warm ? kRefNotConverged : kRefOk;
+  // cold: pass 0 solves for x, pass it >= 1 for the correction dv of
+  // refinement step it; warm: every pass is a correction (one substitution
+  // call site keeps the kernel's code small)
 #pragma unroll 1
   for (int it = 0; it <= iters; ++it) {
-    if (it > 0) cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
-    if (!csubstitute<T>(S, Lst, Linv, it == 0 ? S.b : S.rv, it == 0 ? S.x : S.dv, m)) return kRefTimeout;
+    const bool corr = warm || it > 0;
+    if (corr) cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
+    if (!csubstitute<T>(S, Lst, Linv, corr ? S.rv : S.b, corr ? S.dv : S.x, m)) return kRefTimeout;
     double mdv = 0.0, mx = 0.0;
 #pragma unroll 1
     for (int i = threadIdx.x; i < S.N; i += kThreads) {
       double xi = S.x[i];
-      if (it > 0) {
+      if (corr) {
         xi += S.dv[i];
         S.x[i] = xi;
         mdv = fmax(mdv, fabs(S.dv[i]));
@@ -1396,42 +1411,72 @@ __device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int i
     }
     mdv = cta_max(mdv, red);
     mx = cta_max(mx, red);
-    if (it == 0) {
+    if (!corr) {
       prev = mx;
       continue;
     }
-    steps = it;
-    if (!(mdv * fmin(1.0, mdv / prev) > kRefineTol * mx)) break;  // converged (also on 0/0)
-    if (mdv > 0.5 * prev) {
-      if (mdv > kFloorTol * mx) rc = kRefStalled;
+    steps = warm ? it + 1 : it;
+    const bool first = warm && it == 0;
+    const double pred = first ? mdv : mdv * fmin(1.0, mdv / prev);
+    if (!(pred > kRefineTol * mx)) {  // converged (also on 0/0)
+      rc = kRefOk;
+      break;
+    }
+    if (!first && mdv > 0.5 * prev) {
+      rc = mdv > kFloorTol * mx ? kRefStalled : kRefOk;
       break;
     }
     prev = mdv;
   }
-  if (threadIdx.x == 0 && S.info) S.info[0] = steps;
+  if (threadIdx.x == 0 && S.info) {
+    S.info[kInfoPasses] = steps;
+    S.info[kInfoPassSum] += steps + (warm ? 0 : 1);  // every substitution pass
+  }
   return rc;
 }
 
 constexpr int kStRetry64 = 1;  // transient status: redo this simulation's solve in FP64
+constexpr int kStRetry32 = 2;  // transient status: refactor in FP32 now and solve again
 
-// The FP32 path runs as two kernels, factorisation then substitutions and
-// refinement, so that the CTAs sharing an SM execute the same code (a smaller
-// instruction working set than one kernel whose CTAs are in different phases).
-// A simulation whose FP32 factorisation meets a non-positive pivot, or whose
-// refinement stalls, is marked for the FP64 kernel.
+// The FP32 factor of an earlier step serves as the preconditioner of the
+// refinement (A changes only through the fitted mobility coefficients, so
+// the factor of a nearby step still contracts) until a step needs more than
+// kRefactorPasses correction passes; the next step then refactors. A stale
+// factor gets at most kStalePasses passes; if it has not converged by then,
+// or stalls, the step refactors at once (kStRetry32).
+constexpr int kRefactorPasses = 8;
+constexpr int kStalePasses = 12;
+
+__device__ __forceinline__ bool wants_factor(const SimDev& S) {
+  return S.info[kInfoAge] == 0 || S.info[kInfoRefactor] != 0;
+}
+
+// FP32 factorisation of the simulations that need one this step (no factor
+// yet, or marked by the last step's refinement). A non-positive pivot hands
+// the simulation to the FP64 kernel.
 __global__ void __launch_bounds__(kThreads, 4) k_factor32(const SimDev* __restrict__ sims,
                                                           const int* __restrict__ active, int n_active) {
   const int a = blockIdx.x;
   if (a >= n_active) return;
   const SimDev& S = sims[active[a]];
-  if (S.status[0] != kStOk) return;
+  if (S.status[0] != kStOk || !wants_factor(S)) return;
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
   const int f = cfactor_mma(S, reinterpret_cast<float*>(S.L), reinterpret_cast<float*>(S.Linv), m);
-  if (f != kFacOk && threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
+  if (threadIdx.x == 0) {
+    if (f == kFacOk) {
+      S.info[kInfoFactors] += 1;
+      S.info[kInfoAge] = 1;
+      S.info[kInfoRefactor] = 0;
+    } else {
+      S.info[kInfoAge] = 0;
+      S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
+    }
+  }
 }
 
+// Warm-started refinement with the current FP32 factor (fresh or stale).
 __global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restrict__ sims,
                                                           const int* __restrict__ active, int n_active, int iters) {
   const int a = blockIdx.x;
@@ -1441,9 +1486,58 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restri
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
+  const bool fresh = S.info[kInfoAge] == 1;
+  const int budget = fresh ? iters : max(iters, kStalePasses - 1);
   const int r = csolve_refine<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
-                                     iters, m);
-  if (threadIdx.x == 0 && r != kRefOk) S.status[0] = r == kRefStalled ? kStRetry64 : kStTimeout;
+                                     budget, m, true);
+  if (threadIdx.x == 0) {
+    if (r == kRefOk) {
+      S.info[kInfoSolves] += 1;
+      S.info[kInfoAge] += 1;
+      if (S.info[kInfoPasses] > kRefactorPasses) S.info[kInfoRefactor] = 1;
+    } else if (r == kRefTimeout) {
+      S.status[0] = kStTimeout;
+    } else {
+      S.status[0] = fresh ? kStRetry64 : kStRetry32;
+    }
+  }
+}
+
+// A stale factor that did not converge: refactor in FP32 now and solve from
+// scratch (cold start); a failure there hands the simulation to FP64.
+__global__ void __launch_bounds__(kThreads) k_retry32(const SimDev* __restrict__ sims,
+                                                      const int* __restrict__ active, int n_active, int iters) {
+  const int a = blockIdx.x;
+  if (a >= n_active) return;
+  const SimDev& S = sims[active[a]];
+  if (S.status[0] != kStRetry32) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S.status[0] = kStOk;
+    S.info[kInfoStaleRetry] += 1;
+  }
+  extern __shared__ double sm[];
+  unsigned char* b = reinterpret_cast<unsigned char*>(sm);
+  CtaSmem<float> m = cta_carve_and_load<float>(S, b);
+  float* Lf = reinterpret_cast<float*>(S.L);
+  float* Lif = reinterpret_cast<float*>(S.Linv);
+  const int f = cfactor_mma(S, Lf, Lif, m);
+  if (f != kFacOk) {
+    if (threadIdx.x == 0) {
+      S.info[kInfoAge] = 0;
+      S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
+    }
+    return;
+  }
+  const int r = csolve_refine<float>(S, Lf, Lif, iters, m);
+  if (threadIdx.x == 0) {
+    S.info[kInfoFactors] += 1;
+    S.info[kInfoAge] = 2;  // computed this step, and served it
+    S.info[kInfoRefactor] = 0;
+    if (r == kRefTimeout) S.status[0] = kStTimeout;
+    else if (r != kRefOk) S.status[0] = kStRetry64;
+    else S.info[kInfoSolves] += 1;
+  }
 }
 
 // FP64 factor. only_retry: process only the simulations marked by the FP32 kernel.
@@ -1458,7 +1552,11 @@ __global__ void __launch_bounds__(kThreads) k_csolve64(const SimDev* __restrict_
   __syncthreads();
   if (threadIdx.x == 0) {
     S.status[0] = kStOk;
-    if (only_retry && S.info) S.info[1] += 1;
+    if (only_retry && S.info) {
+      S.info[kInfoRedo64] += 1;
+      S.info[kInfoAge] = 0;  // the FP64 factor overwrites the FP32 one
+      S.info[kInfoRefactor] = 0;
+    }
   }
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
@@ -1468,7 +1566,11 @@ __global__ void __launch_bounds__(kThreads) k_csolve64(const SimDev* __restrict_
     if (threadIdx.x == 0) S.status[0] = f == kFacPivot ? kStNotSpd : kStTimeout;
     return;
   }
-  if (csolve_refine<double>(S, S.L, S.Linv, iters, m) == kRefTimeout && threadIdx.x == 0) S.status[0] = kStTimeout;
+  const int r = csolve_refine<double>(S, S.L, S.Linv, iters, m);
+  if (threadIdx.x == 0) {
+    if (r == kRefTimeout) S.status[0] = kStTimeout;
+    else if (S.info) S.info[kInfoSolves] += 1;
+  }
 }
 
 // ---------------------------------------------------------------- static scratch
@@ -1583,8 +1685,10 @@ cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_activ
     const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
     if ((e = set_smem((const void*)k_factor32, s32)) != cudaSuccess) return e;
     if ((e = set_smem((const void*)k_refine32, s32)) != cudaSuccess) return e;
+    if ((e = set_smem((const void*)k_retry32, s32)) != cudaSuccess) return e;
     k_factor32<<<n_active, kThreads, s32, st>>>(sims, active, n_active);
     k_refine32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
+    k_retry32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
   }
   const size_t s64 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(double));
   if ((e = set_smem((const void*)k_csolve64, s64)) != cudaSuccess) return e;

@@ -319,7 +319,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
   const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
   const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
-  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(8);
+  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 8);
   const size_t o_sched = L.add(8 * lrbms::sched_words(n_sub, Sx));
   (void)d_tot;
 
@@ -395,7 +395,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_theta), 0, 8 * lrbms::kMaxM, st));
   CK(cudaMemsetAsync(P(o_status), 0, 4, st));
   CK(cudaMemsetAsync(P(o_steps), 0, 4, st));
-  CK(cudaMemsetAsync(P(o_info), 0, 8, st));
+  CK(cudaMemsetAsync(P(o_info), 0, 4 * 8, st));
   CK(cudaMemsetAsync(P(o_p), 0, 24 * (size_t)n_cells, st));
   CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
   CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
@@ -478,7 +478,8 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(7);
     lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
     mark(8);
-    ctx->launches += 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 3 : 1);  // mixed: factor, refine, FP64 redo
+    // mixed: factor (where needed), refine, fresh-factor retry, FP64 redo
+    ctx->launches += 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1);
   }
   CK(cudaGetLastError());
   if (status) {
@@ -586,7 +587,7 @@ size_t lrbms_field_bytes(lrbms_ctx* ctx, int id, int field) {
     case LRBMS_FIELD_S: return 8 * (size_t)d.n_cells;
     case LRBMS_FIELD_DT: return 8;
     case LRBMS_FIELD_STATUS: return 4;
-    case LRBMS_FIELD_SOLVE_INFO: return 8;
+    case LRBMS_FIELD_SOLVE_INFO: return 24;
     default: return 0;
   }
 }

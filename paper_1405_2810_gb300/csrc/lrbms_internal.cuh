@@ -89,7 +89,7 @@ struct SimDev {
   double* theta;    // [M]
   int* status;      // [1]
   int* steps;       // [1]
-  int* info;        // [2] refinement steps of the last solve; FP64 redos (may be null)
+  int* info;        // [8] solve bookkeeping (kernels_solve.cu, kInfo*); may be null
 };
 
 __host__ __device__ inline int jlo_of(int k, int Sx) { return k - Sx > 0 ? k - Sx : 0; }

@@ -105,4 +105,7 @@ def test_bench_shape_trajectory_mass_balance(L):
     assert rel(s_gpu, s_ref) < TOL and close_elementwise(s_gpu, s_ref, TOL) <= TOL
     vol = prob.poro * m.grid.vol
     assert abs((np.sum(vol * s_gpu) - np.sum(vol * prob.s0)) + mg) <= 1e-13 * abs(mg)
+    info = L.lrbms_get_field(ctx, sid, L.FIELD_SOLVE_INFO, dtype=np.int32)
+    assert info[5] == LATE  # one reduced solve per step
+    assert 1 <= info[2] < LATE  # the FP32 factor was reused on some steps
     L.lrbms_destroy(ctx)
