@@ -104,9 +104,9 @@ typedef struct {
                         contracting above 1e-8 of the solution, is redone
                         in FP64)                                            */
   int refine_iters;  /* FP64: most refinement steps after the first solve;
-                        MIXED: most correction passes with a fresh factor,
-                        minus one. 0: default (1 for FP64, 6 for MIXED); at
-                        most 16. The refinement stops early once the next
+                        MIXED: most correction passes of a step minus one
+                        (at least 11). 0: default (1 for FP64, 6 for MIXED);
+                        at most 16. The refinement stops early once the next
                         correction, predicted from the last two, is below
                         1e-12 of the solution, or once a correction no
                         longer halves (max norms)                           */

@@ -1441,9 +1441,10 @@ constexpr int kStRetry32 = 2;  // transient status: refactor in FP32 now and sol
 // The FP32 factor of an earlier step serves as the preconditioner of the
 // refinement (A changes only through the fitted mobility coefficients, so
 // the factor of a nearby step still contracts) until a step needs more than
-// kRefactorPasses correction passes; the next step then refactors. A stale
-// factor gets at most kStalePasses passes; if it has not converged by then,
-// or stalls, the step refactors at once (kStRetry32).
+// kRefactorPasses correction passes; the next step then refactors. The warm
+// refinement gets at most kStalePasses passes (or refine_iters + 1 if more);
+// a stale factor that has not converged by then, or stalls, is recomputed at
+// once (kStRetry32); a fresh one hands the solve to FP64.
 constexpr int kRefactorPasses = 8;
 constexpr int kStalePasses = 12;
 
@@ -1487,7 +1488,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restri
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
   const bool fresh = S.info[kInfoAge] == 1;
-  const int budget = fresh ? iters : max(iters, kStalePasses - 1);
+  const int budget = max(iters, kStalePasses - 1);
   const int r = csolve_refine<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
                                      budget, m, true);
   if (threadIdx.x == 0) {
@@ -1675,23 +1676,32 @@ static cudaError_t set_smem(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// One CTA of kNW warps per simulation; the CTAs spread over the SMs, as many
-// per SM as their shared memory allows.
-cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
-                              const SolveShape& sh, cudaStream_t st) {
+// Dynamic shared-memory limits of the solve kernels for a launch shape (set
+// before a launch, and before a stream capture of one).
+cudaError_t prepare_chol_solve(int mode, const SolveShape& sh) {
   cudaError_t e;
-  if (n_active <= 0) return cudaSuccess;
   if (mode == 1) {
     const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
     if ((e = set_smem((const void*)k_factor32, s32)) != cudaSuccess) return e;
     if ((e = set_smem((const void*)k_refine32, s32)) != cudaSuccess) return e;
     if ((e = set_smem((const void*)k_retry32, s32)) != cudaSuccess) return e;
+  }
+  const size_t s64 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(double));
+  return set_smem((const void*)k_csolve64, s64);
+}
+
+// One CTA of kNW warps per simulation; the CTAs spread over the SMs, as many
+// per SM as their shared memory allows (attributes from prepare_chol_solve).
+cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
+                              const SolveShape& sh, cudaStream_t st) {
+  if (n_active <= 0) return cudaSuccess;
+  if (mode == 1) {
+    const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
     k_factor32<<<n_active, kThreads, s32, st>>>(sims, active, n_active);
     k_refine32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
     k_retry32<<<n_active, kThreads, s32, st>>>(sims, active, n_active, iters);
   }
   const size_t s64 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(double));
-  if ((e = set_smem((const void*)k_csolve64, s64)) != cudaSuccess) return e;
   k_csolve64<<<n_active, kThreads, s64, st>>>(sims, active, n_active, iters, mode == 1 ? 1 : 0);
   return cudaGetLastError();
 }

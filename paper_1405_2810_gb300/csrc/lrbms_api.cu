@@ -105,6 +105,11 @@ struct lrbms_ctx {
   // profiling of live steps
   int prof_cap = 0, prof_n = 0;
   std::vector<cudaEvent_t> prof_ev;
+  // one online step of the current batch, captured as a CUDA graph; valid
+  // while the batch (active list) and its launch shape stay the same
+  cudaGraphExec_t graph = nullptr;
+  std::vector<long long> graph_key;
+  int graph_kernels = 0;
 };
 
 namespace {
@@ -189,6 +194,7 @@ int lrbms_destroy(lrbms_ctx* ctx) {
   cudaFree(ctx->d_active);
   cudaFree(ctx->d_io);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return LRBMS_OK;
@@ -455,9 +461,12 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     ctx->last_active = act;
   }
   const int mixed = ctx->precision == LRBMS_MIXED;
-  for (int k = 0; k < n_steps; ++k) {
-    cudaEvent_t* ev = nullptr;
-    if (ctx->prof_n < ctx->prof_cap) ev = &ctx->prof_ev[(size_t)ctx->prof_n++ * (LRBMS_N_PHASES + 1)];
+  const int per_step = 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1);  // mixed solve: factor (where
+                                                                     // needed), refine, retry, FP64 redo
+  CK(lrbms::prepare_chol_solve(ctx->solver, sh));  // kernel attributes, outside any capture
+  // The kernels of one step, in order; ev (optional) gets an event before the
+  // first phase and after every phase.
+  auto enqueue_step = [&](cudaEvent_t* ev) -> cudaError_t {
     auto mark = [&](int i) {
       if (ev) cudaEventRecord(ev[i], st);
     };
@@ -466,7 +475,9 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(1);
     lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st);
     mark(2);
-    CK(lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, ctx->solver, ctx->refine_iters, sh, st));
+    cudaError_t e = lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, ctx->solver, ctx->refine_iters,
+                                             sh, st);
+    if (e != cudaSuccess) return e;
     mark(3);
     lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st);
     mark(4);
@@ -478,8 +489,47 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(7);
     lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
     mark(8);
-    // mixed: factor (where needed), refine, fresh-factor retry, FP64 redo
-    ctx->launches += 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1);
+    return cudaGetLastError();
+  };
+  int k = 0;
+  // Profiled steps launch kernel by kernel (events between the phases).
+  for (; k < n_steps && ctx->prof_n < ctx->prof_cap; ++k) {
+    CK(enqueue_step(&ctx->prof_ev[(size_t)ctx->prof_n++ * (LRBMS_N_PHASES + 1)]));
+    ctx->launches += per_step;
+  }
+  if (k < n_steps) {
+    // The other steps replay one captured graph of the step's kernels.
+    std::vector<long long> key(act.begin(), act.end());
+    for (long long v : {(long long)sh.n_sub, (long long)sh.panel_words, (long long)sh.max_w, (long long)sh.N,
+                        (long long)max_tiles, (long long)max_blocks, (long long)max_sub, (long long)max_faces})
+      key.push_back(v);
+    if (!ctx->graph || key != ctx->graph_key) {
+      if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+      ctx->graph_key.clear();
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const cudaError_t e1 = enqueue_step(nullptr);
+        const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (e1 == cudaSuccess && e2 == cudaSuccess && g &&
+            cudaGraphInstantiate(&ctx->graph, g, 0) == cudaSuccess) {
+          ctx->graph_key = key;
+          ctx->graph_kernels = per_step;
+        } else {
+          ctx->graph = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+      }
+      (void)cudaGetLastError();  // a stream that cannot be captured: launch directly below
+    }
+    for (; k < n_steps; ++k) {
+      if (ctx->graph) {
+        CK(cudaGraphLaunch(ctx->graph, st));
+      } else {
+        CK(enqueue_step(nullptr));
+      }
+      ctx->launches += per_step;
+    }
   }
   CK(cudaGetLastError());
   if (status) {

@@ -273,3 +273,27 @@ def test_fixed_step_beyond_cfl_bound_is_refused(L):
     finally:
         m.dt_fixed = None
     L.lrbms_destroy(ctx)
+
+
+@pytest.mark.parametrize("solver", SOLVERS, ids=["fp64-solve", "mixed-solve"])
+def test_graph_replay_equals_direct_launches(L, solver):
+    """Steps replayed from the captured CUDA graph give bitwise the results of
+    the same steps launched kernel by kernel (profiled steps are launched
+    directly), and the launch count grows by the kernels of each step."""
+    c = case("small", kind="snapshots")
+    out = []
+    for profiled in (False, True):
+        ctx = _ctx(L, solver=solver)
+        sid = _load(L, ctx, c)
+        if profiled:
+            L.lrbms_profile_start(ctx, 6)
+        n0 = L.lrbms_launch_count(ctx)
+        assert L.lrbms_step(ctx, [sid], 6)[0] == 0
+        per_step = (L.lrbms_launch_count(ctx) - n0) / 6
+        if profiled:
+            ph, st = L.lrbms_profile_read(ctx, 6)
+            assert len(st) == 6 and np.all(ph >= 0)
+        out.append((L.lrbms_get_field(ctx, sid, L.FIELD_S), L.lrbms_get_field(ctx, sid, L.FIELD_X), per_step))
+        L.lrbms_destroy(ctx)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] >= 8
