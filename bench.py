@@ -53,6 +53,8 @@ def parse_args():
                     help="storage of bases and components (mixed: FP32)")
     ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"],
                     help="reduced solve: FP64 Cholesky, or FP32 Cholesky with FP64 refinement")
+    ap.add_argument("--refactor-period", type=int, default=0,
+                    help="mixed solver: steps one FP32 factor serves (0: the library default)")
     ap.add_argument("--horizon", type=int, default=300, help="steps per simulation (warm-up + timed)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -388,7 +390,8 @@ def main():
     prec = L.LRBMS_FP64 if a.precision == "fp64" else L.LRBMS_MIXED
     solver = L.LRBMS_SOLVE_MIXED if a.solver == "mixed" else L.LRBMS_SOLVE_FP64
     ctx = L.lrbms_create(precision=prec, max_slots=a.n_sims + 8, hbm_budget=budget,
-                         stream=stream.cuda_stream, device=local, solver=solver)
+                         stream=stream.cuda_stream, device=local, solver=solver,
+                         refactor_period=a.refactor_period)
 
     # ---- offline data on the GPU (not timed)
     t0 = time.perf_counter()

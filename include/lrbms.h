@@ -94,11 +94,11 @@ typedef struct {
                         every step, FP64 substitutions) or LRBMS_SOLVE_MIXED
                         (FP32 block Cholesky and substitutions, iterative
                         refinement with FP64 residuals and updates, warm-
-                        started from the previous step's solution; the FP32
-                        factor of an earlier step is reused as long as the
-                        refinement converges in at most 8 correction passes,
-                        else the next step refactors; a reused factor that
-                        has not converged after 12 passes is recomputed at
+                        started from the previous steps' solutions; the FP32
+                        factor of an earlier step is reused for
+                        refactor_period steps, or until a step needs more
+                        than 10 correction passes; a reused factor that has
+                        not converged after 12 passes is recomputed at
                         once; a solve whose fresh FP32 factorisation meets a
                         non-positive pivot, or whose refinement stops
                         contracting above 1e-8 of the solution, is redone
@@ -110,6 +110,10 @@ typedef struct {
                         correction, predicted from the last two, is below
                         1e-12 of the solution, or once a correction no
                         longer halves (max norms)                           */
+  int refactor_period; /* MIXED: steps one FP32 factor serves before the
+                        simulation refactors (1: every step); 0: default 3.
+                        The first guess of each solve is the linear
+                        extrapolation of the last two solutions            */
 } lrbms_config;
 
 /* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with
@@ -271,10 +275,13 @@ int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_id);
 int lrbms_step_io(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int n_steps,
                   const double* const* s_in, double* const* s_out, int* status);
 
-/* Phases of one step, in launch order. */
+/* Phases of one step, in launch order. FIT runs only in the first step after
+ * the saturation was set from outside (load, lrbms_set_saturation,
+ * lrbms_step_io input); otherwise TRANSPORT has already fitted the new
+ * saturation. FLUX includes the per-tile CFL bound. */
 enum {
   LRBMS_PHASE_FIT = 0, LRBMS_PHASE_ASSEMBLE, LRBMS_PHASE_SOLVE, LRBMS_PHASE_RECONSTRUCT,
-  LRBMS_PHASE_FLUX, LRBMS_PHASE_CFL, LRBMS_PHASE_TRANSPORT, LRBMS_PHASE_FINALIZE,
+  LRBMS_PHASE_FLUX, LRBMS_PHASE_TRANSPORT, LRBMS_PHASE_FINALIZE,
   LRBMS_N_PHASES
 };
 /* Profiling of live steps: with max_steps > 0 the next max_steps steps record

@@ -1,13 +1,18 @@
 // Per-cell and per-face kernels of the LRBMS online step:
 //   prepare    (at load) per-face coefficients of Definition 2 and 1/(phi|e|)
 //   fit        lambda(s^n) and f_w(s^n) per cell, and the partial sums of the
-//              normal equations of Eq. leastSquaresFit
+//              normal equations of Eq. leastSquaresFit (only after the
+//              saturation was set from outside: otherwise the transport
+//              kernel of the previous step has computed them)
 //   reconstruct p_E = Phi_E x_E (Algorithm 3, step 5(b))
-//   flux       face fluxes of Definition 2 (Eq. velocityDG), mobility lambda(s^n)
-//   cfl        per-tile maximum of outflow_e / (phi|e|) (the CFL bound's inverse)
-//   transport  explicit upwind update of Definition 3 with P0 saturation
+//   flux_cfl   face fluxes of Definition 2 (Eq. velocityDG) with mobility
+//              lambda(s^n), and per tile the maximum of outflow_e / (phi|e|)
+//              (the inverse of the CFL bound)
+//   transport  explicit upwind update of Definition 3 with P0 saturation, then
+//              lambda, f_w and the fit sums of the new saturation
 //   finalize   time, cumulative boundary outflow and step counter
-// Every reduction uses a fixed tile partition and a fixed order, so a
+// Tiles are blocks of whole grid rows (tile_rows rows, at most kCellTile
+// cells). Every reduction uses this fixed partition and a fixed order, so a
 // simulation's results do not depend on which other simulations share the
 // launch.
 #include "lrbms_internal.cuh"
@@ -23,6 +28,21 @@ __device__ __forceinline__ const double* cur_s(const SimDev& S) {
 }
 __device__ __forceinline__ double* next_s(const SimDev& S) {
   return S.s + (size_t)((S.steps[0] + 1) & 1) * S.n_cells;
+}
+// lambda and f_w of the current saturation, and of the next one (ping-pong
+// like the saturation).
+__device__ __forceinline__ size_t cur_half(const SimDev& S) { return (size_t)(S.steps[0] & 1) * S.n_cells; }
+__device__ __forceinline__ size_t next_half(const SimDev& S) { return (size_t)((S.steps[0] + 1) & 1) * S.n_cells; }
+
+// max(v, 0) for a double by its sign bit (integer pipe; the FP64 pipe of
+// this part is narrow). A NaN with a clear sign bit passes through.
+__device__ __forceinline__ double pos_part(double v) { return __double_as_longlong(v) > 0 ? v : 0.0; }
+
+// First and one-past-last cell of a tile (blocks of whole rows).
+__device__ __forceinline__ void tile_range(const SimDev& S, int tile, int& e0, int& e1) {
+  const int j0 = tile * S.tile_rows;
+  e0 = j0 * S.nx;
+  e1 = min(j0 + S.tile_rows, S.ny) * S.nx;
 }
 
 // Eq. brooksCorey: lambda_w = k_rw/eta_w, lambda_o = k_ro/eta_o.
@@ -138,47 +158,41 @@ __global__ void k_prepare(const SimDev* __restrict__ sp) {
 }
 
 // ------------------------------------------------------------------ fit
-// lambda(s_e) and f_w(s_e) for the step (stored for the flux and transport
-// kernels) and r_q = sum_e Lambda^q_e lambda(s_e) per tile. With the threshold
-// profiles of Algorithm 2 (Lambda^q_e = lambda(1) if q >= k_e else
+// lambda(s_e) and f_w(s_e) (stored for the flux and transport kernels) and the
+// contribution of cell e to r_q = sum_e Lambda^q_e lambda(s_e). With the
+// threshold profiles of Algorithm 2 (Lambda^q_e = lambda(1) if q >= k_e else
 // lambda(0)) the cells are binned by k_e and r follows from the bin sums.
-__global__ void k_fit(const SimDev* __restrict__ sims, const int* __restrict__ active) {
-  const SimDev& S = sims[active[blockIdx.y]];
-  const int tile = blockIdx.x;
-  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
-  const double* s = cur_s(S);
-  const int M = S.M;
-  double acc[kMaxM];
-#pragma unroll
-  for (int q = 0; q < kMaxM; ++q) acc[q] = 0.0;
-  const int e0 = tile * kCellTile;
-  const int e1 = min(e0 + kCellTile, S.n_cells);
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    double lw, lo;
-    phase_mob(S, s[e], lw, lo);
-    const double lam = lw + lo;
-    S.lam[e] = lam;
-    S.fw[e] = lw / lam;  // Eq. frationalFlow
-    if (S.prof_mode == 0) {
-      switch (S.prof_idx[e] - 1) {  // one add: the cell's bin
+__device__ __forceinline__ void fit_cell(const SimDev& S, double s, int e, double* lam_out, double* fw_out,
+                                         double (&acc)[kMaxM]) {
+  double lw, lo;
+  phase_mob(S, s, lw, lo);
+  const double lam = lw + lo;
+  lam_out[e] = lam;
+  fw_out[e] = lw / lam;  // Eq. frationalFlow
+  if (S.prof_mode == 0) {
+    switch (S.prof_idx[e] - 1) {  // one add: the cell's bin
 #define LRBMS_BIN(q) \
   case q:            \
     acc[q] += lam;   \
     break;
-        LRBMS_BIN(0) LRBMS_BIN(1) LRBMS_BIN(2) LRBMS_BIN(3) LRBMS_BIN(4) LRBMS_BIN(5) LRBMS_BIN(6)
-        LRBMS_BIN(7) LRBMS_BIN(8) LRBMS_BIN(9) LRBMS_BIN(10) LRBMS_BIN(11) LRBMS_BIN(12) LRBMS_BIN(13)
-        LRBMS_BIN(14) LRBMS_BIN(15)
+      LRBMS_BIN(0) LRBMS_BIN(1) LRBMS_BIN(2) LRBMS_BIN(3) LRBMS_BIN(4) LRBMS_BIN(5) LRBMS_BIN(6)
+      LRBMS_BIN(7) LRBMS_BIN(8) LRBMS_BIN(9) LRBMS_BIN(10) LRBMS_BIN(11) LRBMS_BIN(12) LRBMS_BIN(13)
+      LRBMS_BIN(14) LRBMS_BIN(15)
 #undef LRBMS_BIN
-        default: break;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < kMaxM; ++q)
-        if (q < M) acc[q] += S.prof[(size_t)q * S.n_cells + e] * lam;
+      default: break;
     }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kMaxM; ++q)
+      if (q < S.M) acc[q] += S.prof[(size_t)q * S.n_cells + e] * lam;
   }
+}
+
+// Block sums of the tile's fit contributions -> fit_part[tile] (fixed order).
+__device__ void fit_store(const SimDev& S, const double (&acc)[kMaxM], int tile) {
   __shared__ double red[32];
   __shared__ double tot[kMaxM];
+  const int M = S.M;
   for (int q = 0; q < M; ++q) {
     const double v = block_sum(acc[q], red);
     if (threadIdx.x == 0) tot[q] = v;
@@ -196,6 +210,24 @@ __global__ void k_fit(const SimDev* __restrict__ sims, const int* __restrict__ a
     }
     S.fit_part[(size_t)tile * kMaxM + q] = r;
   }
+}
+
+// Fit of the current saturation; skipped when the previous step's transport
+// kernel has already computed it (fit_ready).
+__global__ void k_fit(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk || S.fit_ready[0]) return;
+  const double* s = cur_s(S);
+  double acc[kMaxM];
+#pragma unroll
+  for (int q = 0; q < kMaxM; ++q) acc[q] = 0.0;
+  int e0, e1;
+  tile_range(S, tile, e0, e1);
+  double* lam = S.lam + cur_half(S);
+  double* fw = S.fw + cur_half(S);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) fit_cell(S, s[e], e, lam, fw, acc);
+  fit_store(S, acc, tile);
 }
 
 // ------------------------------------------------------------------ reconstruct
@@ -252,11 +284,7 @@ __global__ void k_reconstruct32(const SimDev* __restrict__ sims, const int* __re
 // coefficients of k_prepare
 //   F = -(c0 lambda_1 dp_1 + c1 lambda_2 dp_2) + c2 [p](midpoint),
 // dp the normal-direction dof of each cell (the gradient times h_n / 2).
-__global__ void k_flux(const SimDev* __restrict__ sims, const int* __restrict__ active) {
-  const SimDev& S = sims[active[blockIdx.y]];
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= S.n_faces || S.status[0] != kStOk) return;
-  const double* lam = S.lam;
+__device__ __forceinline__ double face_flux(const SimDev& S, const double* __restrict__ lam, int f) {
   const double* p0 = S.p;
   const int nx = S.nx, ny = S.ny, nf = S.n_faces;
   int e1 = -1, e2 = -1, bidx = -1;
@@ -279,23 +307,65 @@ __global__ void k_flux(const SimDev* __restrict__ sims, const int* __restrict__ 
   }
   const double* pt = S.p + (xface ? 1 : 2) * (size_t)S.n_cells;  // normal-direction dof
   const double c0 = S.fcoef[f], c1 = S.fcoef[(size_t)nf + f], c2 = S.fcoef[2 * (size_t)nf + f];
-  double F;
   if (e1 >= 0 && e2 >= 0) {
     const double jump = (p0[e1] + pt[e1]) - (p0[e2] - pt[e2]);
-    F = -(c0 * lam[e1] * pt[e1] + c1 * lam[e2] * pt[e2]) + c2 * jump;
-  } else {
-    const int e = (e1 >= 0) ? e1 : e2;
-    const double sgn = (e1 >= 0) ? 1.0 : -1.0;  // outward normal along +axis?
-    double Fout;
-    if (S.bc_type[bidx] == 1) {
-      const double pmid = p0[e] + sgn * pt[e];
-      Fout = -c0 * lam[e] * (sgn * pt[e]) + c2 * (pmid - c1);
-    } else {
-      Fout = c1;
-    }
-    F = sgn * Fout;
+    return -(c0 * lam[e1] * pt[e1] + c1 * lam[e2] * pt[e2]) + c2 * jump;
   }
-  S.F[f] = F;
+  const int e = (e1 >= 0) ? e1 : e2;
+  const double sgn = (e1 >= 0) ? 1.0 : -1.0;  // outward normal along +axis?
+  double Fout;
+  if (S.bc_type[bidx] == 1) {
+    const double pmid = p0[e] + sgn * pt[e];
+    Fout = -c0 * lam[e] * (sgn * pt[e]) + c2 * (pmid - c1);
+  } else {
+    Fout = c1;
+  }
+  return sgn * Fout;
+}
+
+// Fluxes of every face that touches the tile's rows, staged in shared memory
+// ([nr][nx+1] x-faces, then [nr+1][nx] y-faces); the faces the tile owns (its
+// x-faces and the y-faces above its rows, plus the bottom boundary for the
+// first tile) are written to F, each face by exactly one tile (the y-faces
+// below a tile are computed again, bitwise the same, by the tile above them).
+// Then per cell outflow_e / (phi_e |e|) and its tile maximum (cfl_part).
+__global__ void k_flux_cfl(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
+  extern __shared__ double fsh[];
+  const int nx = S.nx;
+  const int j0 = tile * S.tile_rows, nr = min(S.tile_rows, S.ny - j0);
+  const int nfx = nr * (nx + 1), nfy = (nr + 1) * nx;
+  const double* lam = S.lam + cur_half(S);
+  for (int t = threadIdx.x; t < nfx + nfy; t += blockDim.x) {
+    int f;
+    bool own;
+    if (t < nfx) {
+      f = j0 * (nx + 1) + t;
+      own = true;
+    } else {
+      const int u = t - nfx, r = u / nx;
+      f = S.nxf + j0 * nx + u;
+      own = r > 0 || j0 == 0;
+    }
+    const double F = face_flux(S, lam, f);
+    fsh[t] = F;
+    if (own) S.F[f] = F;
+  }
+  __syncthreads();
+  const double* Fx = fsh;
+  const double* Fy = fsh + nfx;
+  double m = 0.0;
+  for (int c = threadIdx.x; c < nr * nx; c += blockDim.x) {
+    const int r = c / nx, i = c - r * nx;
+    const double out = pos_part(-Fx[r * (nx + 1) + i]) + pos_part(Fx[r * (nx + 1) + i + 1]) +
+                       pos_part(-Fy[r * nx + i]) + pos_part(Fy[(r + 1) * nx + i]);
+    m = fmax(m, out * S.inv_pv[j0 * nx + c]);
+  }
+  __shared__ double red[32];
+  const double rmax = block_max(m, red);
+  if (threadIdx.x == 0) S.cfl_part[tile] = rmax;
 }
 
 // Outward fluxes of cell (i,j): left face -F, right +F, bottom -F, top +F.
@@ -307,26 +377,6 @@ __device__ __forceinline__ void cell_faces(const SimDev& S, int e, int& fl, int&
   fr = fl + 1;
   fb = S.nxf + j * nx + i;
   ft = fb + nx;
-}
-
-// ------------------------------------------------------------------ cfl
-__global__ void k_cfl(const SimDev* __restrict__ sims, const int* __restrict__ active) {
-  const SimDev& S = sims[active[blockIdx.y]];
-  const int tile = blockIdx.x;
-  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
-  const int e0 = tile * kCellTile;
-  const int e1 = min(e0 + kCellTile, S.n_cells);
-  double m = 0.0;
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    int fl, fr, fb, ft;
-    cell_faces(S, e, fl, fr, fb, ft);
-    const double out = fmax(-S.F[fl], 0.0) + fmax(S.F[fr], 0.0) + fmax(-S.F[fb], 0.0) +
-                       fmax(S.F[ft], 0.0);
-    m = fmax(m, out * S.inv_pv[e]);
-  }
-  __shared__ double red[32];
-  const double r = block_max(m, red);
-  if (threadIdx.x == 0) S.cfl_part[tile] = r;
 }
 
 // Reading R12: dt = cfl min_e phi_e|e| / (L_f outflow_e) = cfl / (L_f max_e outflow_e / (phi_e|e|)).
@@ -380,11 +430,16 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
   const double* s = cur_s(S);
   double* sn = next_s(S);
   const int nx = S.nx, ny = S.ny;
-  const int e0 = tile * kCellTile;
-  const int e1 = min(e0 + kCellTile, S.n_cells);
+  int e0, e1;
+  tile_range(S, tile, e0, e1);
   double bout = 0.0;
   bool bad = !(dt > 0.0 && dt < DBL_MAX);
-  const double* fw = S.fw;
+  const double* fw = S.fw + cur_half(S);
+  double* lam_n = S.lam + next_half(S);
+  double* fw_n = S.fw + next_half(S);
+  double acc[kMaxM];
+#pragma unroll
+  for (int q = 0; q < kMaxM; ++q) acc[q] = 0.0;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int j = e / nx, i = e - j * nx;
     int fl, fr, fb, ft;
@@ -422,6 +477,7 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
     const double v = s[e] - dt * S.inv_pv[e] * net;
     if (!isfinite(v)) bad = true;
     sn[e] = v;
+    fit_cell(S, v, e, lam_n, fw_n, acc);  // the next step's fit (Eq. leastSquaresFit)
   }
   __shared__ double red[32];
   const double tot = block_sum(bout, red);
@@ -430,6 +486,7 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
     S.mass_part[tile] = tot;
     if (anybad) S.status[0] = kStNonFinite;
   }
+  fit_store(S, acc, tile);
 }
 
 // ------------------------------------------------------------------ finalize
@@ -447,6 +504,7 @@ __global__ void k_finalize(const SimDev* __restrict__ sims, const int* __restric
   S.scal[2] += dt * out;
   S.scal[3] = out;
   S.steps[0] += 1;
+  S.fit_ready[0] = 1;  // k_transport computed lambda, f_w and the fit sums of s^{n+1}
 }
 
 // Saturation exchange with caller memory (pinned host or device pointers).
@@ -458,6 +516,7 @@ __global__ void k_sat_in(const SimDev* __restrict__ sims, const int* __restrict_
   double* s = S.s + (size_t)(S.steps[0] & 1) * S.n_cells;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.n_cells; e += gridDim.x * blockDim.x)
     s[e] = in[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) S.fit_ready[0] = 0;  // the next step fits the new state
 }
 __global__ void k_sat_out(const SimDev* __restrict__ sims, const int* __restrict__ active,
                           double* const* __restrict__ dst) {
@@ -507,14 +566,13 @@ void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int
   else
     k_reconstruct<<<dim3(max_sub, n_active), 256, smem, st>>>(sims, active);
 }
-void launch_flux(const SimDev* sims, const int* active, int n_active, int max_faces,
-                 cudaStream_t st) {
-  k_flux<<<dim3((max_faces + kFaceThreads - 1) / kFaceThreads, n_active), kFaceThreads, 0, st>>>(
-      sims, active);
+void launch_flux_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles, size_t smem,
+                     cudaStream_t st) {
+  k_flux_cfl<<<dim3(max_tiles, n_active), kFaceThreads, smem, st>>>(sims, active);
 }
-void launch_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles,
-                cudaStream_t st) {
-  k_cfl<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
+cudaError_t prepare_flux_cfl(size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)k_flux_cfl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 void launch_transport(const SimDev* sims, const int* active, int n_active, int max_tiles,
                       cudaStream_t st) {

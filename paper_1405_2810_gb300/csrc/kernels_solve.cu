@@ -1440,16 +1440,33 @@ constexpr int kStRetry32 = 2;  // transient status: refactor in FP32 now and sol
 
 // The FP32 factor of an earlier step serves as the preconditioner of the
 // refinement (A changes only through the fitted mobility coefficients, so
-// the factor of a nearby step still contracts) until a step needs more than
-// kRefactorPasses correction passes; the next step then refactors. The warm
+// the factor of a nearby step still contracts) for refactor_period steps; then
+// the simulation refactors. Simulations loaded together therefore refactor on
+// the same steps, which keeps the refinement passes of a launch even (a
+// launch lasts as long as its slowest simulation). A step that needs more than
+// kRefactorPasses correction passes also refactors at the next step. The warm
 // refinement gets at most kStalePasses passes (or refine_iters + 1 if more);
 // a stale factor that has not converged by then, or stalls, is recomputed at
 // once (kStRetry32); a fresh one hands the solve to FP64.
-constexpr int kRefactorPasses = 8;
+constexpr int kRefactorPasses = 10;
 constexpr int kStalePasses = 12;
 
 __device__ __forceinline__ bool wants_factor(const SimDev& S) {
-  return S.info[kInfoAge] == 0 || S.info[kInfoRefactor] != 0;
+  const int age = S.info[kInfoAge];
+  return age == 0 || age > S.refactor_period || S.info[kInfoRefactor] != 0;
+}
+
+// Initial guess of the warm refinement: the linear extrapolation 2 x^n - x^{n-1}
+// of the last two solutions once there are two (xp keeps the last one).
+__device__ void extrapolate_guess(const SimDev& S) {
+  const bool two = S.info[kInfoSolves] >= 2;
+  #pragma unroll 1
+  for (int i = threadIdx.x; i < S.N; i += kThreads) {
+    const double xn = S.x[i];
+    if (two) S.x[i] = 2.0 * xn - S.xp[i];
+    S.xp[i] = xn;
+  }
+  __syncthreads();
 }
 
 // FP32 factorisation of the simulations that need one this step (no factor
@@ -1489,6 +1506,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restri
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
   const bool fresh = S.info[kInfoAge] == 1;
   const int budget = max(iters, kStalePasses - 1);
+  extrapolate_guess(S);
   const int r = csolve_refine<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
                                      budget, m, true);
   if (threadIdx.x == 0) {

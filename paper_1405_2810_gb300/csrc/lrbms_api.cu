@@ -92,6 +92,7 @@ struct lrbms_ctx {
   int precision = LRBMS_FP64;
   int solver = LRBMS_SOLVE_FP64;
   int refine_iters = 1;
+  int refactor_period = 3;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   Arena arena;
@@ -148,6 +149,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   if (!out || !cfg) return LRBMS_E_ARG;
   *out = nullptr;
   if (cfg->max_slots < 1 || cfg->hbm_budget == 0 || cfg->refine_iters < 0 || cfg->refine_iters > 16 ||
+      cfg->refactor_period < 0 || cfg->refactor_period > 1000 ||
       (cfg->precision != LRBMS_FP64 && cfg->precision != LRBMS_MIXED) ||
       (cfg->solver != LRBMS_SOLVE_FP64 && cfg->solver != LRBMS_SOLVE_MIXED))
     return LRBMS_E_ARG;
@@ -156,6 +158,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   ctx->precision = cfg->precision;
   ctx->solver = cfg->solver;
   ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 6 : 1);
+  ctx->refactor_period = cfg->refactor_period > 0 ? cfg->refactor_period : 3;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete ctx;
@@ -295,7 +298,9 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   lrbms::solve_panel_sizes(n_sub, Sx, NE.data(), xoff.data(), &panel_words, &max_w);
   if (lrbms::solve_smem_bytes(n_sub, panel_words, max_w, N, sizeof(double)) > lrbms::kMaxSolveSmem)
     return fail(ctx, LRBMS_E_FORMAT, "reduced system too large for the on-chip solve (shared memory)");
-  const int n_tiles = (n_cells + lrbms::kCellTile - 1) / lrbms::kCellTile;
+  if (nx > lrbms::kMaxNx) return fail(ctx, LRBMS_E_ARG, "nx must be at most 8192");
+  const int tile_rows = std::max(1, lrbms::kCellTile / nx);
+  const int n_tiles = (ny + tile_rows - 1) / tile_rows;
   const bool mixed = ctx->precision == LRBMS_MIXED;
   const size_t Q = (size_t)M + 1;
 
@@ -316,16 +321,17 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_comp32 = mixed ? L.add(4 * Q * (size_t)a_tot) : 0;
   const size_t o_s = L.add(16 * (size_t)n_cells), o_p = L.add(24 * (size_t)n_cells);
   const size_t o_F = L.add(8 * (size_t)n_faces);
-  const size_t o_lam = L.add(8 * (size_t)n_cells), o_fw = L.add(8 * (size_t)n_cells),
+  const size_t o_lam = L.add(16 * (size_t)n_cells), o_fw = L.add(16 * (size_t)n_cells),
                o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces);
-  const size_t o_x = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N), o_y = L.add(16 * (size_t)N),
+  const size_t o_x = L.add(8 * (size_t)N), o_xp = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N),
+               o_y = L.add(16 * (size_t)N),
                o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N);
   const size_t o_A = L.add(8 * (size_t)a_tot);
   const size_t o_L = L.add(8 * (size_t)loff[n_sub]), o_Li = L.add(8 * (size_t)ioff[n_sub]);
   const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
   const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
   const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
-  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 8);
+  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 8), o_fitr = L.add(4);
   const size_t o_sched = L.add(8 * lrbms::sched_words(n_sub, Sx));
   (void)d_tot;
 
@@ -337,7 +343,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   SimDev d{};
   d.nx = nx; d.ny = ny; d.Sx = Sx; d.Sy = Sy; d.cx = cx; d.cy = cy;
   d.n_cells = n_cells; d.n_sub = n_sub; d.n_cf = n_cf; d.nb = nb; d.nxf = nxf; d.n_faces = n_faces;
-  d.M = M; d.N = N; d.max_NE = max_NE; d.n_tiles = n_tiles; d.n_blocks = n_blocks;
+  d.M = M; d.N = N; d.max_NE = max_NE; d.n_tiles = n_tiles; d.tile_rows = tile_rows; d.n_blocks = n_blocks;
   d.panel_words = panel_words;
   d.max_w = max_w;
   d.relperm = pr->relperm; d.swapped = pr->mean_weights; d.prof_mode = off->prof_idx ? 0 : 1;
@@ -362,12 +368,14 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.Phi32 = mixed ? (const float*)P(o_phi32) : nullptr;
   d.comp32 = mixed ? (const float*)P(o_comp32) : nullptr;
   d.s = (double*)P(o_s); d.p = (double*)P(o_p); d.F = (double*)P(o_F);
-  d.x = (double*)P(o_x); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
+  d.x = (double*)P(o_x); d.xp = (double*)P(o_xp); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
+  d.refactor_period = ctx->refactor_period;
   d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv);
   d.A = (double*)P(o_A); d.L = (double*)P(o_L); d.Linv = (double*)P(o_Li);
   d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
   d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);
   d.status = (int*)P(o_status); d.steps = (int*)P(o_steps); d.info = (int*)P(o_info);
+  d.fit_ready = (int*)P(o_fitr);
   d.sched = (const unsigned long long*)P(o_sched);
   d.lam = (double*)P(o_lam); d.fw = (double*)P(o_fw); d.inv_pv = (double*)P(o_ipv); d.fcoef = (double*)P(o_fc);
 
@@ -402,9 +410,11 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_status), 0, 4, st));
   CK(cudaMemsetAsync(P(o_steps), 0, 4, st));
   CK(cudaMemsetAsync(P(o_info), 0, 4 * 8, st));
+  CK(cudaMemsetAsync(P(o_fitr), 0, 4, st));
   CK(cudaMemsetAsync(P(o_p), 0, 24 * (size_t)n_cells, st));
   CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
   CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
+  CK(cudaMemsetAsync(P(o_xp), 0, 8 * (size_t)N, st));
   if (mixed) {
     lrbms::launch_to_float((const double*)P(o_phi), (float*)P(o_phi32), phi_tot, st);
     lrbms::launch_to_float((const double*)P(o_comp), (float*)P(o_comp32), Q * a_tot, st);
@@ -441,7 +451,8 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
   if (n_sims > (int)ctx->slots.size()) return fail(ctx, LRBMS_E_ARG, "too many simulations");
   CK(cudaSetDevice(ctx->device));
   std::vector<int> act(ids, ids + n_sims);
-  int max_tiles = 0, max_blocks = 0, max_sub = 0, max_faces = 0;
+  int max_tiles = 0, max_blocks = 0, max_sub = 0;
+  size_t flux_smem = 0;
   lrbms::SolveShape sh{0, 0, 0, 0};
   for (int id : act) {
     if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
@@ -453,7 +464,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     max_tiles = std::max(max_tiles, d.n_tiles);
     max_blocks = std::max(max_blocks, d.n_blocks + d.n_sub);
     max_sub = std::max(max_sub, d.n_sub);
-    max_faces = std::max(max_faces, d.n_faces);
+    flux_smem = std::max(flux_smem, lrbms::flux_cfl_smem(d.nx, d.ny, d.tile_rows));
   }
   cudaStream_t st = ctx->stream;
   if (act != ctx->last_active) {
@@ -461,9 +472,10 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     ctx->last_active = act;
   }
   const int mixed = ctx->precision == LRBMS_MIXED;
-  const int per_step = 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1);  // mixed solve: factor (where
+  const int per_step = 6 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1);  // mixed solve: factor (where
                                                                      // needed), refine, retry, FP64 redo
   CK(lrbms::prepare_chol_solve(ctx->solver, sh));  // kernel attributes, outside any capture
+  CK(lrbms::prepare_flux_cfl(flux_smem));
   // The kernels of one step, in order; ev (optional) gets an event before the
   // first phase and after every phase.
   auto enqueue_step = [&](cudaEvent_t* ev) -> cudaError_t {
@@ -481,14 +493,12 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(3);
     lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st);
     mark(4);
-    lrbms::launch_flux(ctx->d_sims, ctx->d_active, n_sims, max_faces, st);
+    lrbms::launch_flux_cfl(ctx->d_sims, ctx->d_active, n_sims, max_tiles, flux_smem, st);
     mark(5);
-    lrbms::launch_cfl(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
-    mark(6);
     lrbms::launch_transport(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
-    mark(7);
+    mark(6);
     lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
-    mark(8);
+    mark(7);
     return cudaGetLastError();
   };
   int k = 0;
@@ -501,7 +511,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     // The other steps replay one captured graph of the step's kernels.
     std::vector<long long> key(act.begin(), act.end());
     for (long long v : {(long long)sh.n_sub, (long long)sh.panel_words, (long long)sh.max_w, (long long)sh.N,
-                        (long long)max_tiles, (long long)max_blocks, (long long)max_sub, (long long)max_faces})
+                        (long long)max_tiles, (long long)max_blocks, (long long)max_sub, (long long)flux_smem})
       key.push_back(v);
     if (!ctx->graph || key != ctx->graph_key) {
       if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -692,6 +702,7 @@ int lrbms_set_saturation(lrbms_ctx* ctx, int id, const double* s) {
   int steps = 0;
   CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(d.s + (size_t)(steps & 1) * d.n_cells, s, 8 * (size_t)d.n_cells, cudaMemcpyDefault));
+  CK(cudaMemset(d.fit_ready, 0, 4));  // the next step fits the new saturation
   return LRBMS_OK;
 }
 

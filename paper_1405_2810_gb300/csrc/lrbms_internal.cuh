@@ -8,7 +8,8 @@
 namespace lrbms {
 
 constexpr int kMaxM = 16;         // largest number of mobility profiles
-constexpr int kCellTile = 2048;   // cells per tile of the per-cell kernels
+constexpr int kCellTile = 2048;   // most cells per tile of the per-cell kernels (tiles are whole rows)
+constexpr int kMaxNx = 8192;      // widest fine grid (a tile row and its faces sit in shared memory)
 constexpr int kCellThreads = 256;
 constexpr int kFaceThreads = 256;
 
@@ -28,9 +29,11 @@ struct SimDev {
   int M, N, max_NE;
   int panel_words;  // max over block rows of N_k * (padded W_k): shared-memory panel of the solve
   int max_w;        // widest block row W_k of the solve
-  int n_tiles;      // ceil(n_cells / kCellTile)
+  int tile_rows;    // grid rows per tile: max(1, kCellTile / nx)
+  int n_tiles;      // ceil(ny / tile_rows)
   int n_blocks;     // n_sub + n_cf assembled blocks
   int relperm, swapped, prof_mode, dt_mode;
+  int refactor_period;  // steps one FP32 factor serves (mixed solver)
   double hx, hy, vol, c_pen, Lf, inv_eta_w, inv_eta_o, cfl, dt_fixed, dt_max;
   double lam0, lam1;  // lambda(0), lambda(1)
 
@@ -64,8 +67,8 @@ struct SimDev {
   const unsigned long long* sched;  // copy schedule of the substitutions (launch_sched)
 
   // per-step cell data and load-time coefficients
-  double* lam;      // [n_cells] lambda(s^n) of the current step
-  double* fw;       // [n_cells] f_w(s^n) of the current step
+  double* lam;      // [2][n_cells] lambda(s^n), ping-pong like s
+  double* fw;       // [2][n_cells] f_w(s^n), ping-pong like s
   double* inv_pv;   // [n_cells] 1 / (phi_e |e|)
   double* fcoef;    // [3][n_faces] per-face coefficients of the flux (k_prepare)
 
@@ -74,6 +77,7 @@ struct SimDev {
   double* p;        // [3][n_cells]
   double* F;        // [n_faces]
   double* x;        // [N]
+  double* xp;       // [N] previous step's solution (initial guess of the mixed solver)
   double* b;        // [N]
   double* y;        // [2N] substitution work (forward result, then backward result)
   double* rv;       // [N] refinement residual
@@ -89,6 +93,7 @@ struct SimDev {
   double* theta;    // [M]
   int* status;      // [1]
   int* steps;       // [1]
+  int* fit_ready;   // [1] lambda, f_w and the fit sums of the current s are computed
   int* info;        // [8] solve bookkeeping (kernels_solve.cu, kInfo*); may be null
 };
 
@@ -160,10 +165,14 @@ void launch_sched(const SimDev* sim, cudaStream_t st);
 cudaError_t launch_fine_solve(const SimDev* sims, const int* active, int n_active, cudaStream_t st);
 void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
                         int mixed, cudaStream_t st);
-void launch_flux(const SimDev* sims, const int* active, int n_active, int max_faces,
-                 cudaStream_t st);
-void launch_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles,
-                cudaStream_t st);
+// Face fluxes and per-tile CFL maxima; smem = flux_cfl_smem of the widest tile.
+void launch_flux_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles, size_t smem,
+                     cudaStream_t st);
+cudaError_t prepare_flux_cfl(size_t smem);
+inline size_t flux_cfl_smem(int nx, int ny, int tile_rows) {
+  const int nr = tile_rows < ny ? tile_rows : ny;
+  return 8 * ((size_t)nr * (nx + 1) + (size_t)(nr + 1) * nx);
+}
 void launch_transport(const SimDev* sims, const int* active, int n_active, int max_tiles,
                       cudaStream_t st);
 void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st);

@@ -296,4 +296,4 @@ def test_graph_replay_equals_direct_launches(L, solver):
         out.append((L.lrbms_get_field(ctx, sid, L.FIELD_S), L.lrbms_get_field(ctx, sid, L.FIELD_X), per_step))
         L.lrbms_destroy(ctx)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-    assert out[0][2] == out[1][2] >= 8
+    assert out[0][2] == out[1][2] >= 7
