@@ -79,6 +79,7 @@ enum { LRBMS_FP64 = 0, LRBMS_MIXED = 1 };
 enum { LRBMS_SOLVE_FP64 = 0, LRBMS_SOLVE_MIXED = 1 };
 enum { LRBMS_COREY = 0, LRBMS_LINEAR = 1 };
 enum { LRBMS_DT_CFL = 0, LRBMS_DT_FIXED = 1 };
+enum { LRBMS_VELOCITY_STATE = 0, LRBMS_VELOCITY_FITTED = 1 };
 
 typedef struct {
   int precision;     /* LRBMS_FP64: every phase in FP64. LRBMS_MIXED: basis
@@ -139,6 +140,11 @@ typedef struct {
   double dt_max;         /* upper bound on the CFL step; <= 0: none          */
   int mean_weights;      /* face mean weights: 0 tau_l = a_l/(a1+a2) (as
                             printed, Section 3.1); 1 the swapped weights     */
+  int velocity;          /* mobility in the face fluxes of Definition 2:
+                            LRBMS_VELOCITY_STATE lambda(s^n), as Definition 2
+                            and Algorithm 3 step 5 state; LRBMS_VELOCITY_FITTED
+                            the fitted mobility sum_q theta_q Lambda^q that
+                            the reduced pressure system uses (Section 4.4) */
 } lrbms_problem;
 
 /* Offline data of the offline/online decomposition (Section 4.4) for M
@@ -326,6 +332,23 @@ int lrbms_profile_read(lrbms_ctx* ctx, double* phase_ms, double* step_ms, int* n
  * race and must be serialised by the caller. */
 int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double* A, const double* rhs,
                         double* x, int solver, int refine_iters, void* stream);
+
+/* Advance the listed resident simulations by n_steps steps of the
+ * high-dimensional scheme instead of the reduced one (Algorithm 1, with the
+ * piecewise-constant saturation of Definition 3): per step the fine SWIP-DG
+ * pressure of Definition 1 with the mobility lambda(s^n) (Eqs. swipBilP,
+ * penaltyParam; 3 unknowns per cell, FP64 assembly and an FP64 envelope block
+ * Cholesky with one refinement step, one CTA per simulation), then the face
+ * fluxes of Definition 2, the CFL step and the upwind update exactly as in
+ * lrbms_step. The reduced offline data of the simulations are not used; the
+ * simulations keep their state, so reduced and fine steps can alternate.
+ * All listed simulations must share the fine grid (nx, ny) and use
+ * LRBMS_VELOCITY_STATE (LRBMS_E_ARG otherwise). Scratch device memory for the
+ * fine factors (about 8 * 3 nx ny * 3 (nx + 1) bytes per simulation) is taken
+ * with cudaMalloc and released before return. Waits for completion; status
+ * (optional) receives one lrbms_status per simulation (LRBMS_E_NOT_SPD for a
+ * fine system that is not positive definite). */
+int lrbms_fine_step(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int n_steps, int* status);
 
 /* Wait for all enqueued work. */
 int lrbms_sync(lrbms_ctx* ctx);

@@ -5,7 +5,9 @@ For n -> n+1 with saturation s^n:
       A = c + sum_q theta_q b_q, rhs = e + sum_q theta_q d_q (Eq. reducedSystem);
   (b) solve A x = rhs (a dense Cholesky factorisation; the system is SPD);
   (c) reconstruct p_h^r = sum_i x_i phi_i (step 5(b)) and the face fluxes of
-      Definition 2 with lambda(s^n) (step 5(c), reading R7);
+      Definition 2 with lambda(s^n) (step 5(c), reading R7), or, as a
+      variant, with the fitted mobility sum_q theta_q Lambda^q that the
+      reduced pressure system itself uses (Section 4.4);
   (d) advance the saturation with Definition 3 (step 5(d)).
 """
 from __future__ import annotations
@@ -25,7 +27,9 @@ def assemble(off: Offline, theta: np.ndarray):
     return A, rhs
 
 
-def online_step(model: FineModel, off: Offline, s: np.ndarray, Phi_g=None) -> dict:
+def online_step(model: FineModel, off: Offline, s: np.ndarray, Phi_g=None, velocity: str = "state") -> dict:
+    """One online step from saturation s. velocity: "state" (Definition 2
+    with lambda(s^n), reading R7) or "fitted" (the fitted mobility)."""
     if Phi_g is None:
         Phi_g = off.extra["Phi_g"]
     lam = total_mobility(s, model.eta_w, model.eta_o, model.law)
@@ -35,7 +39,12 @@ def online_step(model: FineModel, off: Offline, s: np.ndarray, Phi_g=None) -> di
     A, rhs = assemble(off, theta)
     x = sla.cho_solve(sla.cho_factor(A), rhs)
     p = Phi_g @ x
-    F = model.fluxes(p, lam)
+    if velocity == "state":
+        F = model.fluxes(p, lam)
+    elif velocity == "fitted":
+        F = model.fluxes(p, lam_fit)
+    else:
+        raise ValueError(velocity)
     dt = model.time_step(F)
     s_new, bout = fv_update(model.grid, s, F, model.poro, dt, model.s_D,
                             model.eta_w, model.eta_o, model.law)

@@ -188,14 +188,26 @@ __device__ __forceinline__ void fit_cell(const SimDev& S, double s, int e, doubl
   }
 }
 
-// Block sums of the tile's fit contributions -> fit_part[tile] (fixed order).
+// Block sums of the tile's fit contributions -> fit_part[tile]: every warp
+// reduces its M bins by shuffles (the accumulators stay in registers: every
+// index is a compile-time constant), then thread q adds the warps' partial
+// sums of bin q in warp order (fixed order, one barrier).
 __device__ void fit_store(const SimDev& S, const double (&acc)[kMaxM], int tile) {
-  __shared__ double red[32];
+  __shared__ double red[kCellThreads / 32][kMaxM];
   __shared__ double tot[kMaxM];
-  const int M = S.M;
-  for (int q = 0; q < M; ++q) {
-    const double v = block_sum(acc[q], red);
-    if (threadIdx.x == 0) tot[q] = v;
+  const int M = S.M, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kMaxM; ++q) {
+    if (q < M) {
+      const double v = warp_sum(acc[q]);
+      if (lane == 0) red[w][q] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double v = 0.0;
+    for (int i = 0; i < nw; ++i) v += red[i][threadIdx.x];
+    tot[threadIdx.x] = v;
   }
   __syncthreads();
   if (threadIdx.x < M) {
@@ -284,7 +296,31 @@ __global__ void k_reconstruct32(const SimDev* __restrict__ sims, const int* __re
 // coefficients of k_prepare
 //   F = -(c0 lambda_1 dp_1 + c1 lambda_2 dp_2) + c2 [p](midpoint),
 // dp the normal-direction dof of each cell (the gradient times h_n / 2).
-__device__ __forceinline__ double face_flux(const SimDev& S, const double* __restrict__ lam, int f) {
+// Mobility of a cell in Definition 2: lambda(s^n) of the cell (reading R7),
+// or the fitted mobility sum_q theta_q Lambda^q_e of the reduced system
+// (variant; from a per-profile-index table for threshold profiles).
+struct MobState {
+  const double* lam;
+  __device__ __forceinline__ double operator[](int e) const { return lam[e]; }
+};
+struct MobFitIndexed {
+  const uint8_t* k;
+  const double* tab;  // [kMaxM + 1]: fitted mobility of a cell whose first lambda(1) index is k
+  __device__ __forceinline__ double operator[](int e) const { return tab[k[e]]; }
+};
+struct MobFitDense {
+  const double* prof;
+  const double* theta;  // shared copy
+  int M, n;
+  __device__ __forceinline__ double operator[](int e) const {
+    double v = 0.0;
+    for (int q = 0; q < M; ++q) v = fma(theta[q], prof[(size_t)q * n + e], v);
+    return v;
+  }
+};
+
+template <typename Mob>
+__device__ __forceinline__ double face_flux(const SimDev& S, const Mob& lam, int f) {
   const double* p0 = S.p;
   const int nx = S.nx, ny = S.ny, nf = S.n_faces;
   int e1 = -1, e2 = -1, bidx = -1;
@@ -329,15 +365,9 @@ __device__ __forceinline__ double face_flux(const SimDev& S, const double* __res
 // first tile) are written to F, each face by exactly one tile (the y-faces
 // below a tile are computed again, bitwise the same, by the tile above them).
 // Then per cell outflow_e / (phi_e |e|) and its tile maximum (cfl_part).
-__global__ void k_flux_cfl(const SimDev* __restrict__ sims, const int* __restrict__ active) {
-  const SimDev& S = sims[active[blockIdx.y]];
-  const int tile = blockIdx.x;
-  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
-  extern __shared__ double fsh[];
+template <typename Mob>
+__device__ void tile_fluxes(const SimDev& S, const Mob& lam, double* fsh, int j0, int nfx, int nfy) {
   const int nx = S.nx;
-  const int j0 = tile * S.tile_rows, nr = min(S.tile_rows, S.ny - j0);
-  const int nfx = nr * (nx + 1), nfy = (nr + 1) * nx;
-  const double* lam = S.lam + cur_half(S);
   for (int t = threadIdx.x; t < nfx + nfy; t += blockDim.x) {
     int f;
     bool own;
@@ -352,6 +382,36 @@ __global__ void k_flux_cfl(const SimDev* __restrict__ sims, const int* __restric
     const double F = face_flux(S, lam, f);
     fsh[t] = F;
     if (own) S.F[f] = F;
+  }
+}
+
+__global__ void k_flux_cfl(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
+  extern __shared__ double fsh[];
+  const int nx = S.nx;
+  const int j0 = tile * S.tile_rows, nr = min(S.tile_rows, S.ny - j0);
+  const int nfx = nr * (nx + 1), nfy = (nr + 1) * nx;
+  if (S.vel_mode == 0) {
+    tile_fluxes(S, MobState{S.lam + cur_half(S)}, fsh, j0, nfx, nfy);
+  } else {
+    __shared__ double th[kMaxM], tab[kMaxM + 1];
+    if (threadIdx.x < S.M) th[threadIdx.x] = S.theta[threadIdx.x];
+    __syncthreads();
+    if (S.prof_mode == 0) {
+      // index k: Lambda^q = lambda(0) for q < k, lambda(1) for q >= k (1-based)
+      if (threadIdx.x >= 1 && threadIdx.x <= S.M) {
+        const int k = threadIdx.x;
+        double v = 0.0;
+        for (int q = 1; q <= S.M; ++q) v = fma(th[q - 1], q >= k ? S.lam1 : S.lam0, v);
+        tab[k] = v;
+      }
+      __syncthreads();
+      tile_fluxes(S, MobFitIndexed{S.prof_idx, tab}, fsh, j0, nfx, nfy);
+    } else {
+      tile_fluxes(S, MobFitDense{S.prof, th, S.M, S.n_cells}, fsh, j0, nfx, nfy);
+    }
   }
   __syncthreads();
   const double* Fx = fsh;

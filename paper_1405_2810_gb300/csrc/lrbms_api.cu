@@ -158,7 +158,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   ctx->precision = cfg->precision;
   ctx->solver = cfg->solver;
   ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 6 : 1);
-  ctx->refactor_period = cfg->refactor_period > 0 ? cfg->refactor_period : 3;
+  ctx->refactor_period = cfg->refactor_period > 0 ? cfg->refactor_period : 3;  // measured best at 512 sims
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete ctx;
@@ -212,6 +212,8 @@ int lrbms_internal_sim(lrbms_ctx* ctx, int id, SimDev* out) {
   return LRBMS_OK;
 }
 int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+SimDev* lrbms_internal_dsims(lrbms_ctx* ctx) { return ctx->d_sims; }
+void lrbms_internal_count(lrbms_ctx* ctx, long long n) { ctx->launches += n; }
 
 long long lrbms_launch_count(const lrbms_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
@@ -246,6 +248,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
     return fail(ctx, LRBMS_E_ARG, "exactly one of prof_idx and prof must be given");
   if (pr->dt_mode == LRBMS_DT_CFL && !(pr->cfl > 0 && off->Lf > 0))
     return fail(ctx, LRBMS_E_ARG, "CFL step needs cfl > 0 and Lf > 0");
+  if (pr->velocity != LRBMS_VELOCITY_STATE && pr->velocity != LRBMS_VELOCITY_FITTED)
+    return fail(ctx, LRBMS_E_ARG, "velocity must be LRBMS_VELOCITY_STATE or LRBMS_VELOCITY_FITTED");
   if (pr->dt_mode == LRBMS_DT_FIXED && !(pr->dt_fixed > 0))
     return fail(ctx, LRBMS_E_ARG, "fixed step needs dt_fixed > 0");
   int slot = -1;
@@ -347,6 +351,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.panel_words = panel_words;
   d.max_w = max_w;
   d.relperm = pr->relperm; d.swapped = pr->mean_weights; d.prof_mode = off->prof_idx ? 0 : 1;
+  d.vel_mode = pr->velocity;
   d.dt_mode = pr->dt_mode;
   d.hx = pr->Lx / nx; d.hy = pr->Ly / ny; d.vol = d.hx * d.hy; d.c_pen = off->c_pen; d.Lf = off->Lf;
   d.inv_eta_w = 1.0 / pr->eta_w; d.inv_eta_o = 1.0 / pr->eta_o; d.cfl = pr->cfl;

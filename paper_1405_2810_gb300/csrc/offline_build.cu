@@ -351,6 +351,22 @@ __device__ double block_reduce_sum(double v, double* red) {
 // of modified Gram-Schmidt in L2(E) (weights |e| (1, 1/3, 1/3)) and rejected
 // when its remaining norm is below 1e-10 of its original norm; stops at N_E.
 // Output layout: [N_E][3 cells_E], row k*cells_E + c.
+// The fine solution x [n_cells][3] of system blockIdx.y into the pressure
+// field p [3][n_cells] of its resident simulation.
+struct SoaJob {
+  const double* x;
+  double* p;
+  int n_cells;
+};
+__global__ void k_fine_to_soa(const SoaJob* __restrict__ jobs) {
+  const SoaJob J = jobs[blockIdx.y];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J.n_cells; e += gridDim.x * blockDim.x) {
+    J.p[e] = J.x[3 * e];
+    J.p[(size_t)J.n_cells + e] = J.x[3 * e + 1];
+    J.p[2 * (size_t)J.n_cells + e] = J.x[3 * e + 2];
+  }
+}
+
 struct GsJob {
   int prob, E, NE, n_snap;
   const double* const* snaps;  // cell-major fine pressures
@@ -707,6 +723,8 @@ using namespace lrbms;
 extern "C" cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx);
 extern "C" int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg);
 extern "C" int lrbms_internal_sim(lrbms_ctx* ctx, int id, lrbms::SimDev* out);
+extern "C" lrbms::SimDev* lrbms_internal_dsims(lrbms_ctx* ctx);
+extern "C" void lrbms_internal_count(lrbms_ctx* ctx, long long n);
 
 #define BCK(call)                                                              \
   do {                                                                         \
@@ -1146,10 +1164,102 @@ extern "C" int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_
   pr.relperm = d.relperm; pr.bc_type = d.bc_type; pr.p_D = d.p_D; pr.v_N = d.v_N; pr.s_D = d.s_D;
   pr.s0 = s0; pr.cfl = d.cfl; pr.dt_mode = d.dt_mode; pr.dt_fixed = d.dt_fixed; pr.dt_max = d.dt_max;
   pr.mean_weights = d.swapped;
+  pr.velocity = d.vel_mode;
   lrbms_offline off{};
   off.M = d.M; off.N_E = d.NE; off.prof_idx = d.prof_idx; off.prof = d.prof; off.Gpinv = d.Gpinv;
   off.Phi = uPhi; off.Dblk = ucomp; off.Fblk = n_cf ? ucomp + (size_t)Q * aoff[n_sub] : nullptr;
   off.rhs = urhs; off.c_pen = d.c_pen; off.Lf = d.Lf;
   BCK(cudaStreamSynchronize(st));
   return lrbms_offline_load(ctx, &pr, &off, sim_id);
+}
+
+// Algorithm 1 (the high-dimensional IMPES scheme) on resident simulations:
+// per step the fine SWIP-DG pressure system of Definition 1 with lambda(s^n)
+// is assembled and solved in FP64 (one envelope block Cholesky per system,
+// one-cell blocks), and the fine pressure then goes through the same flux
+// (Definition 2), CFL and upwind transport (Definition 3) kernels as the
+// reduced step.
+extern "C" int lrbms_fine_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* status) {
+  if (!ctx || n_sims < 1 || !ids || n_steps < 0) return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad arguments");
+  cudaStream_t st = lrbms_internal_stream(ctx);
+  std::vector<SimDev> sd(n_sims);
+  for (int i = 0; i < n_sims; ++i) {
+    if (lrbms_internal_sim(ctx, ids[i], &sd[i])) return lrbms_internal_fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+    if (sd[i].nx != sd[0].nx || sd[i].ny != sd[0].ny)
+      return lrbms_internal_fail(ctx, LRBMS_E_ARG, "the simulations of one fine step must share the fine grid");
+    if (sd[i].vel_mode != 0)
+      return lrbms_internal_fail(ctx, LRBMS_E_ARG, "the fine scheme uses lambda(s^n): velocity must be STATE");
+    if (sd[i].nx < 2 || sd[i].ny < 2) return lrbms_internal_fail(ctx, LRBMS_E_ARG, "fine grid must be at least 2x2");
+  }
+  const int nx = sd[0].nx, ny = sd[0].ny, n_cells = nx * ny;
+  DevBuf B;
+  FineSolver fs;
+  if (!fs.init(B, nx, ny, n_sims, st))
+    return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the fine systems");
+  std::vector<FineDev> fd(n_sims);
+  int max_tiles = 0;
+  size_t flux_smem = 0;
+  for (int i = 0; i < n_sims; ++i) {
+    const SimDev& d = sd[i];
+    FineDev& f = fd[i];
+    f.nx = nx; f.ny = ny; f.Sx = d.Sx; f.Sy = d.Sy; f.cx = d.cx; f.cy = d.cy; f.n_cells = n_cells;
+    f.nxf = d.nxf; f.n_faces = d.n_faces; f.nb = d.nb; f.M = d.M; f.relperm = d.relperm; f.swapped = d.swapped;
+    f.hx = d.hx; f.hy = d.hy; f.vol = d.vol; f.c_pen = d.c_pen; f.inv_eta_w = d.inv_eta_w; f.inv_eta_o = d.inv_eta_o;
+    f.lam0 = d.lam0; f.lam1 = d.lam1;
+    f.perm = d.perm; f.poro = d.poro; f.bc_type = d.bc_type; f.p_D = d.p_D; f.v_N = d.v_N; f.s_D = d.s_D;
+    f.prof_idx = nullptr;
+    max_tiles = std::max(max_tiles, d.n_tiles);
+    flux_smem = std::max(flux_smem, flux_cfl_smem(d.nx, d.ny, d.tile_rows));
+  }
+  FineDev* d_fd = B.get<FineDev>(n_sims);
+  SysJob* d_jobs = B.get<SysJob>(n_sims);
+  SoaJob* d_soa = B.get<SoaJob>(n_sims);
+  int* d_act = B.get<int>(n_sims);
+  if (!d_fd || !d_jobs || !d_soa || !d_act)
+    return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the fine systems");
+  std::vector<SysJob> jobs(n_sims);
+  std::vector<SoaJob> soa(n_sims);
+  for (int i = 0; i < n_sims; ++i) {
+    jobs[i] = SysJob{i, 0, 3, 0, nullptr, fs.sims[i].A, fs.sims[i].A + 9 * (size_t)n_cells, fs.sims[i].b};
+    soa[i] = SoaJob{fs.sims[i].x, sd[i].p, n_cells};
+  }
+  BCK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(SysJob) * n_sims, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(d_soa, soa.data(), sizeof(SoaJob) * n_sims, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(d_act, ids, sizeof(int) * n_sims, cudaMemcpyHostToDevice, st));
+  BCK(prepare_flux_cfl(flux_smem));
+  SimDev* d_sims = lrbms_internal_dsims(ctx);
+  std::vector<int> sst(n_sims, 0), steps(n_sims, 0);
+  for (int k = 0; k < n_steps; ++k) {
+    // the current saturation of each simulation (ping-pong by its step count)
+    BCK(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_sims; ++i) {
+      BCK(cudaMemcpy(&steps[i], sd[i].steps, 4, cudaMemcpyDeviceToHost));
+      fd[i].s0 = sd[i].s + (size_t)(steps[i] & 1) * n_cells;
+      BCK(cudaMemsetAsync(sd[i].fit_ready, 0, 4, st));  // lambda, f_w of s^n for flux and transport
+    }
+    BCK(cudaMemcpyAsync(d_fd, fd.data(), sizeof(FineDev) * n_sims, cudaMemcpyHostToDevice, st));
+    const int n = std::max(n_cells, sd[0].n_faces);
+    k_fine_system<<<dim3((n + 127) / 128, (unsigned)n_sims), 128, 0, st>>>(d_fd, d_jobs);
+    BCK(launch_fine_solve(fs.d_sims, fs.d_active, n_sims, st));
+    k_fine_to_soa<<<dim3((n_cells + 255) / 256 < 152 ? (n_cells + 255) / 256 : 152, (unsigned)n_sims), 256, 0, st>>>(
+        d_soa);
+    BCK(cudaGetLastError());
+    // a fine system that is not positive definite freezes its simulation
+    BCK(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_sims; ++i) {
+      int fst = 0;
+      BCK(cudaMemcpy(&fst, fs.sims[i].status, 4, cudaMemcpyDeviceToHost));
+      if (fst != 0) BCK(cudaMemcpy(sd[i].status, &fst, 4, cudaMemcpyHostToDevice));
+    }
+    launch_fit(d_sims, d_act, n_sims, max_tiles, st);
+    launch_flux_cfl(d_sims, d_act, n_sims, max_tiles, flux_smem, st);
+    launch_transport(d_sims, d_act, n_sims, max_tiles, st);
+    launch_finalize(d_sims, d_act, n_sims, st);
+    BCK(cudaGetLastError());
+    lrbms_internal_count(ctx, 8);
+  }
+  BCK(cudaStreamSynchronize(st));
+  if (status)
+    for (int i = 0; i < n_sims; ++i) BCK(cudaMemcpy(&status[i], sd[i].status, 4, cudaMemcpyDeviceToHost));
+  return LRBMS_OK;
 }

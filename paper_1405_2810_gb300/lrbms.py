@@ -32,6 +32,8 @@ LRBMS_COREY = 0
 LRBMS_LINEAR = 1
 LRBMS_DT_CFL = 0
 LRBMS_DT_FIXED = 1
+LRBMS_VELOCITY_STATE = 0
+LRBMS_VELOCITY_FITTED = 1
 LRBMS_SOLVE_FP64 = 0
 LRBMS_SOLVE_MIXED = 1
 FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS, FIELD_SOLVE_INFO = range(10)
@@ -40,7 +42,7 @@ EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offlin
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
             "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count", "lrbms_solve_noalloc",
-            "lrbms_last_error"]
+            "lrbms_fine_step", "lrbms_last_error"]
 
 
 class LrbmsError(RuntimeError):
@@ -63,7 +65,7 @@ class Problem(C.Structure):
                 ("bc_type", C.c_void_p), ("p_D", C.c_void_p), ("v_N", C.c_void_p),
                 ("s_D", C.c_void_p), ("s0", C.c_void_p),
                 ("cfl", C.c_double), ("dt_mode", C.c_int), ("dt_fixed", C.c_double),
-                ("dt_max", C.c_double), ("mean_weights", C.c_int)]
+                ("dt_max", C.c_double), ("mean_weights", C.c_int), ("velocity", C.c_int)]
 
 
 class Offline(C.Structure):
@@ -100,6 +102,7 @@ def library() -> C.CDLL:
         lib.lrbms_profile_read.argtypes = [vp, dp, dp, C.POINTER(i)]
         lib.lrbms_release.argtypes = [vp, i]
         lib.lrbms_step.argtypes = [vp, i, vp, i, vp]
+        lib.lrbms_fine_step.argtypes = [vp, i, vp, i, vp]
         lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
         lib.lrbms_get_state.argtypes = [vp, i, vp, dp, dp]
         lib.lrbms_set_saturation.argtypes = [vp, i, vp]
@@ -162,7 +165,7 @@ def _problem_struct(problem: dict, keep: dict) -> Problem:
                    problem.get("relperm", LRBMS_COREY), _ptr(pa["bc_type"]), _ptr(pa["p_D"]),
                    _ptr(pa["v_N"]), _ptr(pa["s_D"]), _ptr(pa["s0"]), problem.get("cfl", 0.5),
                    problem.get("dt_mode", LRBMS_DT_CFL), problem.get("dt_fixed", 0.0),
-                   problem.get("dt_max", 0.0), problem.get("mean_weights", 0))
+                   problem.get("dt_max", 0.0), problem.get("mean_weights", 0), problem.get("velocity", 0))
 
 
 def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return_sizes=False):
@@ -221,7 +224,7 @@ def lrbms_offline_load(ctx, problem: dict, offline: dict) -> int:
                  problem.get("relperm", LRBMS_COREY), _ptr(pa["bc_type"]), _ptr(pa["p_D"]),
                  _ptr(pa["v_N"]), _ptr(pa["s_D"]), _ptr(pa["s0"]), problem.get("cfl", 0.5),
                  problem.get("dt_mode", LRBMS_DT_CFL), problem.get("dt_fixed", 0.0),
-                 problem.get("dt_max", 0.0), problem.get("mean_weights", 0))
+                 problem.get("dt_max", 0.0), problem.get("mean_weights", 0), problem.get("velocity", 0))
     oa = {k: _as(offline.get(k), dt) for k, dt in (("N_E", np.int32), ("prof_idx", np.uint8),
                                                  ("prof", np.float64), ("Gpinv", np.float64),
                                                  ("Phi", np.float64), ("Dblk", np.float64),
@@ -244,6 +247,15 @@ def lrbms_step(ctx, sim_ids, n_steps: int = 1, wait: bool = True):
     ids = np.ascontiguousarray(sim_ids, dtype=np.int32)
     status = np.zeros(len(ids), dtype=np.int32) if wait else None
     _check(ctx, library().lrbms_step(ctx, len(ids), _ptr(ids), n_steps, _ptr(status)))
+    return status
+
+
+def lrbms_fine_step(ctx, sim_ids, n_steps: int = 1):
+    """Steps of the high-dimensional scheme (Algorithm 1) on resident
+    simulations; returns the per-simulation status."""
+    ids = np.ascontiguousarray(sim_ids, dtype=np.int32)
+    status = np.zeros(len(ids), dtype=np.int32)
+    _check(ctx, library().lrbms_fine_step(ctx, len(ids), _ptr(ids), n_steps, _ptr(status)))
     return status
 
 

@@ -297,3 +297,22 @@ def test_graph_replay_equals_direct_launches(L, solver):
         L.lrbms_destroy(ctx)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2] == out[1][2] >= 7
+
+
+@pytest.mark.parametrize("dense", [False, True], ids=["threshold-profiles", "dense-profiles"])
+def test_fitted_velocity_variant(L, dense):
+    """Fluxes with the fitted mobility sum_q theta_q Lambda^q (reading R7's
+    variant) against the oracle's variant, three steps from its states."""
+    prob, m, co, off = c = case("small", kind="snapshots")
+    ctx = _ctx(L, solver=1)
+    sid = _load(L, ctx, c, dense=dense, velocity=1)
+    s = prob.s0.copy()
+    for _ in range(8):
+        s = online_step(m, off, s, velocity="fitted")["s"]
+    for _ in range(3):
+        L.lrbms_set_saturation(ctx, sid, s)
+        assert L.lrbms_step(ctx, [sid], 1)[0] == 0
+        ref = online_step(m, off, s, velocity="fitted")
+        _compare_step(L, ctx, sid, c, s, ref=ref)
+        s = ref["s"]
+    L.lrbms_destroy(ctx)

@@ -168,3 +168,27 @@ def test_reduced_close_to_fine_early(small_case):
     a = online_step(m, off, prob.s0)
     f = m.step(prob.s0)
     assert np.linalg.norm(a["p"] - f["p"]) <= 1e-2 * np.linalg.norm(f["p"])
+
+
+def test_fitted_velocity_variant():
+    """The fitted-mobility velocity (reading R7's variant) uses
+    sum_q theta_q Lambda^q in Definition 2. For a uniform saturation the fit
+    is exact (T8), so both variants give the same fluxes to round-off; after
+    the front has formed they differ, and the variant still conserves the
+    water volume exactly (its fluxes are single-valued per face)."""
+    from lrbms_cases import case
+    from oracle.reduced import online_step
+    prob, m, co, off = case("small", kind="snapshots")
+    s_u = np.full(prob.n_cells, 0.4)
+    a = online_step(m, off, s_u)
+    b = online_step(m, off, s_u, velocity="fitted")
+    assert np.linalg.norm(a["F"] - b["F"]) <= 1e-11 * np.linalg.norm(a["F"])
+    s = prob.s0.copy()
+    for _ in range(10):
+        s = online_step(m, off, s)["s"]
+    a = online_step(m, off, s)
+    b = online_step(m, off, s, velocity="fitted")
+    assert np.linalg.norm(a["F"] - b["F"]) > 1e-6 * np.linalg.norm(a["F"])
+    vol = prob.poro * m.grid.vol
+    dm = np.sum(vol * b["s"]) - np.sum(vol * s)
+    assert abs(dm + b["dt"] * b["boundary_outflow"]) <= 1e-13 * abs(b["dt"] * b["boundary_outflow"])
