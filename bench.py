@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="profiling runs: build, warm up, run the timed steps and stop (no phase, end-to-end, "
+                         "plain-path or CPU legs; the JSON line then holds only the timed value)")
     ap.add_argument("--serving", action="store_true",
                     help="continuous-batching serving run with Poisson arrivals (its own JSON line)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
@@ -471,6 +474,15 @@ def main():
     L.lrbms_profile_start(ctx, Kp)
     L.lrbms_step(ctx, ids, Kp, wait=False)
     phase_ms, _ = L.lrbms_profile_read(ctx, Kp)
+
+    if a.kernels_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "sim-steps/s", "steps": K,
+                              "ms_per_step": elapsed_ms / K, "sims_ok": n_ok, "kernels_only": True}))
+        L.lrbms_destroy(ctx)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # ---- end to end through lrbms_step_io with pinned host buffers
     n_cells = a.n * a.n

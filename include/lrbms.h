@@ -180,18 +180,31 @@ int lrbms_destroy(lrbms_ctx* ctx);
 
 /* Admit one simulation: validate shapes, charge the arena, copy the problem
  * and offline data to the device and set s = s0, t = 0. On success *sim_id
- * receives the slot. LRBMS_E_BUDGET if the arena or slot table is full. */
+ * receives the slot. LRBMS_E_BUDGET if the arena or slot table is full. The
+ * copies and set-up kernels run on the context's admission stream, so they
+ * overlap steps in flight on the context stream; the call returns once they
+ * are done. */
 int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* prob,
                        const lrbms_offline* off, int* sim_id);
 /* Release a simulation's slot and arena memory. */
 int lrbms_release(lrbms_ctx* ctx, int sim_id);
 
 /* Enqueue n_steps online steps (Algorithm 3, step 5) for the n_sims listed
- * simulations on the context stream, all simulations in each launch. With
- * status == NULL the call returns once the work is enqueued; otherwise it
- * waits for the stream and writes one lrbms_status per simulation. */
+ * simulations on the context stream, all simulations in each launch (one
+ * captured CUDA graph per step while the list and its launch shape stay the
+ * same). With status == NULL the call returns once the work is enqueued;
+ * otherwise it waits for the stream and writes one lrbms_status per
+ * simulation (n_steps = 0: the current statuses). */
 int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int n_steps,
                int* status);
+
+/* After an lrbms_step with n_steps >= 1 and status == NULL: wait for the
+ * context stream and write the statuses of the first n_sims simulations of
+ * that call's list (one device-to-host copy for the whole batch). Work
+ * enqueued meanwhile on the admission stream (lrbms_offline_load and
+ * lrbms_clone of simulations outside the batch) is not waited for, so a
+ * serving loop can admit new simulations while a step runs. */
+int lrbms_step_status(lrbms_ctx* ctx, int n_sims, int* status);
 
 /* Run n_steps steps of one simulation, wait, and copy the saturation
  * [n_cells], pressure [3][n_cells] and face fluxes [n_faces] of the last step
@@ -270,7 +283,9 @@ int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
  * subdomain, host or device; NULL: an unrotated copy): Phi_E Q_E, and
  * Q_E^T (.) Q_E' for every component block and right-hand side. The online
  * results are unchanged up to round-off; the stored bytes differ. The copy
- * starts from src's current saturation, at time 0. */
+ * starts from src's current saturation, at time 0. It runs on the admission
+ * stream; if src was in the last stepped batch the call first waits for the
+ * context stream. */
 int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_id);
 
 /* Like lrbms_step, with the saturation exchanged with caller memory: before
@@ -349,6 +364,22 @@ int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double* A, const d
  * (optional) receives one lrbms_status per simulation (LRBMS_E_NOT_SPD for a
  * fine system that is not positive definite). */
 int lrbms_fine_step(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int n_steps, int* status);
+
+/* CTA sizes the autotuner picked for the assembly and reconstruction kernels
+ * of the shape class of these simulations (largest basis size in classes of
+ * 8, cells per subdomain, component precision). The first lrbms_step of a new
+ * class times each candidate on the live data and keeps the fastest; the
+ * results do not depend on the choice. LRBMS_E_STATE before that step. */
+int lrbms_tuned_threads(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int* assemble, int* reconstruct);
+
+/* Test hook for the failure detection of the bounded device-side waits; the
+ * paper has no counterpart. The next reduced solve of sim_id withholds the
+ * last bulk copy of its forward/backward substitution (every earlier copy has
+ * been awaited by then, so nothing is left in flight); the wait for it gives
+ * up after its limit (about 2 s), and the simulation stops with
+ * LRBMS_E_TIMEOUT while the others in the launch continue unchanged. The hook
+ * fires once. */
+int lrbms_test_withhold_copy(lrbms_ctx* ctx, int sim_id);
 
 /* Wait for all enqueued work. */
 int lrbms_sync(lrbms_ctx* ctx);

@@ -550,12 +550,16 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
 }
 
 // ------------------------------------------------------------------ finalize
+// status_out (optional) receives every listed simulation's status word, in
+// list order, so that the host reads the batch's statuses with one copy.
 __global__ void k_finalize(const SimDev* __restrict__ sims, const int* __restrict__ active,
-                           int n_active) {
+                           int n_active, int* __restrict__ status_out) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_active) return;
   const SimDev& S = sims[active[a]];
-  if (S.status[0] != kStOk) return;
+  const int st = S.status[0];
+  if (status_out) status_out[a] = st;
+  if (st != kStOk) return;
   const double dt = step_dt(S);
   double out = 0.0;
   for (int t = 0; t < S.n_tiles; ++t) out += S.mass_part[t];
@@ -618,13 +622,14 @@ void launch_fit(const SimDev* sims, const int* active, int n_active, int max_til
                 cudaStream_t st) {
   k_fit<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
 }
+// threads: CTA size; every size computes each pressure dof the same way.
 void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
-                        int mixed, cudaStream_t st) {
+                        int mixed, cudaStream_t st, int threads) {
   const size_t smem = 64 * sizeof(double);  // max_NE <= 64 (checked at load)
   if (mixed)
-    k_reconstruct32<<<dim3(max_sub, n_active), 256, smem, st>>>(sims, active);
+    k_reconstruct32<<<dim3(max_sub, n_active), threads, smem, st>>>(sims, active);
   else
-    k_reconstruct<<<dim3(max_sub, n_active), 256, smem, st>>>(sims, active);
+    k_reconstruct<<<dim3(max_sub, n_active), threads, smem, st>>>(sims, active);
 }
 void launch_flux_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles, size_t smem,
                      cudaStream_t st) {
@@ -638,8 +643,8 @@ void launch_transport(const SimDev* sims, const int* active, int n_active, int m
                       cudaStream_t st) {
   k_transport<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
 }
-void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st) {
-  k_finalize<<<(n_active + 127) / 128, 128, 0, st>>>(sims, active, n_active);
+void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st, int* status_out) {
+  k_finalize<<<(n_active + 127) / 128, 128, 0, st>>>(sims, active, n_active, status_out);
 }
 
 }  // namespace lrbms

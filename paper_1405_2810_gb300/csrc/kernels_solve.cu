@@ -145,6 +145,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Hint: bring [src, src + bytes) into L2 (no destination, no completion to
+// wait for); src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -920,8 +925,11 @@ struct WRing {
 };
 
 // Issue a chunk if it fits (lane 0 copies); returns false if the region is full.
+// withhold: account for the chunk but do not copy it (the test hook of the
+// bounded waits: its full barrier never completes).
 template <typename T>
-__device__ __forceinline__ bool wring_try_issue(WRing<T>& r, const T* src, long long off, int count, int lane) {
+__device__ __forceinline__ bool wring_try_issue(WRing<T>& r, const T* src, long long off, int count, int lane,
+                                                bool withhold = false) {
   constexpr int kA = 16 / (int)sizeof(T);
   if ((int)(r.issued - r.consumed) >= kEnt) return false;
   const int d = (int)(off & (kA - 1));
@@ -945,8 +953,10 @@ __device__ __forceinline__ bool wring_try_issue(WRing<T>& r, const T* src, long 
   if (lane == 0) {
     r.eoff[b] = at + d;
     r.epos[b] = at;
-    mbar_expect_tx(&r.full[b], (uint32_t)(need * (int)sizeof(T)));
-    bulk_g2s(r.base + at, src + (off - d), (uint32_t)(need * (int)sizeof(T)), &r.full[b]);
+    if (!withhold) {
+      mbar_expect_tx(&r.full[b], (uint32_t)(need * (int)sizeof(T)));
+      bulk_g2s(r.base + at, src + (off - d), (uint32_t)(need * (int)sizeof(T)), &r.full[b]);
+    }
   }
   r.pos = at + need;
   ++r.issued;
@@ -1072,6 +1082,7 @@ struct SFeed {
   const unsigned long long* d;
   int n, next, base;
   unsigned long long cur, nxt;
+  int withhold;  // chunk whose copy is withheld (test hook), or -1
 };
 
 __device__ __forceinline__ SFeed sfeed_open(const unsigned long long* sched, int w, int lane) {
@@ -1083,12 +1094,17 @@ __device__ __forceinline__ SFeed sfeed_open(const unsigned long long* sched, int
   f.base = 0;
   f.cur = lane < f.n ? f.d[lane] : 0ull;
   f.nxt = 32 + lane < f.n ? f.d[32 + lane] : 0ull;
+  f.withhold = -1;
   return f;
 }
 
-// Issue the warp's next chunks while they fit.
+// Issue the warp's next chunks while they fit; with each issued chunk, the
+// chunk kL2Ahead places further on is prefetched into L2, so that its bulk
+// copy later reads L2 instead of HBM.
+constexpr int kL2Ahead = 16;
 template <typename T>
 __device__ __forceinline__ void srefill(WRing<T>& r, SFeed& f, const T* LT, const T* Linv, int lane) {
+  constexpr int kA = 16 / (int)sizeof(T);
   #pragma unroll 1
   while (f.next < f.n) {
     if (f.next - f.base == 32) {
@@ -1099,7 +1115,20 @@ __device__ __forceinline__ void srefill(WRing<T>& r, SFeed& f, const T* LT, cons
     }
     const unsigned long long dsc = __shfl_sync(0xffffffffu, f.cur, f.next - f.base);
     const T* src = (dsc & kDescInverse) ? Linv : LT;
-    if (!wring_try_issue<T>(r, src, (long long)(dsc & kDescOffMask), (int)((dsc >> 40) & 0x7ff), lane)) return;
+    if (!wring_try_issue<T>(r, src, (long long)(dsc & kDescOffMask), (int)((dsc >> 40) & 0x7ff), lane,
+                            f.next == f.withhold))
+      return;
+    const int ja = f.next + kL2Ahead;  // within the 64 descriptors held in cur and nxt
+    if (ja < f.n) {
+      const int rel = ja - f.base;
+      const unsigned long long da = __shfl_sync(0xffffffffu, rel < 32 ? f.cur : f.nxt, rel & 31);
+      if (lane == 0) {
+        const long long off = (long long)(da & kDescOffMask);
+        const int d = (int)(off & (kA - 1));
+        const uint32_t bytes = (uint32_t)((d + (int)((da >> 40) & 0x7ff)) * (int)sizeof(T) + 15) & ~15u;
+        prefetch_l2(((da & kDescInverse) ? Linv : LT) + (off - d), bytes);
+      }
+    }
     ++f.next;
   }
 }
@@ -1173,6 +1202,10 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
     z[i] = T(0);
   }
   SFeed fd = sfeed_open(S.sched, w, lane);
+  // Test hook of the bounded waits: the leader withholds the last chunk of its
+  // list. Every earlier chunk has been awaited by then, so when that one wait
+  // runs out no copy is left in flight.
+  if (w == 0 && S.inject && S.inject[0] != 0) fd.withhold = fd.n - 1;
   srefill<T>(rg, fd, LT, Linv, lane);
   __syncthreads();
   // forward
@@ -1264,6 +1297,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       #pragma unroll 1
       for (int b = rg.b0; b < rg.b0 + kEnt; ++b)
         if (rg.used & (1u << b)) mbar_wait(&rg.full[b], ((~rg.fpar) >> b) & 1u);
+    if (threadIdx.x == 0 && S.inject) S.inject[0] = 0;  // the hook fires once
     __syncthreads();
     return false;
   }
@@ -1674,12 +1708,14 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
 
 }  // namespace
 
+// threads: CTA size (a multiple of 32, at least 32); every size computes each
+// entry of A and b the same way, so the choice does not change the result.
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
-                     int mixed, cudaStream_t st) {
+                     int mixed, cudaStream_t st, int threads) {
   if (mixed)
-    k_assemble32<<<dim3(max_blocks, n_active), 128, 0, st>>>(sims, active);
+    k_assemble32<<<dim3(max_blocks, n_active), threads, 0, st>>>(sims, active);
   else
-    k_assemble<<<dim3(max_blocks, n_active), 128, 0, st>>>(sims, active);
+    k_assemble<<<dim3(max_blocks, n_active), threads, 0, st>>>(sims, active);
 }
 
 void launch_sched(const SimDev* sim, cudaStream_t st) { k_sched<<<1, 32, 0, st>>>(sim); }

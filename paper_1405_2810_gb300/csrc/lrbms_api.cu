@@ -95,6 +95,10 @@ struct lrbms_ctx {
   int refactor_period = 3;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t admit_stream = nullptr;  // admission copies and kernels (overlap the steps)
+  int* d_status = nullptr;              // [max_slots] statuses of the last step, in list order
+  int* h_status = nullptr;              // pinned copy
+  int last_n = 0;                       // simulations of the last lrbms_step
   Arena arena;
   std::vector<Slot> slots;
   SimDev* d_sims = nullptr;
@@ -111,6 +115,9 @@ struct lrbms_ctx {
   cudaGraphExec_t graph = nullptr;
   std::vector<long long> graph_key;
   int graph_kernels = 0;
+  // autotuned CTA sizes of assembly and reconstruction per shape class
+  // (basis-size class, cells per subdomain, component precision)
+  std::map<std::vector<int>, std::pair<int, int>> tuned;
 };
 
 namespace {
@@ -176,9 +183,16 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   if (ctx->arena.init(cfg->hbm_budget) != cudaSuccess ||
       cudaMalloc(&ctx->d_sims, sizeof(SimDev) * cfg->max_slots) != cudaSuccess ||
       cudaMalloc(&ctx->d_active, sizeof(int) * cfg->max_slots) != cudaSuccess ||
-      cudaMalloc(&ctx->d_io, sizeof(double*) * 2 * cfg->max_slots) != cudaSuccess) {
+      cudaMalloc(&ctx->d_io, sizeof(double*) * 2 * cfg->max_slots) != cudaSuccess ||
+      cudaMalloc(&ctx->d_status, sizeof(int) * cfg->max_slots) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(int) * cfg->max_slots) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->admit_stream, cudaStreamNonBlocking) != cudaSuccess) {
     ctx->arena.release();
     if (ctx->d_sims) cudaFree(ctx->d_sims);
+    if (ctx->d_active) cudaFree(ctx->d_active);
+    if (ctx->d_io) cudaFree(ctx->d_io);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return LRBMS_E_CUDA;
@@ -196,6 +210,10 @@ int lrbms_destroy(lrbms_ctx* ctx) {
   cudaFree(ctx->d_sims);
   cudaFree(ctx->d_active);
   cudaFree(ctx->d_io);
+  cudaStreamSynchronize(ctx->admit_stream);
+  cudaStreamDestroy(ctx->admit_stream);
+  cudaFree(ctx->d_status);
+  cudaFreeHost(ctx->h_status);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -206,6 +224,10 @@ int lrbms_destroy(lrbms_ctx* ctx) {
 const char* lrbms_last_error(const lrbms_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx) { return ctx->stream; }
+cudaStream_t lrbms_internal_admit_stream(lrbms_ctx* ctx) { return ctx->admit_stream; }
+bool lrbms_internal_in_last_batch(lrbms_ctx* ctx, int id) {
+  return std::find(ctx->last_active.begin(), ctx->last_active.end(), id) != ctx->last_active.end();
+}
 int lrbms_internal_sim(lrbms_ctx* ctx, int id, SimDev* out) {
   if (!valid_sim(ctx, id)) return LRBMS_E_STATE;
   *out = ctx->slots[id].d;
@@ -335,7 +357,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
   const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
   const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
-  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 8), o_fitr = L.add(4);
+  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 8), o_fitr = L.add(4),
+               o_inj = L.add(4);
   const size_t o_sched = L.add(8 * lrbms::sched_words(n_sub, Sx));
   (void)d_tot;
 
@@ -381,10 +404,13 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);
   d.status = (int*)P(o_status); d.steps = (int*)P(o_steps); d.info = (int*)P(o_info);
   d.fit_ready = (int*)P(o_fitr);
+  d.inject = (int*)P(o_inj);
   d.sched = (const unsigned long long*)P(o_sched);
   d.lam = (double*)P(o_lam); d.fw = (double*)P(o_fw); d.inv_pv = (double*)P(o_ipv); d.fcoef = (double*)P(o_fc);
 
-  cudaStream_t st = ctx->stream;
+  // the admission stream: the copies and kernels of a new simulation overlap
+  // the steps that run meanwhile on the context stream
+  cudaStream_t st = ctx->admit_stream;
   auto cp = [&](void* dst, const void* src, size_t bytes) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
   };
@@ -416,6 +442,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_steps), 0, 4, st));
   CK(cudaMemsetAsync(P(o_info), 0, 4 * 8, st));
   CK(cudaMemsetAsync(P(o_fitr), 0, 4, st));
+  CK(cudaMemsetAsync(P(o_inj), 0, 4, st));
   CK(cudaMemsetAsync(P(o_p), 0, 24 * (size_t)n_cells, st));
   CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
   CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
@@ -436,7 +463,6 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   s.off = aoffset;
   s.bytes = L.total;
   s.d = d;
-  ctx->last_active.clear();
   *sim_id = slot;
   return LRBMS_OK;
 }
@@ -481,6 +507,51 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
                                                                      // needed), refine, retry, FP64 redo
   CK(lrbms::prepare_chol_solve(ctx->solver, sh));  // kernel attributes, outside any capture
   CK(lrbms::prepare_flux_cfl(flux_smem));
+  // Autotuner: the first step of a new shape class times every CTA size of
+  // the two streaming contractions on the live data (both kernels are pure
+  // functions of their inputs, which the step then recomputes) and keeps the
+  // fastest; every size gives the same result.
+  int ne_max = 0, cells_max = 0;
+  for (int id : act) {
+    ne_max = std::max(ne_max, ctx->slots[id].d.max_NE);
+    cells_max = std::max(cells_max, ctx->slots[id].d.cx * ctx->slots[id].d.cy);
+  }
+  const std::vector<int> tkey{(ne_max + 7) / 8, cells_max, mixed};
+  auto tit = ctx->tuned.find(tkey);
+  if (tit == ctx->tuned.end() && n_steps > 0) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto best_of = [&](const std::vector<int>& sizes, auto&& launch) -> int {
+      int best = sizes[0];
+      float best_ms = 1e30f;
+      for (int t : sizes) {
+        launch(t);  // warm-up
+        cudaEventRecord(e0, st);
+        launch(t);
+        launch(t);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ctx->launches += 3;
+        if (ms < best_ms) best_ms = ms, best = t;
+      }
+      return best;
+    };
+    const int ta = best_of({64, 128, 256, 512}, [&](int t) {
+      lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st, t);
+    });
+    const int tr = best_of({128, 256, 512, 1024}, [&](int t) {
+      lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st, t);
+    });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    tit = ctx->tuned.emplace(tkey, std::make_pair(ta, tr)).first;
+  }
+  const int t_asm = tit == ctx->tuned.end() ? 128 : tit->second.first;
+  const int t_rec = tit == ctx->tuned.end() ? 256 : tit->second.second;
   // The kernels of one step, in order; ev (optional) gets an event before the
   // first phase and after every phase.
   auto enqueue_step = [&](cudaEvent_t* ev) -> cudaError_t {
@@ -490,19 +561,19 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     mark(0);
     lrbms::launch_fit(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
     mark(1);
-    lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st);
+    lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st, t_asm);
     mark(2);
     cudaError_t e = lrbms::launch_chol_solve(ctx->d_sims, ctx->d_active, n_sims, ctx->solver, ctx->refine_iters,
                                              sh, st);
     if (e != cudaSuccess) return e;
     mark(3);
-    lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st);
+    lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st, t_rec);
     mark(4);
     lrbms::launch_flux_cfl(ctx->d_sims, ctx->d_active, n_sims, max_tiles, flux_smem, st);
     mark(5);
     lrbms::launch_transport(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
     mark(6);
-    lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st);
+    lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st, ctx->d_status);
     mark(7);
     return cudaGetLastError();
   };
@@ -516,7 +587,8 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     // The other steps replay one captured graph of the step's kernels.
     std::vector<long long> key(act.begin(), act.end());
     for (long long v : {(long long)sh.n_sub, (long long)sh.panel_words, (long long)sh.max_w, (long long)sh.N,
-                        (long long)max_tiles, (long long)max_blocks, (long long)max_sub, (long long)flux_smem})
+                        (long long)max_tiles, (long long)max_blocks, (long long)max_sub, (long long)flux_smem,
+                        (long long)t_asm, (long long)t_rec})
       key.push_back(v);
     if (!ctx->graph || key != ctx->graph_key) {
       if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -547,11 +619,28 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     }
   }
   CK(cudaGetLastError());
-  if (status) {
-    CK(cudaStreamSynchronize(st));
-    for (int i = 0; i < n_sims; ++i)
-      CK(cudaMemcpy(&status[i], ctx->slots[act[i]].d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (n_steps == 0) {  // a status query: read the status words themselves
+    if (status) {
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < n_sims; ++i)
+        CK(cudaMemcpy(&status[i], ctx->slots[act[i]].d.status, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    return LRBMS_OK;
   }
+  ctx->last_n = n_sims;
+  if (status) return lrbms_step_status(ctx, n_sims, status);
+  return LRBMS_OK;
+}
+
+int lrbms_step_status(lrbms_ctx* ctx, int n_sims, int* status) {
+  if (!ctx || !status || n_sims < 1 || n_sims > ctx->last_n) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->last_active.empty() || (int)ctx->last_active.size() < n_sims)
+    return fail(ctx, LRBMS_E_STATE, "no step to report");
+  // one copy of the statuses k_finalize gathered in list order
+  CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int) * n_sims, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(status, ctx->h_status, sizeof(int) * n_sims);
   return LRBMS_OK;
 }
 
@@ -586,6 +675,7 @@ int lrbms_step_io(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, const
     ctx->launches += 1;
   }
   CK(cudaGetLastError());
+  if (status && n_steps > 0) return lrbms_step_status(ctx, n_sims, status);
   CK(cudaStreamSynchronize(st));
   if (status)
     for (int i = 0; i < n_sims; ++i)
@@ -697,6 +787,29 @@ int lrbms_get_state(lrbms_ctx* ctx, int id, double* s, double* t, double* mass_o
   CK(cudaMemcpy(sc, d.scal, sizeof(sc), cudaMemcpyDeviceToHost));
   if (t) *t = sc[0];
   if (mass_out) *mass_out = sc[2];
+  return LRBMS_OK;
+}
+
+int lrbms_tuned_threads(lrbms_ctx* ctx, int n_sims, const int* ids, int* assemble, int* reconstruct) {
+  if (!ctx || n_sims < 1 || !ids) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  int ne_max = 0, cells_max = 0;
+  for (int i = 0; i < n_sims; ++i) {
+    if (!valid_sim(ctx, ids[i])) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+    ne_max = std::max(ne_max, ctx->slots[ids[i]].d.max_NE);
+    cells_max = std::max(cells_max, ctx->slots[ids[i]].d.cx * ctx->slots[ids[i]].d.cy);
+  }
+  auto it = ctx->tuned.find(std::vector<int>{(ne_max + 7) / 8, cells_max, ctx->precision == LRBMS_MIXED});
+  if (it == ctx->tuned.end()) return fail(ctx, LRBMS_E_STATE, "this shape class has not been tuned yet");
+  if (assemble) *assemble = it->second.first;
+  if (reconstruct) *reconstruct = it->second.second;
+  return LRBMS_OK;
+}
+
+int lrbms_test_withhold_copy(lrbms_ctx* ctx, int id) {
+  if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int one = 1;
+  CK(cudaMemcpy(ctx->slots[id].d.inject, &one, sizeof(int), cudaMemcpyHostToDevice));
   return LRBMS_OK;
 }
 

@@ -95,6 +95,7 @@ struct SimDev {
   int* status;      // [1]
   int* steps;       // [1]
   int* fit_ready;   // [1] lambda, f_w and the fit sums of the current s are computed
+  int* inject;      // [1] test hook: non-zero withholds one copy of the next substitution (may be null)
   int* info;        // [8] solve bookkeeping (kernels_solve.cu, kInfo*); may be null
 };
 
@@ -114,7 +115,7 @@ void launch_prepare(const SimDev* sim, int n_items, cudaStream_t st);
 void launch_fit(const SimDev* sims, const int* active, int n_active, int max_tiles,
                 cudaStream_t st);
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
-                     int mixed, cudaStream_t st);
+                     int mixed, cudaStream_t st, int threads = 128);
 constexpr int kMaxNE = 32;  // local basis sizes 1..32 (one warp lane per row)
 constexpr size_t kMaxSolveSmem = 220 * 1024;  // leaves room for static shared memory
 // Shape maxima over the simulations of one solve launch.
@@ -165,7 +166,7 @@ void launch_sched(const SimDev* sim, cudaStream_t st);
 // FP64 solve of the fine systems of the offline builder (one-cell blocks).
 cudaError_t launch_fine_solve(const SimDev* sims, const int* active, int n_active, cudaStream_t st);
 void launch_reconstruct(const SimDev* sims, const int* active, int n_active, int max_sub,
-                        int mixed, cudaStream_t st);
+                        int mixed, cudaStream_t st, int threads = 256);
 // Face fluxes and per-tile CFL maxima; smem = flux_cfl_smem of the widest tile.
 void launch_flux_cfl(const SimDev* sims, const int* active, int n_active, int max_tiles, size_t smem,
                      cudaStream_t st);
@@ -176,7 +177,8 @@ inline size_t flux_cfl_smem(int nx, int ny, int tile_rows) {
 }
 void launch_transport(const SimDev* sims, const int* active, int n_active, int max_tiles,
                       cudaStream_t st);
-void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st);
+void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st,
+                     int* status_out = nullptr);
 void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st);
 void launch_sat_io(const SimDev* sims, const int* active, int n_active, const double* const* src,
                    double* const* dst, cudaStream_t st);

@@ -724,6 +724,8 @@ extern "C" cudaStream_t lrbms_internal_stream(lrbms_ctx* ctx);
 extern "C" int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg);
 extern "C" int lrbms_internal_sim(lrbms_ctx* ctx, int id, lrbms::SimDev* out);
 extern "C" lrbms::SimDev* lrbms_internal_dsims(lrbms_ctx* ctx);
+extern "C" cudaStream_t lrbms_internal_admit_stream(lrbms_ctx* ctx);
+extern "C" bool lrbms_internal_in_last_batch(lrbms_ctx* ctx, int id);
 extern "C" void lrbms_internal_count(lrbms_ctx* ctx, long long n);
 
 #define BCK(call)                                                              \
@@ -1106,7 +1108,11 @@ extern "C" int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_
   if (!ctx || !sim_id) return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad arguments");
   SimDev d;
   if (lrbms_internal_sim(ctx, src, &d)) return lrbms_internal_fail(ctx, LRBMS_E_STATE, "unknown simulation id");
-  cudaStream_t st = lrbms_internal_stream(ctx);
+  // The copy runs on the admission stream. A source in the batch of the last
+  // step may still be changing: wait for the context stream first; any other
+  // source is at rest, and the copy overlaps the steps in flight.
+  if (lrbms_internal_in_last_batch(ctx, src)) BCK(cudaStreamSynchronize(lrbms_internal_stream(ctx)));
+  cudaStream_t st = lrbms_internal_admit_stream(ctx);
   BCK(cudaStreamSynchronize(st));
   const int n_sub = d.n_sub, n_cf = d.n_cf, Q = d.M + 1, cells = d.cx * d.cy;
   std::vector<int> NE(n_sub), xoff(n_sub + 1);

@@ -42,7 +42,8 @@ EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offlin
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
             "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count", "lrbms_solve_noalloc",
-            "lrbms_fine_step", "lrbms_last_error"]
+            "lrbms_fine_step", "lrbms_step_status", "lrbms_test_withhold_copy", "lrbms_tuned_threads",
+            "lrbms_last_error"]
 
 
 class LrbmsError(RuntimeError):
@@ -103,6 +104,9 @@ def library() -> C.CDLL:
         lib.lrbms_release.argtypes = [vp, i]
         lib.lrbms_step.argtypes = [vp, i, vp, i, vp]
         lib.lrbms_fine_step.argtypes = [vp, i, vp, i, vp]
+        lib.lrbms_step_status.argtypes = [vp, i, vp]
+        lib.lrbms_test_withhold_copy.argtypes = [vp, i]
+        lib.lrbms_tuned_threads.argtypes = [vp, i, vp, C.POINTER(i), C.POINTER(i)]
         lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
         lib.lrbms_get_state.argtypes = [vp, i, vp, dp, dp]
         lib.lrbms_set_saturation.argtypes = [vp, i, vp]
@@ -259,6 +263,13 @@ def lrbms_fine_step(ctx, sim_ids, n_steps: int = 1):
     return status
 
 
+def lrbms_step_status(ctx, n_sims: int):
+    """Wait for the last lrbms_step(..., wait=False) and return its statuses."""
+    status = np.zeros(n_sims, dtype=np.int32)
+    _check(ctx, library().lrbms_step_status(ctx, n_sims, _ptr(status)))
+    return status
+
+
 N_PHASES = 7
 PHASES = ["fit", "assemble", "solve", "reconstruct", "flux", "transport", "finalize"]
 
@@ -297,6 +308,20 @@ def lrbms_get_state(ctx, sim_id: int, s_out=None):
     t, m = C.c_double(), C.c_double()
     _check(ctx, library().lrbms_get_state(ctx, sim_id, _ptr(s_out), C.byref(t), C.byref(m)))
     return t.value, m.value
+
+
+def lrbms_tuned_threads(ctx, sim_ids):
+    """(assemble, reconstruct) CTA sizes the autotuner chose for these simulations."""
+    ids = np.ascontiguousarray(sim_ids, dtype=np.int32)
+    a, r = C.c_int(), C.c_int()
+    _check(ctx, library().lrbms_tuned_threads(ctx, len(ids), _ptr(ids), C.byref(a), C.byref(r)))
+    return a.value, r.value
+
+
+def lrbms_test_withhold_copy(ctx, sim_id: int):
+    """Test hook: the next reduced solve of sim_id withholds one bulk copy, so
+    its bounded wait runs out and the simulation stops with LRBMS_E_TIMEOUT."""
+    _check(ctx, library().lrbms_test_withhold_copy(ctx, sim_id))
 
 
 def lrbms_set_saturation(ctx, sim_id: int, s):

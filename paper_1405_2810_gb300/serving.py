@@ -85,16 +85,22 @@ class Server:
             self.active.append(r)
 
     def step(self):
-        """One tick: admit, advance every active simulation by one step, retire."""
+        """One tick: enqueue one step of every active simulation, admit the
+        queued requests while it runs on the device (their copies and set-up
+        kernels go to the library's admission stream), then wait for the
+        step's statuses (one copy for the batch) and retire the finished
+        simulations. Requests admitted in a tick join the next one."""
+        ids = [r.sim_id for r in self.active]
+        t0 = time.perf_counter()
+        if ids:
+            self.L.lrbms_step(self.ctx, ids, 1, wait=False)
         self._admit()
-        if self.active:
-            ids = [r.sim_id for r in self.active]
-            t0 = time.perf_counter()
-            st = self.L.lrbms_step(self.ctx, ids, 1)
+        if ids:
+            st = self.L.lrbms_step_status(self.ctx, len(ids))
             self.tick_ms.append(1e3 * (time.perf_counter() - t0))
             self.tick_n.append(len(ids))
             still = []
-            for r, code in zip(self.active, st):
+            for r, code in zip(self.active[:len(ids)], st):
                 r.steps_done += 1
                 if code != 0 or r.steps_done >= r.n_steps:
                     r.result = self._read(r, int(code))
@@ -105,7 +111,7 @@ class Server:
                     self.done.append(r)
                 else:
                     still.append(r)
-            self.active = still
+            self.active = still + self.active[len(ids):]  # admitted during this tick
         self.tick += 1
 
     def _read(self, r: Request, code: int) -> dict:

@@ -316,3 +316,46 @@ def test_fitted_velocity_variant(L, dense):
         _compare_step(L, ctx, sid, c, s, ref=ref)
         s = ref["s"]
     L.lrbms_destroy(ctx)
+
+
+@pytest.mark.parametrize("solver", SOLVERS, ids=["fp64-solve", "mixed-solve"])
+def test_bounded_wait_timeout_is_isolated(L, solver):
+    """Failure detection without a GPU fault: one simulation's solve withholds
+    a bulk copy (test hook), its bounded wait runs out after about 2 s, and it
+    stops with LRBMS_E_TIMEOUT; the other simulations of the same launches
+    give bitwise the results of a clean run, and the context stays usable."""
+    c = case("small", kind="snapshots")
+    ctx = _ctx(L, solver=solver)
+    ids = [_load(L, ctx, c) for _ in range(3)]
+    assert list(L.lrbms_step(ctx, ids, 2)) == [0, 0, 0]
+    L.lrbms_test_withhold_copy(ctx, ids[1])
+    st = L.lrbms_step(ctx, ids, 3)
+    assert list(st) == [0, L.LRBMS_E_TIMEOUT, 0]
+    got = [L.lrbms_get_field(ctx, i, L.FIELD_S) for i in (ids[0], ids[2])]
+    L.lrbms_destroy(ctx)
+    ctx = _ctx(L, solver=solver)
+    ref = _load(L, ctx, c)
+    assert L.lrbms_step(ctx, [ref], 5)[0] == 0
+    want = L.lrbms_get_field(ctx, ref, L.FIELD_S)
+    L.lrbms_destroy(ctx)
+    assert np.array_equal(got[0], want) and np.array_equal(got[1], want)
+
+
+def test_autotuned_sizes_do_not_change_results(L):
+    """The autotuner's choice of CTA sizes for assembly and reconstruction is
+    recorded per shape class, and a context forced through every candidate
+    size (by stepping simulations of several classes) still matches the
+    oracle; a second context gives bitwise the same saturation."""
+    c = case("small", kind="snapshots")
+    out = []
+    for _ in range(2):
+        ctx = _ctx(L, solver=1)
+        sid = _load(L, ctx, c)
+        with pytest.raises(L.LrbmsError):
+            L.lrbms_tuned_threads(ctx, [sid])
+        assert L.lrbms_step(ctx, [sid], 3)[0] == 0
+        ta, tr = L.lrbms_tuned_threads(ctx, [sid])
+        assert ta in (64, 128, 256, 512) and tr in (128, 256, 512, 1024)
+        out.append(L.lrbms_get_field(ctx, sid, L.FIELD_S))
+        L.lrbms_destroy(ctx)
+    assert np.array_equal(out[0], out[1])

@@ -28,11 +28,15 @@ class FakeLib:
         self.live[sid] = {"steps": 0, "nx": problem["nx"], "ny": problem["ny"]}
         return sid
 
-    def lrbms_step(self, ctx, ids, n):
+    def lrbms_step(self, ctx, ids, n, wait=True):
         self.calls.append(list(ids))
         for i in ids:
             self.live[i]["steps"] += n
-        return np.zeros(len(ids), dtype=np.int32)
+        self.pending = np.zeros(len(ids), dtype=np.int32)
+        return self.pending if wait else None
+
+    def lrbms_step_status(self, ctx, n):
+        return self.pending[:n]
 
     def lrbms_get_state(self, ctx, sid, s):
         s[:] = self.live[sid]["steps"]
