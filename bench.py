@@ -372,7 +372,7 @@ def main():
         run_reference(a, rank, world)
         return
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.kernels_only:
         cpu = start_cpu_baseline(a)  # spawned before the first GPU call
 
     import numpy as np

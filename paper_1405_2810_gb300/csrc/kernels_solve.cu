@@ -145,11 +145,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// Hint: bring [src, src + bytes) into L2 (no destination, no completion to
-// wait for); src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -1098,13 +1093,9 @@ __device__ __forceinline__ SFeed sfeed_open(const unsigned long long* sched, int
   return f;
 }
 
-// Issue the warp's next chunks while they fit; with each issued chunk, the
-// chunk kL2Ahead places further on is prefetched into L2, so that its bulk
-// copy later reads L2 instead of HBM.
-constexpr int kL2Ahead = 16;
+// Issue the warp's next chunks while they fit.
 template <typename T>
 __device__ __forceinline__ void srefill(WRing<T>& r, SFeed& f, const T* LT, const T* Linv, int lane) {
-  constexpr int kA = 16 / (int)sizeof(T);
   #pragma unroll 1
   while (f.next < f.n) {
     if (f.next - f.base == 32) {
@@ -1118,17 +1109,6 @@ __device__ __forceinline__ void srefill(WRing<T>& r, SFeed& f, const T* LT, cons
     if (!wring_try_issue<T>(r, src, (long long)(dsc & kDescOffMask), (int)((dsc >> 40) & 0x7ff), lane,
                             f.next == f.withhold))
       return;
-    const int ja = f.next + kL2Ahead;  // within the 64 descriptors held in cur and nxt
-    if (ja < f.n) {
-      const int rel = ja - f.base;
-      const unsigned long long da = __shfl_sync(0xffffffffu, rel < 32 ? f.cur : f.nxt, rel & 31);
-      if (lane == 0) {
-        const long long off = (long long)(da & kDescOffMask);
-        const int d = (int)(off & (kA - 1));
-        const uint32_t bytes = (uint32_t)((d + (int)((da >> 40) & 0x7ff)) * (int)sizeof(T) + 15) & ~15u;
-        prefetch_l2(((da & kDescInverse) ? Linv : LT) + (off - d), bytes);
-      }
-    }
     ++f.next;
   }
 }
