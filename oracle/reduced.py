@@ -60,3 +60,29 @@ def online_run(model: FineModel, off: Offline, s0: np.ndarray, n_steps: int):
         s = r["s"]
         hist.append(r)
     return s, hist
+
+
+def online_step_dg(model: FineModel, off: Offline, c: np.ndarray, Phi_g=None) -> dict:
+    """The online step with the piecewise-linear DG saturation and its limiter
+    (Definition 3 with k = 1, Section 3.4): the fit, the reduced system and the
+    fluxes take the mobility at the cell means c[:, 0]; the transport is
+    oracle.transport_dg."""
+    from .transport_dg import dg_step, dg_time_step, limit
+    if Phi_g is None:
+        Phi_g = off.extra["Phi_g"]
+    s_mean = c[:, 0]
+    lam = total_mobility(s_mean, model.eta_w, model.eta_o, model.law)
+    r = off.P @ lam
+    theta = off.Gp @ r
+    A, rhs = assemble(off, theta)
+    x = sla.cho_solve(sla.cho_factor(A), rhs)
+    p = Phi_g @ x
+    F = model.fluxes(p, lam)
+    if model.dt_fixed is not None:
+        dt = float(model.dt_fixed)
+    else:
+        dt = dg_time_step(model.grid, F, model.poro, model.Lf, model.cfl, model.dt_max)
+    c_new, bout = dg_step(model.grid, c, F, model.poro, dt, model.s_D, model.eta_w, model.eta_o, model.law)
+    c_lim, flagged = limit(model.grid, c_new, F, model.s_D)
+    return dict(theta=theta, A=A, rhs=rhs, x=x, p=p, F=F, dt=dt, c_unlimited=c_new, c=c_lim,
+                flagged=flagged, boundary_outflow=bout)
