@@ -80,6 +80,7 @@ enum { LRBMS_SOLVE_FP64 = 0, LRBMS_SOLVE_MIXED = 1 };
 enum { LRBMS_COREY = 0, LRBMS_LINEAR = 1 };
 enum { LRBMS_DT_CFL = 0, LRBMS_DT_FIXED = 1 };
 enum { LRBMS_VELOCITY_STATE = 0, LRBMS_VELOCITY_FITTED = 1 };
+enum { LRBMS_TRANSPORT_FV = 0, LRBMS_TRANSPORT_DG1 = 1 };
 
 typedef struct {
   int precision;     /* LRBMS_FP64: every phase in FP64. LRBMS_MIXED: basis
@@ -145,6 +146,17 @@ typedef struct {
                             and Algorithm 3 step 5 state; LRBMS_VELOCITY_FITTED
                             the fitted mobility sum_q theta_q Lambda^q that
                             the reduced pressure system uses (Section 4.4) */
+  int transport;         /* saturation scheme (Definition 3): LRBMS_TRANSPORT_FV
+                            piecewise constant (finite-volume upwind);
+                            LRBMS_TRANSPORT_DG1 piecewise linear (P1 DG,
+                            explicit Euler, Raviart-Thomas velocity of the
+                            face fluxes, 3x3 Gauss points in a cell and 3 on
+                            a face, CFL step divided by 3) followed by the
+                            slope limiter of Section 3.4 (Eq. limiterMain).
+                            The saturation penalty term is dropped in both;
+                            the fit, the reduced system and the fluxes take
+                            the mobility at the cell means. s0 is a cell mean
+                            (slopes start at zero)                          */
 } lrbms_problem;
 
 /* Offline data of the offline/online decomposition (Section 4.4) for M
@@ -216,8 +228,12 @@ int lrbms_run(lrbms_ctx* ctx, int sim_id, int n_steps, double* s_out,
  * water volume that left through the boundary (NULL skipped). */
 int lrbms_get_state(lrbms_ctx* ctx, int sim_id, double* s, double* t,
                     double* mass_out);
-/* Overwrite a simulation's saturation (host or device pointer). */
+/* Overwrite a simulation's saturation (host or device pointer): the cell
+ * values (finite volume) or cell means (P1 DG, whose slopes are reset to 0). */
 int lrbms_set_saturation(lrbms_ctx* ctx, int sim_id, const double* s);
+/* Overwrite the slopes [2][n_cells] (c1 then c2, see LRBMS_FIELD_SLOPES) of a
+ * simulation with the P1-DG transport; LRBMS_E_ARG for the finite-volume one. */
+int lrbms_set_slopes(lrbms_ctx* ctx, int sim_id, const double* slopes);
 
 /* Intermediate fields of the last step, for inspection and parity tests. */
 enum {
@@ -231,6 +247,9 @@ enum {
   LRBMS_FIELD_S = 6,     /* [n_cells] saturation                                */
   LRBMS_FIELD_DT = 7,    /* [1] last time step                                  */
   LRBMS_FIELD_STATUS = 8,/* [1] int status word                                 */
+  LRBMS_FIELD_SLOPES = 10, /* [2][n_cells] slopes c1, c2 of the piecewise-linear
+                            saturation s = c0 + c1 psi1 + c2 psi2 (c0 is
+                            LRBMS_FIELD_S); zeros for LRBMS_TRANSPORT_FV      */
   LRBMS_FIELD_SOLVE_INFO = 9 /* [6] int: correction passes of the last reduced
                             solve; then, counted since load: reduced solves
                             redone in FP64 after the FP32 factorisation or

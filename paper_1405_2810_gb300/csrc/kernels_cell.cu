@@ -439,12 +439,14 @@ __device__ __forceinline__ void cell_faces(const SimDev& S, int e, int& fl, int&
   ft = fb + nx;
 }
 
-// Reading R12: dt = cfl min_e phi_e|e| / (L_f outflow_e) = cfl / (L_f max_e outflow_e / (phi_e|e|)).
+// Reading R12: dt = cfl min_e phi_e|e| / (L_f outflow_e) = cfl / (L_f max_e outflow_e / (phi_e|e|)),
+// divided by 2k + 1 = 3 for the piecewise-linear DG transport.
 __device__ __forceinline__ double step_dt(const SimDev& S) {
   if (S.dt_mode == 1) return S.dt_fixed;
   double m = 0.0;
   for (int t = 0; t < S.n_tiles; ++t) m = fmax(m, S.cfl_part[t]);
   double dt = (m > 0.0) ? S.cfl / (S.Lf * m) : DBL_MAX;
+  if (S.transport == 1 && dt < DBL_MAX) dt /= 3.0;
   if (S.dt_max > 0.0) dt = fmin(dt, S.dt_max);
   return dt;
 }
@@ -470,13 +472,13 @@ __device__ __forceinline__ bool fixed_step_breaks_cfl(const SimDev& S) {
   if (S.dt_mode != 1 || !(S.Lf > 0.0)) return false;
   double m = 0.0;
   for (int t = 0; t < S.n_tiles; ++t) m = fmax(m, S.cfl_part[t]);
-  return S.dt_fixed * S.Lf * m > 1.0;
+  return S.dt_fixed * S.Lf * m * (S.transport == 1 ? 3.0 : 1.0) > 1.0;
 }
 
 __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restrict__ active) {
   const SimDev& S = sims[active[blockIdx.y]];
   const int tile = blockIdx.x;
-  if (tile >= S.n_tiles || S.status[0] != kStOk) return;
+  if (tile >= S.n_tiles || S.status[0] != kStOk || S.transport != 0) return;
   __shared__ double dt_sh;
   __shared__ int cfl_bad;
   if (threadIdx.x == 0) {
@@ -547,6 +549,204 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
     if (anybad) S.status[0] = kStNonFinite;
   }
   fit_store(S, acc, tile);
+}
+
+
+// ------------------------------------------------------------------ P1-DG transport
+// Definition 3 with k = 1 (Eq. saturationDG, explicit Euler, gravity and
+// sources zero, the saturation penalty dropped as for k = 0): per cell the
+// mean c0 (in s) and the slopes c1, c2 of s_h = c0 + c1 psi1 + c2 psi2 in the
+// pressure's local basis (in sslope); the velocity is the lowest-order
+// Raviart-Thomas field of the face fluxes, u_x = (F_l (1 - r) + F_r (1 + r)) /
+// (2 hy), u_y = (F_b (1 - t) + F_t (1 + t)) / (2 hx) in the cell's reference
+// coordinates r, t; 3 x 3 Gauss points in the cell and 3 on each face. Both
+// cells of a face evaluate its upwind values from the same operands, so the
+// face terms of the means cancel exactly in the total water volume.
+__constant__ double kGX[3] = {-0.7745966692414834, 0.0, 0.7745966692414834};  // Gauss-Legendre nodes sqrt(3/5)
+__constant__ double kGW[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+
+// s_h at tangential coordinate q on side 0 (left), 1 (right), 2 (bottom), 3 (top)
+__device__ __forceinline__ double dg_trace(double c0, double c1, double c2, int side, double q) {
+  switch (side) {
+    case 0: return c0 - c1 + c2 * q;
+    case 1: return c0 + c1 + c2 * q;
+    case 2: return c0 + c1 * q - c2;
+    default: return c0 + c1 * q + c2;
+  }
+}
+
+__device__ __forceinline__ size_t slope_half(const SimDev& S, int parity) {
+  return (size_t)(parity & 1) * 2 * S.n_cells;
+}
+
+__global__ void k_transport_dg(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk || S.transport != 1) return;
+  __shared__ double dt_sh;
+  __shared__ int cfl_bad;
+  if (threadIdx.x == 0) {
+    dt_sh = step_dt(S);
+    cfl_bad = fixed_step_breaks_cfl(S);
+    if (cfl_bad && tile == 0) S.status[0] = kStCfl;
+  }
+  __syncthreads();
+  if (cfl_bad) return;
+  const double dt = dt_sh;
+  const int n = S.n_cells, nx = S.nx, ny = S.ny;
+  const double* s = cur_s(S);
+  double* sn = next_s(S);
+  const double* sl = S.sslope + slope_half(S, S.steps[0]);
+  double* unl = S.sunl;  // [2][n] unlimited slopes of s^{n+1}
+  double* lam_n = S.lam + next_half(S);
+  double* fw_n = S.fw + next_half(S);
+  const double hx = S.hx, hy = S.hy, vol = S.vol;
+  int e0, e1;
+  tile_range(S, tile, e0, e1);
+  double bout = 0.0;
+  bool bad = !(dt > 0.0 && dt < DBL_MAX);
+  double acc[kMaxM];
+#pragma unroll
+  for (int q = 0; q < kMaxM; ++q) acc[q] = 0.0;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int j = e / nx, i = e - j * nx;
+    const double c0 = s[e], c1 = sl[e], c2 = sl[n + e];
+    int fl, fr, fb, ft;
+    cell_faces(S, e, fl, fr, fb, ft);
+    const double Fs[4] = {S.F[fl], S.F[fr], S.F[fb], S.F[ft]};
+    double R0 = 0.0, R1 = 0.0, R2 = 0.0;
+    // volume term: f(s) u . grad psi_j with grad psi1 = (2/hx, 0), grad psi2 = (0, 2/hy)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double ux = (Fs[0] * (1.0 - kGX[a]) + Fs[1] * (1.0 + kGX[a])) / (2.0 * hy);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double uy = (Fs[2] * (1.0 - kGX[b]) + Fs[3] * (1.0 + kGX[b])) / (2.0 * hx);
+        const double w = kGW[a] * kGW[b] * vol / 4.0;
+        const double f = frac_flow(S, c0 + c1 * kGX[a] + c2 * kGX[b]);
+        R1 += w * f * ux * (2.0 / hx);
+        R2 += w * f * uy * (2.0 / hy);
+      }
+    }
+    // face terms: -int_f (u . n_out) f(s_up) psi_j ds
+#pragma unroll
+    for (int side = 0; side < 4; ++side) {
+      const double sgn = (side & 1) ? 1.0 : -1.0;
+      const double Fout = sgn * Fs[side];
+      int nb = -1, bidx = -1;
+      if (side == 0) { if (i > 0) nb = e - 1; else bidx = j; }
+      if (side == 1) { if (i < nx - 1) nb = e + 1; else bidx = ny + j; }
+      if (side == 2) { if (j > 0) nb = e - nx; else bidx = 2 * ny + i; }
+      if (side == 3) { if (j < ny - 1) nb = e + nx; else bidx = 2 * ny + nx + i; }
+      const bool own_up = sgn > 0.0 ? (Fout >= 0.0) : (Fout > 0.0);
+      double gsum = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double own = dg_trace(c0, c1, c2, side, kGX[q]);
+        double up;
+        if (nb >= 0) {
+          up = own_up ? own : dg_trace(s[nb], sl[nb], sl[n + nb], side ^ 1, kGX[q]);
+        } else {
+          up = (Fout >= 0.0) ? own : S.s_D[bidx];
+        }
+        const double g = kGW[q] * frac_flow(S, up);
+        const double p1 = side < 2 ? sgn : kGX[q];
+        const double p2 = side < 2 ? kGX[q] : sgn;
+        R0 -= Fout * 0.5 * g;
+        R1 -= Fout * 0.5 * g * p1;
+        R2 -= Fout * 0.5 * g * p2;
+        gsum += g;
+      }
+      if (nb < 0) bout += Fout * 0.5 * gsum;
+    }
+    const double pv = S.poro[e] * vol;
+    const double c0n = c0 + dt * R0 / pv;
+    const double c1n = c1 + dt * R1 / (pv / 3.0);
+    const double c2n = c2 + dt * R2 / (pv / 3.0);
+    if (!isfinite(c0n) || !isfinite(c1n) || !isfinite(c2n)) bad = true;
+    sn[e] = c0n;
+    unl[e] = c1n;
+    unl[n + e] = c2n;
+    fit_cell(S, c0n, e, lam_n, fw_n, acc);  // the next step's fit, at the cell means
+  }
+  __shared__ double red[32];
+  const double tot = block_sum(bout, red);
+  const int anybad = __syncthreads_or(bad ? 1 : 0);
+  if (threadIdx.x == 0) {
+    S.mass_part[tile] = tot;
+    if (anybad) S.status[0] = kStNonFinite;
+  }
+  fit_store(S, acc, tile);
+}
+
+// m_i of the limiter (Section 3.4) from g_i and d_i, the three cases as printed.
+__device__ __forceinline__ double gradient_scale(double g, double d) {
+  if (g * d < 0.0 && fabs(g) > 1e-8 && fabs(d) > 1e-8) return 0.0;
+  if (g * d > 0.0 && fabs(g) > fabs(d) && fabs(g) > 1e-8 && fabs(d) > 1e-8) return d / g;
+  return 1.0;
+}
+
+// The limiter of Section 3.4 (Eq. limiterMain) on s^{n+1}: shock detector on
+// the upstream faces (|int_f [s] ds| / (0.08 d sqrt(h_e) |e|), d = 2, h_e =
+// diam(e), s_D on an inflow boundary face), flagged if > 1 or if s_h leaves
+// [0, 1] at a vertex; a flagged cell keeps its mean and scales its slopes by
+// min_i m_i over its face neighbours. Reads the unlimited slopes of every
+// cell (sunl) and writes the limited ones, so cells never see a limited
+// neighbour.
+__global__ void k_limit_dg(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.y]];
+  const int tile = blockIdx.x;
+  if (tile >= S.n_tiles || S.status[0] != kStOk || S.transport != 1) return;
+  const int n = S.n_cells, nx = S.nx, ny = S.ny;
+  const double* sn = next_s(S);
+  const double* unl = S.sunl;
+  double* sl_n = S.sslope + slope_half(S, S.steps[0] + 1);
+  const double scale = 1.0 / (0.08 * 2.0 * sqrt(sqrt(S.hx * S.hx + S.hy * S.hy)) * S.vol);
+  int e0, e1;
+  tile_range(S, tile, e0, e1);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int j = e / nx, i = e - j * nx;
+    const double c0 = sn[e], c1 = unl[e], c2 = unl[n + e];
+    int fl, fr, fb, ft;
+    cell_faces(S, e, fl, fr, fb, ft);
+    const double Fs[4] = {S.F[fl], S.F[fr], S.F[fb], S.F[ft]};
+    int nbs[4];
+    double eta = 0.0;
+#pragma unroll
+    for (int side = 0; side < 4; ++side) {
+      const double sgn = (side & 1) ? 1.0 : -1.0;
+      int nb = -1, bidx = -1;
+      if (side == 0) { if (i > 0) nb = e - 1; else bidx = j; }
+      if (side == 1) { if (i < nx - 1) nb = e + 1; else bidx = ny + j; }
+      if (side == 2) { if (j > 0) nb = e - nx; else bidx = 2 * ny + i; }
+      if (side == 3) { if (j < ny - 1) nb = e + nx; else bidx = 2 * ny + nx + i; }
+      nbs[side] = nb;
+      if (sgn * Fs[side] < 0.0) {  // upstream face
+        const double own = dg_trace(c0, c1, c2, side, 0.0);
+        const double other = nb >= 0 ? dg_trace(sn[nb], unl[nb], unl[n + nb], side ^ 1, 0.0) : S.s_D[bidx];
+        eta += fabs((side < 2 ? S.hy : S.hx) * (own - other));
+      }
+    }
+    eta *= scale;
+    bool flag = eta > 1.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double sv = c0 + ((v & 1) ? c1 : -c1) + ((v & 2) ? c2 : -c2);
+      flag |= sv < 0.0 || sv > 1.0;
+    }
+    double alpha = 1.0;
+    if (flag) {
+#pragma unroll
+      for (int side = 0; side < 4; ++side) {
+        const int nb = nbs[side];
+        if (nb < 0) continue;
+        const double g = ((side & 1) ? 2.0 : -2.0) * (side < 2 ? c1 : c2);
+        alpha = fmin(alpha, gradient_scale(g, sn[nb] - c0));
+      }
+    }
+    sl_n[e] = flag ? alpha * c1 : c1;
+    sl_n[n + e] = flag ? alpha * c2 : c2;
+  }
 }
 
 // ------------------------------------------------------------------ finalize
@@ -642,6 +842,11 @@ cudaError_t prepare_flux_cfl(size_t smem) {
 void launch_transport(const SimDev* sims, const int* active, int n_active, int max_tiles,
                       cudaStream_t st) {
   k_transport<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
+}
+void launch_transport_dg(const SimDev* sims, const int* active, int n_active, int max_tiles,
+                         cudaStream_t st) {
+  k_transport_dg<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
+  k_limit_dg<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active);
 }
 void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st, int* status_out) {
   k_finalize<<<(n_active + 127) / 128, 128, 0, st>>>(sims, active, n_active, status_out);

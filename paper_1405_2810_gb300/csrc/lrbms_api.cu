@@ -270,6 +270,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
     return fail(ctx, LRBMS_E_ARG, "exactly one of prof_idx and prof must be given");
   if (pr->dt_mode == LRBMS_DT_CFL && !(pr->cfl > 0 && off->Lf > 0))
     return fail(ctx, LRBMS_E_ARG, "CFL step needs cfl > 0 and Lf > 0");
+  if (pr->transport != LRBMS_TRANSPORT_FV && pr->transport != LRBMS_TRANSPORT_DG1)
+    return fail(ctx, LRBMS_E_ARG, "transport must be LRBMS_TRANSPORT_FV or LRBMS_TRANSPORT_DG1");
   if (pr->velocity != LRBMS_VELOCITY_STATE && pr->velocity != LRBMS_VELOCITY_FITTED)
     return fail(ctx, LRBMS_E_ARG, "velocity must be LRBMS_VELOCITY_STATE or LRBMS_VELOCITY_FITTED");
   if (pr->dt_mode == LRBMS_DT_FIXED && !(pr->dt_fixed > 0))
@@ -346,6 +348,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_phi32 = mixed ? L.add(4 * (size_t)phi_tot) : 0;
   const size_t o_comp32 = mixed ? L.add(4 * Q * (size_t)a_tot) : 0;
   const size_t o_s = L.add(16 * (size_t)n_cells), o_p = L.add(24 * (size_t)n_cells);
+  const bool dg = pr->transport == LRBMS_TRANSPORT_DG1;
+  const size_t o_slope = dg ? L.add(32 * (size_t)n_cells) : 0, o_unl = dg ? L.add(16 * (size_t)n_cells) : 0;
   const size_t o_F = L.add(8 * (size_t)n_faces);
   const size_t o_lam = L.add(16 * (size_t)n_cells), o_fw = L.add(16 * (size_t)n_cells),
                o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces);
@@ -375,6 +379,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.max_w = max_w;
   d.relperm = pr->relperm; d.swapped = pr->mean_weights; d.prof_mode = off->prof_idx ? 0 : 1;
   d.vel_mode = pr->velocity;
+  d.transport = pr->transport;
   d.dt_mode = pr->dt_mode;
   d.hx = pr->Lx / nx; d.hy = pr->Ly / ny; d.vol = d.hx * d.hy; d.c_pen = off->c_pen; d.Lf = off->Lf;
   d.inv_eta_w = 1.0 / pr->eta_w; d.inv_eta_o = 1.0 / pr->eta_o; d.cfl = pr->cfl;
@@ -396,6 +401,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.Phi32 = mixed ? (const float*)P(o_phi32) : nullptr;
   d.comp32 = mixed ? (const float*)P(o_comp32) : nullptr;
   d.s = (double*)P(o_s); d.p = (double*)P(o_p); d.F = (double*)P(o_F);
+  d.sslope = dg ? (double*)P(o_slope) : nullptr;
+  d.sunl = dg ? (double*)P(o_unl) : nullptr;
   d.x = (double*)P(o_x); d.xp = (double*)P(o_xp); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
   d.refactor_period = ctx->refactor_period;
   d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv);
@@ -443,6 +450,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_info), 0, 4 * 8, st));
   CK(cudaMemsetAsync(P(o_fitr), 0, 4, st));
   CK(cudaMemsetAsync(P(o_inj), 0, 4, st));
+  if (dg) CK(cudaMemsetAsync(P(o_slope), 0, 32 * (size_t)n_cells, st));  // s0 piecewise constant
   CK(cudaMemsetAsync(P(o_p), 0, 24 * (size_t)n_cells, st));
   CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
   CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
@@ -483,6 +491,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
   CK(cudaSetDevice(ctx->device));
   std::vector<int> act(ids, ids + n_sims);
   int max_tiles = 0, max_blocks = 0, max_sub = 0;
+  bool any_dg = false;
   size_t flux_smem = 0;
   lrbms::SolveShape sh{0, 0, 0, 0};
   for (int id : act) {
@@ -496,6 +505,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     max_blocks = std::max(max_blocks, d.n_blocks + d.n_sub);
     max_sub = std::max(max_sub, d.n_sub);
     flux_smem = std::max(flux_smem, lrbms::flux_cfl_smem(d.nx, d.ny, d.tile_rows));
+    any_dg |= d.transport == LRBMS_TRANSPORT_DG1;
   }
   cudaStream_t st = ctx->stream;
   if (act != ctx->last_active) {
@@ -503,8 +513,8 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     ctx->last_active = act;
   }
   const int mixed = ctx->precision == LRBMS_MIXED;
-  const int per_step = 6 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1);  // mixed solve: factor (where
-                                                                     // needed), refine, retry, FP64 redo
+  const int per_step = 6 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1)  // mixed solve: factor (where
+                       + (any_dg ? 2 : 0);                             // needed), refine, retry, FP64 redo
   CK(lrbms::prepare_chol_solve(ctx->solver, sh));  // kernel attributes, outside any capture
   CK(lrbms::prepare_flux_cfl(flux_smem));
   // Autotuner: the first step of a new shape class times every CTA size of
@@ -572,6 +582,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     lrbms::launch_flux_cfl(ctx->d_sims, ctx->d_active, n_sims, max_tiles, flux_smem, st);
     mark(5);
     lrbms::launch_transport(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
+    if (any_dg) lrbms::launch_transport_dg(ctx->d_sims, ctx->d_active, n_sims, max_tiles, st);
     mark(6);
     lrbms::launch_finalize(ctx->d_sims, ctx->d_active, n_sims, st, ctx->d_status);
     mark(7);
@@ -588,7 +599,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     std::vector<long long> key(act.begin(), act.end());
     for (long long v : {(long long)sh.n_sub, (long long)sh.panel_words, (long long)sh.max_w, (long long)sh.N,
                         (long long)max_tiles, (long long)max_blocks, (long long)max_sub, (long long)flux_smem,
-                        (long long)t_asm, (long long)t_rec})
+                        (long long)t_asm, (long long)t_rec, (long long)any_dg})
       key.push_back(v);
     if (!ctx->graph || key != ctx->graph_key) {
       if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -743,6 +754,7 @@ size_t lrbms_field_bytes(lrbms_ctx* ctx, int id, int field) {
     case LRBMS_FIELD_DT: return 8;
     case LRBMS_FIELD_STATUS: return 4;
     case LRBMS_FIELD_SOLVE_INFO: return 24;
+    case LRBMS_FIELD_SLOPES: return 16 * (size_t)d.n_cells;
     default: return 0;
   }
 }
@@ -769,6 +781,15 @@ int lrbms_get_field(lrbms_ctx* ctx, int id, int field, void* dst, size_t bytes) 
     case LRBMS_FIELD_DT: src = d.scal + 1; break;
     case LRBMS_FIELD_STATUS: src = d.status; break;
     case LRBMS_FIELD_SOLVE_INFO: src = d.info; break;
+    case LRBMS_FIELD_SLOPES:
+      if (!d.sslope) {  // piecewise-constant transport: no slopes (dst may be host memory)
+        const std::vector<double> zeros(bytes / sizeof(double), 0.0);
+        CK(cudaMemcpy(dst, zeros.data(), bytes, cudaMemcpyDefault));
+        return LRBMS_OK;
+      }
+      CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
+      src = d.sslope + (size_t)(steps & 1) * 2 * d.n_cells;
+      break;
     default: return fail(ctx, LRBMS_E_ARG, "unknown field");
   }
   CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDefault));
@@ -821,6 +842,19 @@ int lrbms_set_saturation(lrbms_ctx* ctx, int id, const double* s) {
   CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(d.s + (size_t)(steps & 1) * d.n_cells, s, 8 * (size_t)d.n_cells, cudaMemcpyDefault));
   CK(cudaMemset(d.fit_ready, 0, 4));  // the next step fits the new saturation
+  if (d.sslope) CK(cudaMemset(d.sslope + (size_t)(steps & 1) * 2 * d.n_cells, 0, 16 * (size_t)d.n_cells));
+  return LRBMS_OK;
+}
+
+int lrbms_set_slopes(lrbms_ctx* ctx, int id, const double* slopes) {
+  if (!valid_sim(ctx, id) || !slopes) return fail(ctx, LRBMS_E_ARG, "bad arguments");
+  const SimDev& d = ctx->slots[id].d;
+  if (!d.sslope) return fail(ctx, LRBMS_E_ARG, "the simulation uses the piecewise-constant transport");
+  CK(cudaStreamSynchronize(ctx->stream));
+  int steps = 0;
+  CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(d.sslope + (size_t)(steps & 1) * 2 * d.n_cells, slopes, 16 * (size_t)d.n_cells,
+                cudaMemcpyDefault));
   return LRBMS_OK;
 }
 

@@ -35,6 +35,7 @@ struct SimDev {
   int relperm, swapped, prof_mode, dt_mode;
   int refactor_period;  // steps one FP32 factor serves (mixed solver)
   int vel_mode;         // mobility of the velocity: 0 lambda(s^n), 1 fitted (needs theta of the step)
+  int transport;        // 0: P0 finite volume upwind; 1: P1 DG with the slope limiter
   double hx, hy, vol, c_pen, Lf, inv_eta_w, inv_eta_o, cfl, dt_fixed, dt_max;
   double lam0, lam1;  // lambda(0), lambda(1)
 
@@ -74,7 +75,9 @@ struct SimDev {
   double* fcoef;    // [3][n_faces] per-face coefficients of the flux (k_prepare)
 
   // state and work arrays
-  double* s;        // [2][n_cells] ping-pong; current = steps & 1
+  double* s;        // [2][n_cells] ping-pong; current = steps & 1 (cell means)
+  double* sslope;   // [2][2][n_cells] P1-DG slopes c1, c2 per half (transport 1; else null)
+  double* sunl;     // [2][n_cells] unlimited slopes of the next step (transport 1; else null)
   double* p;        // [3][n_cells]
   double* F;        // [n_faces]
   double* x;        // [N]
@@ -177,6 +180,9 @@ inline size_t flux_cfl_smem(int nx, int ny, int tile_rows) {
 }
 void launch_transport(const SimDev* sims, const int* active, int n_active, int max_tiles,
                       cudaStream_t st);
+// P1-DG transport and the slope limiter (simulations with transport 1 only).
+void launch_transport_dg(const SimDev* sims, const int* active, int n_active, int max_tiles,
+                         cudaStream_t st);
 void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st,
                      int* status_out = nullptr);
 void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st);

@@ -1171,6 +1171,7 @@ extern "C" int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_
   pr.s0 = s0; pr.cfl = d.cfl; pr.dt_mode = d.dt_mode; pr.dt_fixed = d.dt_fixed; pr.dt_max = d.dt_max;
   pr.mean_weights = d.swapped;
   pr.velocity = d.vel_mode;
+  pr.transport = d.transport;
   lrbms_offline off{};
   off.M = d.M; off.N_E = d.NE; off.prof_idx = d.prof_idx; off.prof = d.prof; off.Gpinv = d.Gpinv;
   off.Phi = uPhi; off.Dblk = ucomp; off.Fblk = n_cf ? ucomp + (size_t)Q * aoff[n_sub] : nullptr;
@@ -1204,9 +1205,11 @@ extern "C" int lrbms_fine_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n
     return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the fine systems");
   std::vector<FineDev> fd(n_sims);
   int max_tiles = 0;
+  bool any_dg = false;
   size_t flux_smem = 0;
   for (int i = 0; i < n_sims; ++i) {
     const SimDev& d = sd[i];
+    any_dg |= d.transport == 1;
     FineDev& f = fd[i];
     f.nx = nx; f.ny = ny; f.Sx = d.Sx; f.Sy = d.Sy; f.cx = d.cx; f.cy = d.cy; f.n_cells = n_cells;
     f.nxf = d.nxf; f.n_faces = d.n_faces; f.nb = d.nb; f.M = d.M; f.relperm = d.relperm; f.swapped = d.swapped;
@@ -1260,9 +1263,10 @@ extern "C" int lrbms_fine_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n
     launch_fit(d_sims, d_act, n_sims, max_tiles, st);
     launch_flux_cfl(d_sims, d_act, n_sims, max_tiles, flux_smem, st);
     launch_transport(d_sims, d_act, n_sims, max_tiles, st);
+    if (any_dg) launch_transport_dg(d_sims, d_act, n_sims, max_tiles, st);
     launch_finalize(d_sims, d_act, n_sims, st);
     BCK(cudaGetLastError());
-    lrbms_internal_count(ctx, 8);
+    lrbms_internal_count(ctx, any_dg ? 10 : 8);
   }
   BCK(cudaStreamSynchronize(st));
   if (status)

@@ -34,16 +34,19 @@ LRBMS_DT_CFL = 0
 LRBMS_DT_FIXED = 1
 LRBMS_VELOCITY_STATE = 0
 LRBMS_VELOCITY_FITTED = 1
+LRBMS_TRANSPORT_FV = 0
+LRBMS_TRANSPORT_DG1 = 1
 LRBMS_SOLVE_FP64 = 0
 LRBMS_SOLVE_MIXED = 1
-FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS, FIELD_SOLVE_INFO = range(10)
+FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS, FIELD_SOLVE_INFO, \
+    FIELD_SLOPES = range(11)
 
 EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offline_build",
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
             "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count", "lrbms_solve_noalloc",
             "lrbms_fine_step", "lrbms_step_status", "lrbms_test_withhold_copy", "lrbms_tuned_threads",
-            "lrbms_last_error"]
+            "lrbms_last_error", "lrbms_set_slopes"]
 
 
 class LrbmsError(RuntimeError):
@@ -66,7 +69,8 @@ class Problem(C.Structure):
                 ("bc_type", C.c_void_p), ("p_D", C.c_void_p), ("v_N", C.c_void_p),
                 ("s_D", C.c_void_p), ("s0", C.c_void_p),
                 ("cfl", C.c_double), ("dt_mode", C.c_int), ("dt_fixed", C.c_double),
-                ("dt_max", C.c_double), ("mean_weights", C.c_int), ("velocity", C.c_int)]
+                ("dt_max", C.c_double), ("mean_weights", C.c_int), ("velocity", C.c_int),
+                ("transport", C.c_int)]
 
 
 class Offline(C.Structure):
@@ -110,6 +114,7 @@ def library() -> C.CDLL:
         lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
         lib.lrbms_get_state.argtypes = [vp, i, vp, dp, dp]
         lib.lrbms_set_saturation.argtypes = [vp, i, vp]
+        lib.lrbms_set_slopes.argtypes = [vp, i, vp]
         lib.lrbms_get_field.argtypes = [vp, i, i, vp, sz]
         lib.lrbms_field_bytes.argtypes = [vp, i, i]
         lib.lrbms_field_bytes.restype = sz
@@ -169,7 +174,8 @@ def _problem_struct(problem: dict, keep: dict) -> Problem:
                    problem.get("relperm", LRBMS_COREY), _ptr(pa["bc_type"]), _ptr(pa["p_D"]),
                    _ptr(pa["v_N"]), _ptr(pa["s_D"]), _ptr(pa["s0"]), problem.get("cfl", 0.5),
                    problem.get("dt_mode", LRBMS_DT_CFL), problem.get("dt_fixed", 0.0),
-                   problem.get("dt_max", 0.0), problem.get("mean_weights", 0), problem.get("velocity", 0))
+                   problem.get("dt_max", 0.0), problem.get("mean_weights", 0), problem.get("velocity", 0),
+                   problem.get("transport", 0))
 
 
 def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return_sizes=False):
@@ -228,7 +234,8 @@ def lrbms_offline_load(ctx, problem: dict, offline: dict) -> int:
                  problem.get("relperm", LRBMS_COREY), _ptr(pa["bc_type"]), _ptr(pa["p_D"]),
                  _ptr(pa["v_N"]), _ptr(pa["s_D"]), _ptr(pa["s0"]), problem.get("cfl", 0.5),
                  problem.get("dt_mode", LRBMS_DT_CFL), problem.get("dt_fixed", 0.0),
-                 problem.get("dt_max", 0.0), problem.get("mean_weights", 0), problem.get("velocity", 0))
+                 problem.get("dt_max", 0.0), problem.get("mean_weights", 0), problem.get("velocity", 0),
+                   problem.get("transport", 0))
     oa = {k: _as(offline.get(k), dt) for k, dt in (("N_E", np.int32), ("prof_idx", np.uint8),
                                                  ("prof", np.float64), ("Gpinv", np.float64),
                                                  ("Phi", np.float64), ("Dblk", np.float64),
@@ -322,6 +329,12 @@ def lrbms_test_withhold_copy(ctx, sim_id: int):
     """Test hook: the next reduced solve of sim_id withholds one bulk copy, so
     its bounded wait runs out and the simulation stops with LRBMS_E_TIMEOUT."""
     _check(ctx, library().lrbms_test_withhold_copy(ctx, sim_id))
+
+
+def lrbms_set_slopes(ctx, sim_id: int, slopes):
+    """Slopes [2][n_cells] of a simulation with the P1-DG transport."""
+    sl = _as(slopes, np.float64)
+    _check(ctx, library().lrbms_set_slopes(ctx, sim_id, _ptr(sl)))
 
 
 def lrbms_set_saturation(ctx, sim_id: int, s):

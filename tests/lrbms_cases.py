@@ -14,13 +14,14 @@ from oracle.offline import (build_offline, initial_profiles, local_mass_rows, or
 from synth import make_problem, simplex_params, basis_sizes
 
 
-def abi_problem(prob, model: FineModel, s0=None, dt_mode=0, dt_fixed=0.0, dt_max=0.0, velocity=0):
+def abi_problem(prob, model: FineModel, s0=None, dt_mode=0, dt_fixed=0.0, dt_max=0.0, velocity=0, transport=0):
     return dict(nx=prob.nx, ny=prob.ny, Sx=prob.Sx, Sy=prob.Sy, Lx=prob.Lx, Ly=prob.Ly,
                 perm=prob.perm, poro=prob.poro, eta_w=prob.eta_w, eta_o=prob.eta_o,
                 relperm=0 if prob.relperm == "corey" else 1, bc_type=prob.bc_type,
                 p_D=prob.p_D, v_N=prob.v_N, s_D=prob.s_D,
                 s0=prob.s0 if s0 is None else s0, cfl=prob.cfl, dt_mode=dt_mode,
-                dt_fixed=dt_fixed, dt_max=dt_max, mean_weights=1 if model.swapped else 0, velocity=velocity)
+                dt_fixed=dt_fixed, dt_max=dt_max, mean_weights=1 if model.swapped else 0, velocity=velocity,
+                transport=transport)
 
 
 def abi_offline(co: Coarse, off, dense_profiles: bool = False):
