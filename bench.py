@@ -64,6 +64,10 @@ def parse_args():
                          "plain-path or CPU legs; the JSON line then holds only the timed value)")
     ap.add_argument("--serving", action="store_true",
                     help="continuous-batching serving run with Poisson arrivals (its own JSON line)")
+    ap.add_argument("--c2", action="store_true",
+                    help="C2: one simulation on the 256x256 anisotropic field (16x16 subdomains, contrast 1e6), "
+                         "plain FP64 reduced steps against full fine SWIP-DG steps (its own JSON line)")
+    ap.add_argument("--c2-fine-steps", type=int, default=2)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-steps", type=int, default=300, help="online steps per request")
@@ -360,10 +364,62 @@ def run_serving(a):
     L.lrbms_destroy(ctx)
 
 
+def run_c2(a):
+    """C2: one simulation of the 256x256 anisotropic workload (correlation
+    lengths 0.2 x 0.02, contrast 1e6, viscosity ratio 5, 16x16 subdomains,
+    local bases of at most 20 functions from 24 snapshots built on the GPU).
+    Times plain FP64 reduced steps (FP64 block Cholesky every step, one
+    simulation per call, waiting for each step) and full fine SWIP-DG steps
+    (Algorithm 1 through lrbms_fine_step) from the same state."""
+    import numpy as np
+    import torch
+    from paper_1405_2810_gb300 import build, lrbms as L
+    from synth import make_problem, simplex_params
+    build.build()
+    prob = make_problem("aniso")
+    n_sub = prob.Sx * prob.Sy
+    ctx = L.lrbms_create(precision=L.LRBMS_FP64, solver=L.LRBMS_SOLVE_FP64, max_slots=4, hbm_budget=8 << 30)
+    t0 = time.perf_counter()
+    (sid,), sizes = L.lrbms_offline_build(ctx, [abi_problem(prob)], [dict(
+        M=prob.M, n_steps_T=prob.n_steps, N_E=np.full(n_sub, 20, dtype=np.int32),
+        mu=simplex_params(24, prob.M, 2811), c_pen=penalty_scale(prob), allow_fewer=1)], 1, None,
+        return_sizes=True)
+    t_build = time.perf_counter() - t0
+    fine = L.lrbms_clone(ctx, sid, None)
+    L.lrbms_step(ctx, [sid], 3)  # warm-up (also the autotuner)
+    K = 20
+    t0 = time.perf_counter()
+    for _ in range(K):
+        st = L.lrbms_step(ctx, [sid], 1)
+    t_red = (time.perf_counter() - t0) / K
+    s_now = L.lrbms_get_field(ctx, sid, L.FIELD_S)
+    L.lrbms_set_saturation(ctx, fine, s_now)
+    L.lrbms_fine_step(ctx, [fine], 1)  # warm-up (allocation, code load)
+    L.lrbms_set_saturation(ctx, fine, s_now)
+    t0 = time.perf_counter()
+    stf = L.lrbms_fine_step(ctx, [fine], a.c2_fine_steps)
+    t_fine = (time.perf_counter() - t0) / a.c2_fine_steps
+    print(json.dumps({
+        "metric": "C2: plain FP64 reduced step vs full fine SWIP-DG step, one simulation",
+        "value": t_fine / t_red, "unit": "x (fine step time / reduced step time)", "higher_is_better": True,
+        "reduced_step_ms": 1e3 * t_red, "fine_step_ms": 1e3 * t_fine, "reduced_status": int(st[0]),
+        "fine_status": int(stf[0]), "basis_sizes_mean": float(sizes.mean()), "N": int(sizes.sum()),
+        "offline_build_s": t_build, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "256x256 anisotropic log-normal field (0.2 x 0.02, contrast 1e6), 16x16 subdomains, "
+                               "viscosity ratio 5, M=8, basis sizes <= 20",
+                   "reduced": "FP64 block Cholesky every step, one refinement step",
+                   "fine": "SWIP-DG P1 (3 x 65536 unknowns), FP64 envelope block Cholesky, one CTA"},
+    }))
+    L.lrbms_destroy(ctx)
+
+
 def main():
     a = parse_args()
     if a.serving:
         run_serving(a)
+        return
+    if a.c2:
+        run_c2(a)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -155,6 +155,7 @@ __global__ void k_prepare(const SimDev* __restrict__ sp) {
     S.fcoef[(size_t)nf + f] = c1;
     S.fcoef[2 * (size_t)nf + f] = c2;
   }
+  for (int b = i0; b < S.nb; b += stride) S.fwD[b] = frac_flow(S, S.s_D[b]);
 }
 
 // ------------------------------------------------------------------ fit
@@ -456,13 +457,22 @@ __device__ __forceinline__ double step_dt(const SimDev& S) {
 // (s|e1 if F >= 0, else s|e2; s_D on boundary inflow). Both cells of an
 // interior face evaluate G_f from identical operands, so it cancels exactly
 // in the total water volume.
-__device__ __forceinline__ double face_term_interior(const double* fw, double F, int e1, int e2) {
-  return F * ((F >= 0.0) ? fw[e1] : fw[e2]);
+// F >= 0 by the bit pattern (integer pipe): +0 and -0 count as >= 0; a NaN
+// flux makes the new saturation non-finite either way.
+__device__ __forceinline__ bool nonneg(double F) {
+  const long long b = __double_as_longlong(F);
+  return b >= 0 || b == (long long)0x8000000000000000ULL;
 }
-// Boundary face with outward flux Fo: the cell's own f_w on outflow, f_w(s_D) on inflow.
-__device__ __forceinline__ double face_term_boundary(const SimDev& S, const double* fw, double Fo, int e,
-                                                     double sD) {
-  return Fo * ((Fo >= 0.0) ? fw[e] : frac_flow(S, sD));
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ double face_term_interior(const double* fw, double F, int e1, int e2) {
+  return F * (nonneg(F) ? fw[e1] : fw[e2]);
+}
+// Boundary face b with outward flux Fo: the cell's own f_w on outflow,
+// f_w(s_D) (computed at load) on inflow.
+__device__ __forceinline__ double face_term_boundary(const SimDev& S, const double* fw, double Fo, int e, int b) {
+  return Fo * (nonneg(Fo) ? fw[e] : S.fwD[b]);
 }
 
 // A fixed step beyond the CFL bound with CFL number 1 (dt L_f outflow_e /
@@ -511,33 +521,33 @@ __global__ void k_transport(const SimDev* __restrict__ sims, const int* __restri
     if (i > 0) {
       net -= face_term_interior(fw, S.F[fl], e - 1, e);
     } else {
-      g = face_term_boundary(S, fw, -S.F[fl], e, S.s_D[j]);
+      g = face_term_boundary(S, fw, -S.F[fl], e, j);
       net += g;
       bout += g;
     }
     if (i < nx - 1) {
       net += face_term_interior(fw, S.F[fr], e, e + 1);
     } else {
-      g = face_term_boundary(S, fw, S.F[fr], e, S.s_D[ny + j]);
+      g = face_term_boundary(S, fw, S.F[fr], e, ny + j);
       net += g;
       bout += g;
     }
     if (j > 0) {
       net -= face_term_interior(fw, S.F[fb], e - nx, e);
     } else {
-      g = face_term_boundary(S, fw, -S.F[fb], e, S.s_D[2 * ny + i]);
+      g = face_term_boundary(S, fw, -S.F[fb], e, 2 * ny + i);
       net += g;
       bout += g;
     }
     if (j < ny - 1) {
       net += face_term_interior(fw, S.F[ft], e, e + nx);
     } else {
-      g = face_term_boundary(S, fw, S.F[ft], e, S.s_D[2 * ny + nx + i]);
+      g = face_term_boundary(S, fw, S.F[ft], e, 2 * ny + nx + i);
       net += g;
       bout += g;
     }
     const double v = s[e] - dt * S.inv_pv[e] * net;
-    if (!isfinite(v)) bad = true;
+    if (!finite_bits(v)) bad = true;
     sn[e] = v;
     fit_cell(S, v, e, lam_n, fw_n, acc);  // the next step's fit (Eq. leastSquaresFit)
   }

@@ -1284,24 +1284,21 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   return true;
 }
 
-// acc += sum_{c < n} a[c * sa] xs[c * sx] (FP64). The loads of a (global
-// memory) go out in rounds of 16 independent, predicated loads before their
-// products, so that a row of up to 32 entries costs two memory latencies
-// rather than one per four entries; four accumulation chains.
+// acc += sum_{c < n} a[c * sa] xs[c * sx] with four chains (FP64).
 __device__ __noinline__ double dot_strided(const double* __restrict__ a, int sa, const double* xs, int sx, int n,
                                            double acc) {
-  constexpr int kB = 16;
-  double s[4] = {acc, 0.0, 0.0, 0.0};
+  double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = 0;
   #pragma unroll 1
-  for (int c = 0; c < n; c += kB) {
-    double v[kB];
-#pragma unroll
-    for (int k = 0; k < kB; ++k) v[k] = (c + k < n) ? a[(c + k) * sa] : 0.0;
-#pragma unroll
-    for (int k = 0; k < kB; ++k)
-      if (c + k < n) s[k & 3] = fma(v[k], xs[(c + k) * sx], s[k & 3]);
+  for (; c + 3 < n; c += 4) {
+    acc = fma(a[c * sa], xs[c * sx], acc);
+    a1 = fma(a[(c + 1) * sa], xs[(c + 1) * sx], a1);
+    a2 = fma(a[(c + 2) * sa], xs[(c + 2) * sx], a2);
+    a3 = fma(a[(c + 3) * sa], xs[(c + 3) * sx], a3);
   }
-  return (s[0] + s[1]) + (s[2] + s[3]);
+  #pragma unroll 1
+  for (; c < n; ++c) acc = fma(a[c * sa], xs[c * sx], acc);
+  return (acc + a1) + (a2 + a3);
 }
 
 // r = b - A x with the block-sparse assembled A, in FP64, by the CTA

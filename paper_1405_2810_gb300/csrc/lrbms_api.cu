@@ -352,7 +352,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_slope = dg ? L.add(32 * (size_t)n_cells) : 0, o_unl = dg ? L.add(16 * (size_t)n_cells) : 0;
   const size_t o_F = L.add(8 * (size_t)n_faces);
   const size_t o_lam = L.add(16 * (size_t)n_cells), o_fw = L.add(16 * (size_t)n_cells),
-               o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces);
+               o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces), o_fwD = L.add(8 * (size_t)nb);
   const size_t o_x = L.add(8 * (size_t)N), o_xp = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N),
                o_y = L.add(16 * (size_t)N),
                o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N);
@@ -414,6 +414,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.inject = (int*)P(o_inj);
   d.sched = (const unsigned long long*)P(o_sched);
   d.lam = (double*)P(o_lam); d.fw = (double*)P(o_fw); d.inv_pv = (double*)P(o_ipv); d.fcoef = (double*)P(o_fc);
+  d.fwD = (double*)P(o_fwD);
 
   // the admission stream: the copies and kernels of a new simulation overlap
   // the steps that run meanwhile on the context stream

@@ -73,6 +73,7 @@ struct SimDev {
   double* fw;       // [2][n_cells] f_w(s^n), ping-pong like s
   double* inv_pv;   // [n_cells] 1 / (phi_e |e|)
   double* fcoef;    // [3][n_faces] per-face coefficients of the flux (k_prepare)
+  double* fwD;      // [nb] f_w(s_D) of every boundary face (k_prepare)
 
   // state and work arrays
   double* s;        // [2][n_cells] ping-pong; current = steps & 1 (cell means)
