@@ -282,6 +282,20 @@ typedef struct {
   int allow_fewer;   /* 0: fail with LRBMS_E_FORMAT when a subdomain's snapshots
                         give fewer than N_E independent functions; 1: keep the
                         functions obtained (smaller N_E)                       */
+  int greedy;        /* 0: the local bases are the unit function and the
+                        snapshots at mu, in order (Gram-Schmidt, truncated to
+                        N_E); 1: Algorithm 2 step 2, greedy selection over the
+                        training set mu with the true error of Section 6 in
+                        the energy norm of the fine SWIP matrix at mu_bar:
+                        every subdomain below its cap N_E grows by the
+                        orthonormalised restriction of the worst-approximated
+                        snapshot until that error is at most greedy_tol      */
+  double greedy_tol; /* greedy stopping tolerance                              */
+  const double* mu_bar;  /* [M] energy-norm parameter; NULL: uniform 1/M        */
+  double* history;   /* greedy: the worst error of every iteration (host or
+                        device, at most max_history entries), or NULL          */
+  int max_history;
+  int* n_history;    /* greedy: number of iterations (host), or NULL           */
 } lrbms_build_opts;
 
 /* Build the offline data of n_prob problems (same grids, one options entry

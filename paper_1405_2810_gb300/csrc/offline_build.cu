@@ -372,6 +372,7 @@ struct GsJob {
   const double* const* snaps;  // cell-major fine pressures
   double* Phi;                 // output for this subdomain
   int* got;                    // number of functions produced
+  int have0;                   // functions already in Phi (0: start with the unit function)
 };
 
 __global__ void k_gram_schmidt(const FineDev* __restrict__ fds, const GsJob* __restrict__ jobs) {
@@ -382,8 +383,8 @@ __global__ void k_gram_schmidt(const FineDev* __restrict__ fds, const GsJob* __r
   extern __shared__ double v[];  // rows
   __shared__ double red[32];
   const double w3[3] = {f.vol, f.vol / 3.0, f.vol / 3.0};
-  int have = 0;
-  for (int cand = -1; cand < J.n_snap && have < J.NE; ++cand) {
+  int have = J.have0;
+  for (int cand = have > 0 ? 0 : -1; cand < J.n_snap && have < J.NE; ++cand) {
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
       const int k = r / cells, c = r - k * cells;
       if (cand < 0) {
@@ -557,6 +558,111 @@ __global__ void k_rotate(const RotJob* __restrict__ jobs) {
 
 // ----------------------------------------------------------------- host side
 namespace {
+
+
+// ---- greedy basis selection (Algorithm 2, step 2): training systems
+// A_t = c + sum_q mu_tq b_q, rhs_t = e + sum_q mu_tq d_q of the current local
+// bases, their reduced solutions, and the true error of Section 6 in the
+// energy norm of the fine SWIP matrix at mu_bar.
+struct GreedyDev {
+  int n_sub, n_blocks, M, nx, ny, cells, n_int;
+  const int* NE;            // [n_sub] current sizes
+  const int* xoff;          // [n_sub + 1]
+  const long long* aoff;    // [n_blocks + 1]
+  const long long* phioff;  // [n_sub] (cap layout)
+  const double* comp;       // block b at (M+1) aoff[b]: [M+1][size_b]
+  const double* rhs;        // subdomain E at (M+1) xoff[E]: [M+1][N_E]
+  const double* Phi;
+  const double* mu;         // [n_tr][M]
+  double* A;                // [n_tr][aoff[n_blocks]]
+  double* b;                // [n_tr][N]
+  const double* x;          // [n_tr][N]
+  const double* const* snaps;  // [n_tr] cell-major fine pressures
+  double* diff;             // [n_tr][3 n_cells]
+  const double* Dbar;       // [n_cells][9]  fine matrix at mu_bar
+  const double* Obar;       // [n_int][9]
+  double* part;             // [n_tr][gridDim.x] energy partial sums
+  long long a_tot;
+  int N;
+};
+
+__global__ void k_greedy_assemble(const GreedyDev* __restrict__ gp) {
+  const GreedyDev& G = *gp;
+  const int t = blockIdx.y, bidx = blockIdx.x;
+  const int Q = G.M + 1;
+  __shared__ double w[kMaxM + 1];
+  if (threadIdx.x == 0) w[0] = 1.0;
+  if (threadIdx.x < G.M) w[1 + threadIdx.x] = G.mu[(size_t)t * G.M + threadIdx.x];
+  __syncthreads();
+  if (bidx < G.n_blocks) {
+    const long long o = G.aoff[bidx];
+    const int size = (int)(G.aoff[bidx + 1] - o);
+    const double* c = G.comp + (size_t)Q * o;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc = fma(w[q], c[(size_t)q * size + i], acc);
+      G.A[(size_t)t * G.a_tot + o + i] = acc;
+    }
+  } else if (bidx < G.n_blocks + G.n_sub) {
+    const int E = bidx - G.n_blocks, NE = G.NE[E], x0 = G.xoff[E];
+    const double* c = G.rhs + (size_t)Q * x0;
+    for (int i = threadIdx.x; i < NE; i += blockDim.x) {
+      double acc = 0.0;
+      for (int q = 0; q < Q; ++q) acc = fma(w[q], c[(size_t)q * NE + i], acc);
+      G.b[(size_t)t * G.N + x0 + i] = acc;
+    }
+  }
+}
+
+// diff_t = (sum_i x_ti phi_i) - p_h(mu_t), cell-major, for every training t
+__global__ void k_greedy_diff(const FineDev* __restrict__ fds, const GreedyDev* __restrict__ gp, int prob) {
+  const GreedyDev& G = *gp;
+  const FineDev& f = fds[prob];
+  const int t = blockIdx.y, n_cells = G.nx * G.ny, cells = G.cells, rows = 3 * cells;
+  const double* x = G.x + (size_t)t * G.N;
+  const double* snap = G.snaps[t];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_cells; e += gridDim.x * blockDim.x) {
+    const int i = e % G.nx, j = e / G.nx;
+    const int E = (j / f.cy) * f.Sx + (i / f.cx);
+    const int c = (j % f.cy) * f.cx + (i % f.cx);
+    const double* Ph = G.Phi + G.phioff[E];
+    const int NE = G.NE[E], x0 = G.xoff[E];
+    for (int k = 0; k < 3; ++k) {
+      double v = 0.0;
+      for (int a = 0; a < NE; ++a) v = fma(Ph[(size_t)a * rows + k * cells + c], x[x0 + a], v);
+      G.diff[((size_t)t * n_cells + e) * 3 + k] = v - snap[e * 3 + k];
+    }
+  }
+}
+
+// Partial sums of diff^T Kbar diff per CTA (fixed partition): the cell's
+// diagonal block, and twice its coupling to the right and upper neighbours
+// (the matrix is symmetric; each interior face block is stored once, row e1).
+__global__ void k_greedy_energy(const GreedyDev* __restrict__ gp) {
+  const GreedyDev& G = *gp;
+  const int t = blockIdx.y, nx = G.nx, ny = G.ny, n_cells = nx * ny;
+  const double* d = G.diff + (size_t)t * n_cells * 3;
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_cells; e += gridDim.x * blockDim.x) {
+    const int i = e % nx, j = e / nx;
+    const double* v = d + (size_t)e * 3;
+    const double* D = G.Dbar + (size_t)e * 9;
+    for (int k = 0; k < 3; ++k) acc += v[k] * (D[k * 3] * v[0] + D[k * 3 + 1] * v[1] + D[k * 3 + 2] * v[2]);
+    if (i + 1 < nx) {
+      const double* O = G.Obar + (size_t)(j * (nx - 1) + i) * 9;
+      const double* u = d + (size_t)(e + 1) * 3;
+      for (int k = 0; k < 3; ++k) acc += 2.0 * v[k] * (O[k * 3] * u[0] + O[k * 3 + 1] * u[1] + O[k * 3 + 2] * u[2]);
+    }
+    if (j + 1 < ny) {
+      const double* O = G.Obar + (size_t)(ny * (nx - 1) + j * nx + i) * 9;
+      const double* u = d + (size_t)(e + nx) * 3;
+      for (int k = 0; k < 3; ++k) acc += 2.0 * v[k] * (O[k * 3] * u[0] + O[k * 3 + 1] * u[1] + O[k * 3 + 2] * u[2]);
+    }
+  }
+  const double r = block_reduce_sum(acc, red);
+  if (threadIdx.x == 0) G.part[(size_t)t * gridDim.x + blockIdx.x] = r;
+}
 
 struct DevBuf {
   std::vector<void*> ptrs;
@@ -735,6 +841,225 @@ extern "C" void lrbms_internal_count(lrbms_ctx* ctx, long long n);
       return lrbms_internal_fail(ctx, LRBMS_E_CUDA, (std::string(#call) + ": " + \
                                                      cudaGetErrorString(e_)).c_str()); \
   } while (0)
+
+
+// Algorithm 2, step 2 for one problem: starting from the unit function of
+// every subdomain, solve the reduced system of every training parameter mu_t
+// (FP64 block Cholesky, batched), measure the true error of Section 6,
+// ||p_N(mu_t) - p_h(mu_t)|| in the energy norm of the fine SWIP matrix at
+// mu_bar (the oracle's reading), and extend every subdomain below its cap by
+// the Gram-Schmidt orthonormalised restriction of the worst-approximated
+// snapshot, until the worst error is at most the tolerance, every cap is
+// reached or no subdomain grows. NE: caps on entry, sizes on return; Phi and
+// phioff: the compacted bases.
+template <typename RunSystems>
+static int greedy_bases(lrbms_ctx* ctx, DevBuf& B, cudaStream_t st, const FineDev* d_fd, const FineDev& f, int p,
+                        const lrbms_build_opts& O, const double* dmu, const double* const* dsnap, std::vector<int>& NE,
+                        double*& Phi, std::vector<long long>& phioff, const std::vector<int>& cfm,
+                        const std::vector<int>& cfp, int n_int, RunSystems& run_systems) {
+  const int n_sub = f.Sx * f.Sy, n_cf = (int)cfm.size(), n_blocks = n_sub + n_cf, M = O.M, Q = M + 1;
+  const int cells = f.cx * f.cy, rows = 3 * cells, n_cells = f.n_cells, n_tr = O.n_snap;
+  const std::vector<int> cap = NE;
+  // capacities of the growing system (caps)
+  long long a_cap = 0;
+  int N_cap = 0;
+  for (int E = 0; E < n_sub; ++E) a_cap += (long long)cap[E] * cap[E], N_cap += cap[E];
+  for (int c = 0; c < n_cf; ++c) a_cap += (long long)cap[cfm[c]] * cap[cfp[c]];
+  std::vector<int> xcap(n_sub + 1, 0);
+  for (int E = 0; E < n_sub; ++E) xcap[E + 1] = xcap[E] + cap[E];
+  std::vector<long long> lcap(n_sub + 1), icap(n_sub + 1);
+  solve_offsets(n_sub, f.Sx, cap.data(), xcap.data(), lcap.data(), icap.data());
+  // fine component blocks (Section 4.4) and the energy-norm matrix at mu_bar
+  std::vector<double*> D(Q), Ob(Q), R(Q);
+  std::vector<SysJob> jobs(Q + 1);
+  for (int q = 0; q < Q; ++q) {
+    D[q] = B.get<double>(9 * (size_t)n_cells);
+    Ob[q] = B.get<double>(9 * (size_t)std::max(n_int, 1));
+    R[q] = B.get<double>(3 * (size_t)n_cells);
+    if (!D[q] || !Ob[q] || !R[q]) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "greedy component blocks");
+    jobs[q] = q == 0 ? SysJob{p, 2, 1, 0, nullptr, D[q], Ob[q], R[q]} : SysJob{p, 2, 2, q - 1, nullptr, D[q], Ob[q], R[q]};
+  }
+  double* dmubar = B.get<double>(M);
+  double* Dbar = B.get<double>(9 * (size_t)n_cells);
+  double* Obar = B.get<double>(9 * (size_t)std::max(n_int, 1));
+  double* rbar = B.get<double>(3 * (size_t)n_cells);
+  if (!dmubar || !Dbar || !Obar || !rbar) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "greedy energy matrix");
+  std::vector<double> mubar(M, 1.0 / M);
+  if (O.mu_bar) BCK(cudaMemcpy(mubar.data(), O.mu_bar, 8 * (size_t)M, cudaMemcpyDefault));
+  BCK(cudaMemcpyAsync(dmubar, mubar.data(), 8 * (size_t)M, cudaMemcpyHostToDevice, st));
+  jobs[Q] = SysJob{p, 1, 3, 0, dmubar, Dbar, Obar, rbar};
+  if (int rc = run_systems(jobs)) return lrbms_internal_fail(ctx, rc, "greedy assembly");
+  // buffers
+  double* comp = B.get<double>((size_t)Q * a_cap);
+  double* rhs = B.get<double>((size_t)Q * N_cap);
+  double* A = B.get<double>((size_t)n_tr * a_cap);
+  double* bv = B.get<double>((size_t)n_tr * N_cap);
+  double* xv = B.get<double>((size_t)n_tr * N_cap);
+  double* yv = B.get<double>((size_t)n_tr * 2 * N_cap);
+  double* rv = B.get<double>((size_t)n_tr * N_cap);
+  double* dv = B.get<double>((size_t)n_tr * N_cap);
+  double* Lv = B.get<double>((size_t)n_tr * lcap[n_sub]);
+  double* Li = B.get<double>((size_t)n_tr * icap[n_sub]);
+  int* stv = B.get<int>(n_tr);
+  double* diff = B.get<double>((size_t)n_tr * 3 * n_cells);
+  int* dNE = B.get<int>(n_sub);
+  int* dxoff = B.get<int>(n_sub + 1);
+  long long* daoff = B.get<long long>(n_blocks + 1);
+  long long* dloff = B.get<long long>(n_sub + 1);
+  long long* dioff = B.get<long long>(n_sub + 1);
+  long long* dphioff = B.get<long long>(n_sub);
+  unsigned long long* dsched = B.get<unsigned long long>(sched_words(n_sub, f.Sx));
+  int* dgot = B.get<int>(n_sub);
+  int* dact = B.get<int>(n_tr);
+  SimDev* dsims = B.get<SimDev>(n_tr);
+  GreedyDev* dG = B.get<GreedyDev>(1);
+  constexpr int kEnergyBlocks = 64;
+  double* dpart = B.get<double>((size_t)n_tr * kEnergyBlocks);
+  GsJob* dgs = B.get<GsJob>(n_sub);
+  if (!comp || !rhs || !A || !bv || !xv || !yv || !rv || !dv || !Lv || !Li || !stv || !diff || !dNE || !dxoff ||
+      !daoff || !dloff || !dioff || !dphioff || !dsched || !dgot || !dact || !dsims || !dG || !dpart || !dgs)
+    return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "greedy buffers");
+  BCK(cudaMemcpyAsync(dphioff, phioff.data(), 8 * (size_t)n_sub, cudaMemcpyHostToDevice, st));
+  {
+    std::vector<int> act(n_tr);
+    for (int t = 0; t < n_tr; ++t) act[t] = t;
+    BCK(cudaMemcpyAsync(dact, act.data(), 4 * (size_t)n_tr, cudaMemcpyHostToDevice, st));
+  }
+  // unit functions
+  std::vector<int> cur(n_sub, 0);
+  {
+    std::vector<GsJob> gj(n_sub);
+    for (int E = 0; E < n_sub; ++E) gj[E] = GsJob{p, E, 1, 0, dsnap, Phi + phioff[E], dgot + E, 0};
+    BCK(cudaMemcpyAsync(dgs, gj.data(), sizeof(GsJob) * n_sub, cudaMemcpyHostToDevice, st));
+    k_gram_schmidt<<<(unsigned)n_sub, 256, 8 * (size_t)rows, st>>>(d_fd, dgs);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(cur.data(), dgot, 4 * (size_t)n_sub, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+  }
+  std::vector<double> hist;
+  std::vector<double> part((size_t)n_tr * kEnergyBlocks);
+  for (int it = 0; it < 200; ++it) {
+    // layout of the current system
+    std::vector<int> xoff(n_sub + 1, 0);
+    for (int E = 0; E < n_sub; ++E) xoff[E + 1] = xoff[E] + cur[E];
+    std::vector<long long> aoff(n_blocks + 1, 0);
+    for (int E = 0; E < n_sub; ++E) aoff[E + 1] = aoff[E] + (long long)cur[E] * cur[E];
+    for (int c = 0; c < n_cf; ++c) aoff[n_sub + c + 1] = aoff[n_sub + c] + (long long)cur[cfm[c]] * cur[cfp[c]];
+    std::vector<long long> loff(n_sub + 1), ioff(n_sub + 1);
+    solve_offsets(n_sub, f.Sx, cur.data(), xoff.data(), loff.data(), ioff.data());
+    int panel_words = 0, max_w = 0;
+    solve_panel_sizes(n_sub, f.Sx, cur.data(), xoff.data(), &panel_words, &max_w);
+    const int N = xoff[n_sub];
+    if (solve_smem_bytes(n_sub, panel_words, max_w, N, sizeof(double)) > kMaxSolveSmem)
+      return lrbms_internal_fail(ctx, LRBMS_E_FORMAT, "greedy: reduced system too large for the on-chip solve");
+    BCK(cudaMemcpyAsync(dNE, cur.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(dxoff, xoff.data(), 4 * (size_t)(n_sub + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(daoff, aoff.data(), 8 * (size_t)(n_blocks + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(dloff, loff.data(), 8 * (size_t)(n_sub + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(dioff, ioff.data(), 8 * (size_t)(n_sub + 1), cudaMemcpyHostToDevice, st));
+    // components of the current bases (Section 4.4)
+    std::vector<ProjJob> pj;
+    for (int q = 0; q < Q; ++q) {
+      for (int E = 0; E < n_sub; ++E) {
+        const double* PE = Phi + phioff[E];
+        const size_t sz = (size_t)cur[E] * cur[E];
+        pj.push_back(ProjJob{p, 0, E, E, q, cur[E], cur[E], D[q], Ob[q], R[q], PE, PE,
+                             comp + (size_t)Q * aoff[E] + q * sz});
+        pj.push_back(ProjJob{p, 2, E, E, q, cur[E], 0, D[q], Ob[q], R[q], PE, PE,
+                             rhs + (size_t)Q * xoff[E] + (size_t)q * cur[E]});
+      }
+      for (int c = 0; c < n_cf; ++c) {
+        const int Em = cfm[c], Ep = cfp[c];
+        const size_t sz = (size_t)cur[Em] * cur[Ep];
+        pj.push_back(ProjJob{p, 1, Em, Ep, q, cur[Em], cur[Ep], D[q], Ob[q], R[q], Phi + phioff[Em],
+                             Phi + phioff[Ep], comp + (size_t)Q * aoff[n_sub + c] + q * sz});
+      }
+    }
+    ProjJob* dpj = B.get<ProjJob>(pj.size());
+    if (!dpj) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "greedy projection jobs");
+    BCK(cudaMemcpyAsync(dpj, pj.data(), sizeof(ProjJob) * pj.size(), cudaMemcpyHostToDevice, st));
+    k_project<<<(unsigned)pj.size(), 256, 0, st>>>(d_fd, dpj);
+    BCK(cudaGetLastError());
+    // training systems and their solves
+    GreedyDev G{n_sub, n_blocks, M, f.nx, f.ny, cells, n_int, dNE, dxoff, daoff, dphioff, comp, rhs, Phi, dmu,
+                A, bv, xv, dsnap, diff, Dbar, Obar, dpart, aoff[n_blocks], N};
+    BCK(cudaMemcpyAsync(dG, &G, sizeof(G), cudaMemcpyHostToDevice, st));
+    k_greedy_assemble<<<dim3(n_blocks + n_sub, n_tr), 128, 0, st>>>(dG);
+    BCK(cudaGetLastError());
+    std::vector<SimDev> sims(n_tr);
+    for (int t = 0; t < n_tr; ++t) {
+      SimDev d{};
+      d.Sx = f.Sx; d.Sy = f.Sy; d.n_sub = n_sub; d.n_cf = n_cf; d.n_blocks = n_blocks; d.N = N;
+      d.panel_words = panel_words; d.max_w = max_w;
+      d.NE = dNE; d.xoff = dxoff; d.aoff = daoff; d.loff = dloff; d.ioff = dioff; d.sched = dsched;
+      d.A = A + (size_t)t * aoff[n_blocks]; d.b = bv + (size_t)t * N; d.x = xv + (size_t)t * N;
+      d.y = yv + (size_t)t * 2 * N; d.rv = rv + (size_t)t * N; d.dv = dv + (size_t)t * N;
+      d.L = Lv + (size_t)t * loff[n_sub]; d.Linv = Li + (size_t)t * ioff[n_sub]; d.status = stv + t;
+      sims[t] = d;
+    }
+    BCK(cudaMemsetAsync(stv, 0, 4 * (size_t)n_tr, st));
+    BCK(cudaMemcpyAsync(dsims, sims.data(), sizeof(SimDev) * n_tr, cudaMemcpyHostToDevice, st));
+    launch_sched(dsims, st);
+    const SolveShape sh{n_sub, panel_words, max_w, N};
+    BCK(prepare_chol_solve(0, sh));
+    BCK(launch_chol_solve(dsims, dact, n_tr, 0, 1, sh, st));
+    std::vector<int> sst(n_tr);
+    BCK(cudaMemcpyAsync(sst.data(), stv, 4 * (size_t)n_tr, cudaMemcpyDeviceToHost, st));
+    // error fields and energy norms
+    k_greedy_diff<<<dim3(std::min(152, (n_cells + 255) / 256), n_tr), 256, 0, st>>>(d_fd, dG, p);
+    k_greedy_energy<<<dim3(kEnergyBlocks, n_tr), 256, 0, st>>>(dG);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(part.data(), dpart, 8 * part.size(), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    for (int t = 0; t < n_tr; ++t)
+      if (sst[t]) return lrbms_internal_fail(ctx, LRBMS_E_NOT_SPD, "greedy: a training system was not positive definite");
+    int kmax = 0;
+    double emax = -1.0;
+    for (int t = 0; t < n_tr; ++t) {
+      double e2 = 0.0;
+      for (int b = 0; b < kEnergyBlocks; ++b) e2 += part[(size_t)t * kEnergyBlocks + b];
+      const double e = std::sqrt(std::max(e2, 0.0));
+      if (e > emax) emax = e, kmax = t;
+    }
+    hist.push_back(emax);
+    int tot = 0, tot_cap = 0;
+    for (int E = 0; E < n_sub; ++E) tot += cur[E], tot_cap += cap[E];
+    if (emax <= O.greedy_tol || tot >= tot_cap) break;
+    // extend every subdomain below its cap by the worst-approximated snapshot
+    std::vector<GsJob> gj;
+    for (int E = 0; E < n_sub; ++E)
+      if (cur[E] < cap[E]) gj.push_back(GsJob{p, E, cur[E] + 1, 1, dsnap + kmax, Phi + phioff[E], dgot + E, cur[E]});
+    BCK(cudaMemcpyAsync(dgot, cur.data(), 4 * (size_t)n_sub, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(dgs, gj.data(), sizeof(GsJob) * gj.size(), cudaMemcpyHostToDevice, st));
+    k_gram_schmidt<<<(unsigned)gj.size(), 256, 8 * (size_t)rows, st>>>(d_fd, dgs);
+    BCK(cudaGetLastError());
+    std::vector<int> got(n_sub);
+    BCK(cudaMemcpyAsync(got.data(), dgot, 4 * (size_t)n_sub, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    bool grew = false;
+    for (int E = 0; E < n_sub; ++E) grew |= got[E] > cur[E];
+    cur = got;
+    if (!grew) break;
+  }
+  if (O.history) {
+    const int nh = std::min((int)hist.size(), O.max_history);
+    BCK(cudaMemcpy(O.history, hist.data(), 8 * (size_t)nh, cudaMemcpyDefault));
+  }
+  if (O.n_history) *O.n_history = (int)hist.size();
+  // compact the bases to their sizes
+  std::vector<long long> off2(n_sub + 1, 0);
+  for (int E = 0; E < n_sub; ++E) off2[E + 1] = off2[E] + (long long)cur[E] * rows;
+  double* P2 = B.get<double>((size_t)off2[n_sub]);
+  if (!P2) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "basis buffers");
+  for (int E = 0; E < n_sub; ++E)
+    BCK(cudaMemcpyAsync(P2 + off2[E], Phi + phioff[E], 8 * (size_t)(off2[E + 1] - off2[E]), cudaMemcpyDeviceToDevice,
+                        st));
+  BCK(cudaStreamSynchronize(st));
+  Phi = P2;
+  phioff = off2;
+  NE = cur;
+  return LRBMS_OK;
+}
 
 extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
                                    const lrbms_build_opts* opts, int n_copies,
@@ -921,6 +1246,14 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
   for (int s = 0; s < n_snap_tot; ++s) snap_ptrs[s] = snaps.sims[s].x;
   const double** dsnap = (const double**)B.get<double*>(std::max(n_snap_tot, 1));
   BCK(cudaMemcpyAsync(dsnap, snap_ptrs.data(), sizeof(double*) * snap_ptrs.size(), cudaMemcpyHostToDevice, st));
+  std::vector<int> cfm(n_cf), cfp(n_cf);
+  {
+    int fidx = 0;
+    for (int J = 0; J < Sy; ++J)
+      for (int I = 0; I + 1 < Sx; ++I, ++fidx) cfm[fidx] = J * Sx + I, cfp[fidx] = J * Sx + I + 1;
+    for (int J = 0; J + 1 < Sy; ++J)
+      for (int I = 0; I < Sx; ++I, ++fidx) cfm[fidx] = J * Sx + I, cfp[fidx] = (J + 1) * Sx + I;
+  }
   for (int p = 0; p < n_prob; ++p) {
     BCK(cudaMemcpy(NE[p].data(), opts[p].N_E, 4 * (size_t)n_sub, cudaMemcpyDefault));
     for (int E = 0; E < n_sub; ++E) {
@@ -930,19 +1263,31 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
     }
     Phi[p] = B.get<double>((size_t)phioff[p][n_sub]);
     if (!Phi[p]) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "basis buffers");
+    if (opts[p].greedy) {
+      // Algorithm 2, step 2: greedy selection over the training set opts.mu
+      // (caps N_E per subdomain); the bases come out compacted to their sizes
+      std::vector<int> cur;
+      const int rc = greedy_bases(ctx, B, st, d_fd, fd[p], p, opts[p], dmu[p], dsnap + snap_off[p], NE[p], Phi[p],
+                                  phioff[p], cfm, cfp, n_int, run_systems);
+      if (rc) return rc;
+      continue;
+    }
     for (int E = 0; E < n_sub; ++E)
       gjobs.push_back(GsJob{p, E, NE[p][E], opts[p].n_snap, dsnap + snap_off[p], Phi[p] + phioff[p][E],
-                            dgot + p * n_sub + E});
+                            dgot + p * n_sub + E, 0});
   }
   {
-    GsJob* dj = B.get<GsJob>(gjobs.size());
-    BCK(cudaMemcpyAsync(dj, gjobs.data(), sizeof(GsJob) * gjobs.size(), cudaMemcpyHostToDevice, st));
-    k_gram_schmidt<<<(unsigned)gjobs.size(), 256, 8 * (size_t)3 * cells, st>>>(d_fd, dj);
-    BCK(cudaGetLastError());
+    if (!gjobs.empty()) {
+      GsJob* dj = B.get<GsJob>(gjobs.size());
+      BCK(cudaMemcpyAsync(dj, gjobs.data(), sizeof(GsJob) * gjobs.size(), cudaMemcpyHostToDevice, st));
+      k_gram_schmidt<<<(unsigned)gjobs.size(), 256, 8 * (size_t)3 * cells, st>>>(d_fd, dj);
+      BCK(cudaGetLastError());
+    }
     std::vector<int> got((size_t)n_prob * n_sub);
     BCK(cudaMemcpyAsync(got.data(), dgot, 4 * got.size(), cudaMemcpyDeviceToHost, st));
     BCK(cudaStreamSynchronize(st));
     for (int p = 0; p < n_prob; ++p) {
+      if (opts[p].greedy) continue;  // sizes already final
       bool fewer = false;
       for (int E = 0; E < n_sub; ++E)
         if (got[p * n_sub + E] != NE[p][E]) {
@@ -974,14 +1319,6 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
   // ---- components (Section 4.4): fine blocks per component, then projection
   std::vector<std::vector<int>> xoff(n_prob, std::vector<int>(n_sub + 1, 0));
   std::vector<std::vector<long long>> aoff(n_prob, std::vector<long long>(n_sub + n_cf + 1, 0));
-  std::vector<int> cfm(n_cf), cfp(n_cf);
-  {
-    int fidx = 0;
-    for (int J = 0; J < Sy; ++J)
-      for (int I = 0; I + 1 < Sx; ++I, ++fidx) cfm[fidx] = J * Sx + I, cfp[fidx] = J * Sx + I + 1;
-    for (int J = 0; J + 1 < Sy; ++J)
-      for (int I = 0; I < Sx; ++I, ++fidx) cfm[fidx] = J * Sx + I, cfp[fidx] = (J + 1) * Sx + I;
-  }
   std::vector<double*> comp(n_prob), rhs(n_prob);
   for (int p = 0; p < n_prob; ++p) {
     const int Q = opts[p].M + 1;

@@ -81,7 +81,9 @@ class Offline(C.Structure):
 
 class BuildOpts(C.Structure):
     _fields_ = [("M", C.c_int), ("n_steps_T", C.c_int), ("N_E", C.c_void_p), ("n_snap", C.c_int),
-                ("mu", C.c_void_p), ("c_pen", C.c_double), ("allow_fewer", C.c_int)]
+                ("mu", C.c_void_p), ("c_pen", C.c_double), ("allow_fewer", C.c_int), ("greedy", C.c_int),
+                ("greedy_tol", C.c_double), ("mu_bar", C.c_void_p), ("history", C.c_void_p),
+                ("max_history", C.c_int), ("n_history", C.c_void_p)]
 
 
 _lib = None
@@ -193,8 +195,13 @@ def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return
         mu = np.ascontiguousarray(o["mu"], dtype=np.float64)
         keep[id(ne)] = ne
         keep[id(mu)] = mu
+        mub = None if o.get("mu_bar") is None else np.ascontiguousarray(o["mu_bar"], dtype=np.float64)
+        hist = o.get("history")  # a float64 NumPy array to fill, or None
+        nh = o.get("n_history")  # a one-element int32 NumPy array, or None
+        keep[id(mub)] = mub
         ol.append(BuildOpts(o["M"], o["n_steps_T"], _ptr(ne), mu.shape[0], _ptr(mu), o["c_pen"],
-                            int(o.get("allow_fewer", 0))))
+                            int(o.get("allow_fewer", 0)), int(o.get("greedy", 0)), float(o.get("greedy_tol", 0.0)),
+                            _ptr(mub), _ptr(hist), 0 if hist is None else len(hist), _ptr(nh)))
     oarr = (BuildOpts * n)(*ol)
     rp = None
     if rot is not None:

@@ -133,3 +133,34 @@ def test_step_io_and_profiling(L):
     assert st[0] == 0
     assert np.array_equal(s_out.numpy(), L.lrbms_get_field(ctx, ids[0], L.FIELD_S))
     L.lrbms_destroy(ctx)
+
+
+@pytest.mark.parametrize("name,kw,cap,tol", [("small", {}, 10, 1e-6),
+                                             ("rect", dict(n=(24, 16), S=(3, 2)), 8, 1e-2)],
+                         ids=["small", "rect"])
+def test_greedy_matches_oracle_greedy(L, name, kw, cap, tol):
+    """Algorithm 2, step 2 on the GPU (greedy over a training set with the
+    true energy error at mu_bar) against the oracle's greedy on the same
+    problem, training set, caps and tolerance: the same number of iterations,
+    the same worst errors (to the round-off of the two fine solvers), the
+    same local basis sizes, and the same online step."""
+    prob = make_problem(name, **kw)
+    m = FineModel.from_problem(prob)
+    co = Coarse(m.grid, prob.Sx, prob.Sy)
+    train = simplex_params(24, prob.M, 11)
+    off = build_offline(m, co, prob.s0, prob.n_steps, prob.M, kind="greedy", train=train, cap=cap, tol=tol)
+    hist_ref = np.array(off.extra["greedy"])
+    ctx = L.lrbms_create(hbm_budget=1 << 30, max_slots=4)
+    hist = np.zeros(64)
+    nh = np.zeros(1, dtype=np.int32)
+    opts = dict(M=prob.M, n_steps_T=prob.n_steps, N_E=np.full(co.n_sub, cap, dtype=np.int32), mu=train,
+                c_pen=m.c_pen, greedy=1, greedy_tol=tol, history=hist, n_history=nh)
+    (sid,), sizes = L.lrbms_offline_build(ctx, [abi_problem(prob, m)], [opts], 1, None, return_sizes=True)
+    assert int(nh[0]) == len(hist_ref)
+    assert np.all(np.abs(hist[: len(hist_ref)] - hist_ref) <= 1e-6 * hist_ref[0] + 1e-6 * np.abs(hist_ref))
+    assert np.array_equal(sizes[0], off.N_E)
+    assert L.lrbms_step(ctx, [sid], 1)[0] == 0
+    ref = online_step(m, off, prob.s0)
+    assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_P), ref["p"].reshape(-1, 3).T.reshape(-1)) < 1e-6
+    assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_S), ref["s"]) < 1e-6
+    L.lrbms_destroy(ctx)
