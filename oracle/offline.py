@@ -220,6 +220,7 @@ def greedy_bases(model: FineModel, coarse: Coarse, P: np.ndarray, ops: FineOpera
     Kbar = bilinear(g, model.perm, mu_bar @ P, model.c_pen, model.bc_type, swapped=model.swapped)
     Phi = [[unit_function(g, nE)] for _ in range(coarse.n_sub)]
     history = []
+    chosen = []  # training indices whose snapshots extended the bases
     for _ in range(max_iter):
         Phi_g = global_basis(coarse, [np.stack(b, axis=1) for b in Phi])
         B, C, d, e = project(ops, Phi_g)
@@ -234,6 +235,7 @@ def greedy_bases(model: FineModel, coarse: Coarse, P: np.ndarray, ops: FineOpera
         history.append(float(errs[k]))
         if errs[k] <= tol or sum(len(b) for b in Phi) >= N_max:
             break
+        chosen.append(k)  # the snapshot set Psi of step 2(d)
         grew = False
         for E in range(coarse.n_sub):
             if len(Phi[E]) >= cap:
@@ -244,7 +246,7 @@ def greedy_bases(model: FineModel, coarse: Coarse, P: np.ndarray, ops: FineOpera
                 grew = True
         if not grew:
             break
-    return [np.stack(b, axis=1) for b in Phi], history
+    return [np.stack(b, axis=1) for b in Phi], history, chosen
 
 
 def snapshot_bases(model: FineModel, coarse: Coarse, P: np.ndarray, mus: np.ndarray,
@@ -268,11 +270,44 @@ def snapshot_bases(model: FineModel, coarse: Coarse, P: np.ndarray, mus: np.ndar
     return Phi
 
 
+def pca_bases(coarse: Coarse, snaps: list, grid: Grid, eps: float, max_size: int = 32):
+    """Algorithm 2, step 3 (optional compression): on every subdomain E the
+    principal components of the restrictions psi_1..psi_n of the selected
+    snapshots, without centring (a proper orthogonal decomposition), in the
+    L2(E) inner product. With the diagonal local mass m and the singular value
+    decomposition sqrt(m) X = U diag(sigma) V^T (X = [psi_1 .. psi_n], sigma
+    descending), the energies are l_k = sigma_k^2, the eigenvalues of the Gram
+    matrix (psi_i, psi_j)_E; keep the fewest r modes whose discarded energy
+    sum_{k > r} l_k is at most eps^2 sum_k l_k (r at most max_size), and
+    phi_k = U e_k / sqrt(m) = sum_i V_ik psi_i / sigma_k, L2(E)-orthonormal.
+    Singular values at most n eps_64 sigma_1 are round-off of a zero energy:
+    they count as 0 and their modes are never kept.
+    (Reading: the paper gives neither the criterion nor the tolerance.)"""
+    nE = coarse.cx * coarse.cy
+    m = local_mass_rows(grid, nE)
+    sm = np.sqrt(m)
+    Phi = []
+    for E in range(coarse.n_sub):
+        X = np.stack([restrict(coarse, sn, E) for sn in snaps], axis=1)  # (3 nE, n)
+        U, sig, _ = np.linalg.svd(sm[:, None] * X, full_matrices=False)
+        sig = np.where(sig > len(snaps) * np.finfo(float).eps * sig[0], sig, 0.0)
+        lam = sig * sig
+        total = lam.sum()
+        tail = np.concatenate([np.cumsum(lam[::-1])[::-1][1:], [0.0]])  # tail[r-1] = sum_{k >= r} l_k (0-based)
+        r = 1
+        while r < len(lam) and r < max_size and lam[r] > 0.0 and tail[r - 1] > eps * eps * total:
+            r += 1
+        Phi.append(U[:, :r] / sm[:, None])
+    return Phi
+
+
 def build_offline(model: FineModel, coarse: Coarse, s0: np.ndarray, n_steps: int, M: int,
                   kind: str = "greedy", train=None, mu_bar=None, cap: int = 10,
-                  tol: float = 1e-6, mus=None, N_E=None, Phi=None, P=None):
-    """Algorithm 2 (without the optional compression) followed by the
-    offline/online decomposition of Section 4.4."""
+                  tol: float = 1e-6, mus=None, N_E=None, Phi=None, P=None, pca_eps=None):
+    """Algorithm 2 followed by the offline/online decomposition of Section
+    4.4. With pca_eps set, the greedy's bases are replaced by the compression
+    of step 3 (pca_bases) of the snapshots the greedy selected, at most cap
+    modes per subdomain."""
     prof = initial_profiles(model, s0, n_steps, M)
     if P is None:
         P = prof["P"]
@@ -280,12 +315,15 @@ def build_offline(model: FineModel, coarse: Coarse, s0: np.ndarray, n_steps: int
     else:
         idx = np.zeros(model.grid.n_cells, dtype=np.uint8)
     ops = fine_operators(model, P)
-    hist = None
+    hist = chosen = None
     if Phi is None:
         if kind == "greedy":
             if mu_bar is None:
                 mu_bar = np.full(M, 1.0 / M)
-            Phi, hist = greedy_bases(model, coarse, P, ops, train, mu_bar, cap, tol)
+            Phi, hist, chosen = greedy_bases(model, coarse, P, ops, train, mu_bar, cap, tol)
+            if pca_eps is not None:
+                snaps = [fine_solution(model, P, train[k]) for k in chosen]
+                Phi = pca_bases(coarse, snaps, model.grid, pca_eps, max_size=cap)
         elif kind == "snapshots":
             Phi = snapshot_bases(model, coarse, P, mus, N_E)
         else:
@@ -296,4 +334,4 @@ def build_offline(model: FineModel, coarse: Coarse, s0: np.ndarray, n_steps: int
                    B=B, C=C, d=d, e=e, P=P, prof_idx=idx, Gp=gram_pinv(P), c_pen=model.c_pen,
                    Lf=model.Lf, lam0=prof["lam0"], lam1=prof["lam1"],
                    extra=dict(tau=prof["tau"], T=prof["T"], p0=prof["p0"], greedy=hist,
-                              ops=ops, Phi_g=Phi_g))
+                              chosen=chosen, ops=ops, Phi_g=Phi_g))
