@@ -250,6 +250,9 @@ enum {
   LRBMS_FIELD_SLOPES = 10, /* [2][n_cells] slopes c1, c2 of the piecewise-linear
                             saturation s = c0 + c1 psi1 + c2 psi2 (c0 is
                             LRBMS_FIELD_S); zeros for LRBMS_TRANSPORT_FV      */
+  LRBMS_FIELD_PHI = 11,  /* [N][3*cells_E] the local reduced bases (FP64), in
+                            the layout of lrbms_offline.Phi (Algorithm 2 step
+                            4: the union of the local bases)                  */
   LRBMS_FIELD_SOLVE_INFO = 9 /* [6] int: correction passes of the last reduced
                             solve; then, counted since load: reduced solves
                             redone in FP64 after the FP32 factorisation or
@@ -296,6 +299,14 @@ typedef struct {
                         device, at most max_history entries), or NULL          */
   int max_history;
   int* n_history;    /* greedy: number of iterations (host), or NULL           */
+  double pca_eps;    /* greedy: > 0 applies the compression of Algorithm 2 step
+                        3 to the snapshots the greedy selected (at most 256):
+                        per subdomain the uncentred principal components of
+                        their restrictions in L2(E), the fewest modes (at most
+                        N_E) whose discarded energy is at most pca_eps^2 of the
+                        total, singular values at most n eps_64 sigma_1 counted
+                        as 0; 0: no compression. LRBMS_E_FORMAT if a subdomain
+                        keeps no mode                                          */
 } lrbms_build_opts;
 
 /* Build the offline data of n_prob problems (same grids, one options entry

@@ -321,7 +321,7 @@ def build_offline(model: FineModel, coarse: Coarse, s0: np.ndarray, n_steps: int
             if mu_bar is None:
                 mu_bar = np.full(M, 1.0 / M)
             Phi, hist, chosen = greedy_bases(model, coarse, P, ops, train, mu_bar, cap, tol)
-            if pca_eps is not None:
+            if pca_eps is not None and chosen:
                 snaps = [fine_solution(model, P, train[k]) for k in chosen]
                 Phi = pca_bases(coarse, snaps, model.grid, pca_eps, max_size=cap)
         elif kind == "snapshots":

@@ -756,6 +756,7 @@ size_t lrbms_field_bytes(lrbms_ctx* ctx, int id, int field) {
     case LRBMS_FIELD_STATUS: return 4;
     case LRBMS_FIELD_SOLVE_INFO: return 24;
     case LRBMS_FIELD_SLOPES: return 16 * (size_t)d.n_cells;
+    case LRBMS_FIELD_PHI: return 24 * (size_t)d.N * d.cx * d.cy;
     default: return 0;
   }
 }
@@ -782,6 +783,7 @@ int lrbms_get_field(lrbms_ctx* ctx, int id, int field, void* dst, size_t bytes) 
     case LRBMS_FIELD_DT: src = d.scal + 1; break;
     case LRBMS_FIELD_STATUS: src = d.status; break;
     case LRBMS_FIELD_SOLVE_INFO: src = d.info; break;
+    case LRBMS_FIELD_PHI: src = d.Phi; break;
     case LRBMS_FIELD_SLOPES:
       if (!d.sslope) {  // piecewise-constant transport: no slopes (dst may be host memory)
         const std::vector<double> zeros(bytes / sizeof(double), 0.0);

@@ -664,6 +664,184 @@ __global__ void k_greedy_energy(const GreedyDev* __restrict__ gp) {
   if (threadIdx.x == 0) G.part[(size_t)t * gridDim.x + blockIdx.x] = r;
 }
 
+// ---- compression (Algorithm 2, step 3): principal components, without
+// centring, of the restrictions psi_1..psi_n of the snapshots the greedy
+// selected, in L2(E), one CTA per subdomain:
+//  1. X = Q R by two passes of modified Gram-Schmidt in L2(E) (Q
+//     L2(E)-orthonormal; a column whose remaining norm is at most 1e-13 of its
+//     own norm adds no row to R, k <= n rows in all);
+//  2. the singular value decomposition of the k x n matrix R by one-sided
+//     (Hestenes) Jacobi rotations of the k columns of R^T, accumulated in the
+//     k x k matrix W: R^T W has orthogonal columns of norms sigma_j, so the
+//     left singular vectors of X in L2(E) are Q W. Each warp rotates one pair
+//     of columns; the pairs of a round (circle schedule) are disjoint;
+//  3. energies l_j = sigma_j^2 in descending order, singular values at most
+//     n eps_64 sigma_1 counted as 0, and the fewest r modes (r at most the
+//     cap) whose discarded energy is at most eps_pca^2 of the total.
+// Scratch per subdomain: Q [n][rows], Rt [n][n] (row b of R at Rt + b n),
+// W [n][n] (column j at W + j n). Output: [r][rows], row k*cells + c.
+constexpr int kMaxPcaSnap = 256;
+struct PcaJob {
+  int prob, E, n, cap;
+  const double* const* snaps;  // cell-major fine pressures
+  const int* idx;              // [n] selected snapshots
+  double* Q;
+  double* Rt;
+  double* W;
+  double* out;
+  int* got;
+  double eps;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_pca(const FineDev* __restrict__ fds, const PcaJob* __restrict__ jobs) {
+  const PcaJob J = jobs[blockIdx.x];
+  const FineDev& f = fds[J.prob];
+  const int cells = f.cx * f.cy, rows = 3 * cells, n = J.n;
+  const int I = J.E % f.Sx, Jy = J.E / f.Sx;
+  extern __shared__ double v[];  // rows
+  __shared__ double red[32];
+  __shared__ double sig[kMaxPcaSnap];
+  __shared__ int order[kMaxPcaSnap];
+  __shared__ int s_rot, s_r;
+  const double w3[3] = {f.vol, f.vol / 3.0, f.vol / 3.0};
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) J.Rt[i] = 0.0, J.W[i] = 0.0;
+  __syncthreads();
+  // 1. QR
+  int k = 0;
+  for (int j = 0; j < n; ++j) {
+    const double* sn = J.snaps[J.idx[j]];
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      const int kk = r / cells, c = r - kk * cells;
+      const int ge = (Jy * f.cy + c / f.cx) * f.nx + I * f.cx + c % f.cx;
+      v[r] = sn[ge * 3 + kk];
+    }
+    __syncthreads();
+    double n0 = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) n0 += w3[r / cells] * v[r] * v[r];
+    n0 = sqrt(block_reduce_sum(n0, red));
+    if (!(n0 > 0.0)) continue;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int b = 0; b < k; ++b) {
+        const double* qb = J.Q + (size_t)b * rows;
+        double d = 0.0;
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) d += w3[r / cells] * qb[r] * v[r];
+        d = block_reduce_sum(d, red);
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) v[r] -= d * qb[r];
+        if (threadIdx.x == 0) J.Rt[(size_t)b * n + j] += d;
+        __syncthreads();
+      }
+    double nw = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) nw += w3[r / cells] * v[r] * v[r];
+    nw = sqrt(block_reduce_sum(nw, red));
+    if (!(nw > 1e-13 * n0)) continue;
+    double* qk = J.Q + (size_t)k * rows;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) qk[r] = v[r] / nw;
+    if (threadIdx.x == 0) J.Rt[(size_t)k * n + j] = nw;
+    __syncthreads();
+    ++k;
+  }
+  // 2. one-sided Jacobi on the k columns of R^T (column b = row b of R)
+  for (int i = threadIdx.x; i < k; i += blockDim.x) J.W[(size_t)i * n + i] = 1.0;
+  __syncthreads();
+  const int kp = k + (k & 1), n_warps = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int sweep = 0; sweep < 60 && k > 1; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < kp - 1; ++round) {
+      for (int pi = warp; pi < kp / 2; pi += n_warps) {
+        int a, b;
+        if (pi == 0) {
+          a = 0, b = 1 + round;
+        } else {
+          a = 1 + (round + pi) % (kp - 1);
+          b = 1 + (round - pi + (kp - 1)) % (kp - 1);
+        }
+        if (a >= k || b >= k) continue;
+        double* ra = J.Rt + (size_t)a * n;
+        double* rb = J.Rt + (size_t)b * n;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < n; i += 32) al += ra[i] * ra[i], be += rb[i] * rb[i], ga += ra[i] * rb[i];
+        al = warp_sum(al), be = warp_sum(be), ga = warp_sum(ga);
+        if (!(fabs(ga) > 1e-15 * sqrt(al * be))) continue;
+        const double ze = (be - al) / (2.0 * ga);
+        const double tt = (ze >= 0.0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(1.0 + ze * ze));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        for (int i = lane; i < n; i += 32) {
+          const double x = ra[i], y = rb[i];
+          ra[i] = cs * x - sn * y, rb[i] = sn * x + cs * y;
+        }
+        double* wa = J.W + (size_t)a * n;
+        double* wb = J.W + (size_t)b * n;
+        for (int i = lane; i < k; i += 32) {
+          const double x = wa[i], y = wb[i];
+          wa[i] = cs * x - sn * y, wb[i] = sn * x + cs * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  // 3. singular values, order and the number of modes
+  for (int b = warp; b < k; b += n_warps) {
+    const double* rb = J.Rt + (size_t)b * n;
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 += rb[i] * rb[i];
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[b] = sqrt(s2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < k; ++b) order[b] = b;
+    for (int b = 1; b < k; ++b) {  // insertion sort, descending
+      const int o = order[b];
+      int c = b;
+      while (c > 0 && sig[order[c - 1]] < sig[o]) order[c] = order[c - 1], --c;
+      order[c] = o;
+    }
+    const double floor_s = k > 0 ? n * 2.220446049250313e-16 * sig[order[0]] : 0.0;
+    double total = 0.0;
+    for (int b = k - 1; b >= 0; --b) {
+      const double s = sig[order[b]] > floor_s ? sig[order[b]] : 0.0;
+      total += s * s;
+    }
+    // tail(r) = sum of the energies from position r on
+    int r = 1;
+    while (r < k && r < J.cap) {
+      const double sr = sig[order[r]] > floor_s ? sig[order[r]] : 0.0;
+      if (!(sr > 0.0)) break;
+      double tail = 0.0;
+      for (int b = k - 1; b >= r; --b) {
+        const double s = sig[order[b]] > floor_s ? sig[order[b]] : 0.0;
+        tail += s * s;
+      }
+      if (!(tail > J.eps * J.eps * total)) break;
+      ++r;
+    }
+    s_r = k > 0 ? r : 0;
+    *J.got = s_r;
+  }
+  __syncthreads();
+  // modes Q W e_order[j]
+  const int r = s_r;
+  for (int j = 0; j < r; ++j) {
+    const double* wj = J.W + (size_t)order[j] * n;
+    double* o = J.out + (size_t)j * rows;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+      double acc = 0.0;
+      for (int b = 0; b < k; ++b) acc = fma(J.Q[(size_t)b * rows + row], wj[b], acc);
+      o[row] = acc;
+    }
+  }
+}
+
 struct DevBuf {
   std::vector<void*> ptrs;
   ~DevBuf() {
@@ -937,6 +1115,7 @@ static int greedy_bases(lrbms_ctx* ctx, DevBuf& B, cudaStream_t st, const FineDe
     BCK(cudaStreamSynchronize(st));
   }
   std::vector<double> hist;
+  std::vector<int> chosen;  // the snapshot set Psi of step 2(d)
   std::vector<double> part((size_t)n_tr * kEnergyBlocks);
   for (int it = 0; it < 200; ++it) {
     // layout of the current system
@@ -1025,6 +1204,7 @@ static int greedy_bases(lrbms_ctx* ctx, DevBuf& B, cudaStream_t st, const FineDe
     int tot = 0, tot_cap = 0;
     for (int E = 0; E < n_sub; ++E) tot += cur[E], tot_cap += cap[E];
     if (emax <= O.greedy_tol || tot >= tot_cap) break;
+    chosen.push_back(kmax);
     // extend every subdomain below its cap by the worst-approximated snapshot
     std::vector<GsJob> gj;
     for (int E = 0; E < n_sub; ++E)
@@ -1040,6 +1220,30 @@ static int greedy_bases(lrbms_ctx* ctx, DevBuf& B, cudaStream_t st, const FineDe
     for (int E = 0; E < n_sub; ++E) grew |= got[E] > cur[E];
     cur = got;
     if (!grew) break;
+  }
+  if (O.pca_eps > 0.0 && !chosen.empty()) {
+    // step 3: the bases become the principal components of the selected
+    // snapshots' restrictions (written over the cap layout of Phi)
+    const int n = (int)chosen.size();
+    if (n > kMaxPcaSnap) return lrbms_internal_fail(ctx, LRBMS_E_FORMAT, "compression: more than 256 snapshots");
+    double* Qs = B.get<double>((size_t)n_sub * n * rows);
+    double* Rts = B.get<double>((size_t)n_sub * n * n);
+    double* Ws = B.get<double>((size_t)n_sub * n * n);
+    int* didx = B.get<int>(n);
+    PcaJob* dpj = B.get<PcaJob>(n_sub);
+    if (!Qs || !Rts || !Ws || !didx || !dpj) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "compression buffers");
+    std::vector<PcaJob> jobs_pca(n_sub);
+    for (int E = 0; E < n_sub; ++E)
+      jobs_pca[E] = PcaJob{p, E, n, cap[E], dsnap, didx, Qs + (size_t)E * n * rows, Rts + (size_t)E * n * n,
+                           Ws + (size_t)E * n * n, Phi + phioff[E], dgot + E, O.pca_eps};
+    BCK(cudaMemcpyAsync(didx, chosen.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(dpj, jobs_pca.data(), sizeof(PcaJob) * n_sub, cudaMemcpyHostToDevice, st));
+    k_pca<<<(unsigned)n_sub, 256, 8 * (size_t)rows, st>>>(d_fd, dpj);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(cur.data(), dgot, 4 * (size_t)n_sub, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    for (int E = 0; E < n_sub; ++E)
+      if (cur[E] < 1) return lrbms_internal_fail(ctx, LRBMS_E_FORMAT, "compression: a subdomain kept no mode");
   }
   if (O.history) {
     const int nh = std::min((int)hist.size(), O.max_history);

@@ -39,7 +39,7 @@ LRBMS_TRANSPORT_DG1 = 1
 LRBMS_SOLVE_FP64 = 0
 LRBMS_SOLVE_MIXED = 1
 FIELD_THETA, FIELD_A, FIELD_RHS, FIELD_X, FIELD_P, FIELD_FLUX, FIELD_S, FIELD_DT, FIELD_STATUS, FIELD_SOLVE_INFO, \
-    FIELD_SLOPES = range(11)
+    FIELD_SLOPES, FIELD_PHI = range(12)
 
 EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offline_build",
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
@@ -83,7 +83,7 @@ class BuildOpts(C.Structure):
     _fields_ = [("M", C.c_int), ("n_steps_T", C.c_int), ("N_E", C.c_void_p), ("n_snap", C.c_int),
                 ("mu", C.c_void_p), ("c_pen", C.c_double), ("allow_fewer", C.c_int), ("greedy", C.c_int),
                 ("greedy_tol", C.c_double), ("mu_bar", C.c_void_p), ("history", C.c_void_p),
-                ("max_history", C.c_int), ("n_history", C.c_void_p)]
+                ("max_history", C.c_int), ("n_history", C.c_void_p), ("pca_eps", C.c_double)]
 
 
 _lib = None
@@ -182,7 +182,9 @@ def _problem_struct(problem: dict, keep: dict) -> Problem:
 
 def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return_sizes=False):
     """Build offline data on the GPU for each problem (dicts as for
-    lrbms_offline_load; opts: dicts with M, n_steps_T, N_E, mu, c_pen) and
+    lrbms_offline_load; opts: dicts with M, n_steps_T, N_E, mu, c_pen and
+    optionally allow_fewer, greedy, greedy_tol, mu_bar, history, n_history,
+    pca_eps) and
     admit n_copies simulations per problem. rot: optional list (len
     n_prob*n_copies) of concatenated per-subdomain orthogonal matrices or
     None entries. Returns the simulation ids."""
@@ -201,7 +203,8 @@ def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return
         keep[id(mub)] = mub
         ol.append(BuildOpts(o["M"], o["n_steps_T"], _ptr(ne), mu.shape[0], _ptr(mu), o["c_pen"],
                             int(o.get("allow_fewer", 0)), int(o.get("greedy", 0)), float(o.get("greedy_tol", 0.0)),
-                            _ptr(mub), _ptr(hist), 0 if hist is None else len(hist), _ptr(nh)))
+                            _ptr(mub), _ptr(hist), 0 if hist is None else len(hist), _ptr(nh),
+                            float(o.get("pca_eps", 0.0))))
     oarr = (BuildOpts * n)(*ol)
     rp = None
     if rot is not None:
