@@ -57,6 +57,8 @@ def parse_args():
                     help="mixed solver: steps one FP32 factor serves (0: the library default)")
     ap.add_argument("--horizon", type=int, default=300, help="steps per simulation (warm-up + timed)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="oracle processes of the CPU baseline (0: host cores - 2, at most 16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0)
     ap.add_argument("--kernels-only", action="store_true",
@@ -105,18 +107,26 @@ def penalty_scale(prob) -> float:
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def cpu_baseline_worker(args_dict, q):
+def cpu_baseline_worker(args_dict, q, worker: int = 0):
     """Time the CPU oracle's online step (as it stands) on one simulation of
-    the same workload, for about cpu_seconds of work."""
+    the same workload (physical dataset worker mod n_prob), single-threaded,
+    for about cpu_seconds of work."""
     try:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
         import numpy as np
         from types import SimpleNamespace
         a = SimpleNamespace(**args_dict)
+        try:
+            from threadpoolctl import threadpool_limits
+            threadpool_limits(1)
+        except Exception:
+            pass
         from oracle.grid import Coarse
         from oracle.impes import FineModel
         from oracle.offline import build_offline
         from oracle.reduced import online_step
-        prob, N_E, mu, _ = problem_inputs(a, 0)
+        prob, N_E, mu, _ = problem_inputs(a, worker % a.n_prob)
         m = FineModel.from_problem(prob, c_pen=penalty_scale(prob))
         co = Coarse(m.grid, prob.Sx, prob.Sy)
         t0 = time.perf_counter()
@@ -131,27 +141,52 @@ def cpu_baseline_worker(args_dict, q):
             n += 1
             if time.perf_counter() - t0 >= a.cpu_seconds:
                 break
-        el = time.perf_counter() - t0
-        try:
-            from threadpoolctl import threadpool_info
-            cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-        except Exception:
-            cores = os.cpu_count()
-        q.put(dict(value=n / el, unit="sim-steps/s", cores=int(cores), kind="oracle",
-                   sample=f"{n} online steps of 1 simulation of the same workload "
-                          f"(N={int(off.N)}), NumPy/SciPy FP64; offline build {t_off:.1f} s not timed",
-                   seconds=el))
+        q.put(dict(n=n, seconds=time.perf_counter() - t0, N=int(off.N), t_off=t_off, worker=worker))
     except Exception as e:  # report, do not hide
-        q.put(dict(error=repr(e)))
+        q.put(dict(error=repr(e), worker=worker))
+
+
+def cpu_workers(a) -> int:
+    return a.cpu_workers if a.cpu_workers > 0 else max(1, min(16, (os.cpu_count() or 1) - 2))
 
 
 def start_cpu_baseline(a):
+    """One spawned single-threaded oracle process per worker, each stepping
+    its own simulation (processes, not threads: NumPy's small operations do
+    not scale with BLAS threads)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=cpu_baseline_worker, args=(vars(a), q), daemon=True)
-    p.start()
-    return p, q
+    procs = [ctx.Process(target=cpu_baseline_worker, args=(vars(a), q, w), daemon=True)
+             for w in range(cpu_workers(a))]
+    for p in procs:
+        p.start()
+    return procs, q
+
+
+def collect_cpu_baseline(cpu, timeout: float = 900.0) -> dict:
+    """Whole-host oracle throughput: the sum over the workers of their online
+    steps per second."""
+    procs, q = cpu
+    res = []
+    t_end = time.time() + timeout
+    while len(res) < len(procs) and time.time() < t_end:
+        try:
+            res.append(q.get(timeout=max(1.0, t_end - time.time())))
+        except Exception:
+            break
+    for p in procs:
+        p.join(timeout=5)
+    bad = [r for r in res if "error" in r]
+    if bad or len(res) < len(procs):
+        return {"error": bad[0]["error"] if bad else f"{len(procs) - len(res)} oracle workers did not finish"}
+    value = sum(r["n"] / r["seconds"] for r in res)
+    n = sum(r["n"] for r in res)
+    return dict(value=value, unit="sim-steps/s", cores=len(res), kind="oracle",
+                sample=f"{len(res)} single-threaded processes, one simulation each of the same workload "
+                       f"(N = {min(r['N'] for r in res)}..{max(r['N'] for r in res)}), {n} online steps in "
+                       f"about {res[0]['seconds']:.0f} s each, NumPy/SciPy FP64; offline builds "
+                       f"(about {max(r['t_off'] for r in res):.0f} s) not timed")
 
 
 # ------------------------------------------------------------------ clocks
@@ -281,22 +316,18 @@ def job_throughput(n_sims: int, steps: int, seconds: float, world: int) -> float
 def run_reference(a, rank: int, world: int):
     if rank != 0:
         return
-    import multiprocessing as mp
-    p, q = start_cpu_baseline(a)
-    p.join()
-    r = q.get() if not q.empty() else {"error": "no result"}
+    r = collect_cpu_baseline(start_cpu_baseline(a))
     if "error" in r:
         print(json.dumps({"impl": "reference", "unavailable": f"oracle baseline failed: {r['error']}"}))
         return
     line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / r["value"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "sample": "one simulation (CPU)"},
+            "config": {"workload": workload_name(a), "sample": r["sample"]},
             "cpu_baseline": {"value": r["value"], "unit": r["unit"], "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
-    _ = mp
 
 
 SERVE_SHAPES = ((64, 4), (64, 8), (64, 16), (128, 8), (128, 16))  # (grid n, subdomains S), n / S >= 4
@@ -617,9 +648,7 @@ def main():
 
     cpu_line = None
     if cpu is not None:
-        proc, q = cpu
-        proc.join(timeout=900)
-        r = q.get() if not q.empty() else {"error": "cpu baseline did not finish"}
+        r = collect_cpu_baseline(cpu)
         cpu_line = r if "error" in r else {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
