@@ -204,6 +204,25 @@ def initial_profiles(model: FineModel, s0: np.ndarray, n_steps: int, M: int):
     return dict(p0=p0, F0=F0, tau=tau, T=T, P=P, idx=idx, lam0=lam0, lam1=lam1)
 
 
+def saturation_profiles(model: FineModel, s0: np.ndarray, n_steps: int, M: int) -> np.ndarray:
+    """Section 6 variant of Algorithm 2, step 1(c): the profiles are the
+    mobilities of M high-dimensional saturations, Lambda^q = lambda(s_h^{n_q})
+    (each phase's lambda_alpha^q = lambda_alpha(s_h^{n_q}), summed), taken
+    along the fine scheme of Algorithm 1 started at s0. Reading: the paper
+    does not space the times t^q; here n_q = round((q - 1) n_steps / (M - 1)),
+    q = 1..M, so t^1 = 0 and t^M is the end of the n_steps-step run."""
+    P = np.empty((M, model.grid.n_cells))
+    s = np.array(s0, dtype=np.float64)
+    n = 0
+    for q in range(M):
+        nq = int(round(q * n_steps / (M - 1)))
+        while n < nq:
+            s = model.step(s)["s"]
+            n += 1
+        P[q] = model.mobility(s)
+    return P
+
+
 def fine_solution(model: FineModel, P: np.ndarray, mu: np.ndarray) -> np.ndarray:
     """High-dimensional pressure for the mobility sum_q mu_q Lambda^q (Definition 1)."""
     return model.solve_pressure(mu @ P)
