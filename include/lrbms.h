@@ -307,6 +307,13 @@ typedef struct {
                         total, singular values at most n eps_64 sigma_1 counted
                         as 0; 0: no compression. LRBMS_E_FORMAT if a subdomain
                         keeps no mode                                          */
+  const double* prof_s; /* [M][n_cells] saturations s_1..s_M (host or device), or
+                        NULL. Given, the mobility profiles are Lambda^q =
+                        lambda(s_q), stored dense, instead of the
+                        time-of-flight thresholds of Algorithm 2 step 1(c):
+                        the variant of Section 6 with high-dimensional
+                        saturation snapshots (for example states advanced by
+                        lrbms_fine_step). n_steps_T is then unused          */
 } lrbms_build_opts;
 
 /* Build the offline data of n_prob problems (same grids, one options entry

@@ -252,7 +252,9 @@ def greedy_bases(model: FineModel, coarse: Coarse, P: np.ndarray, ops: FineOpera
             errs[t] = np.sqrt(max(diff @ (Kbar @ diff), 0.0))
         k = int(np.argmax(errs))
         history.append(float(errs[k]))
-        if errs[k] <= tol or sum(len(b) for b in Phi) >= N_max:
+        # step 2(g): go on only while |Xi| < N_max, here also while some
+        # subdomain is below its cap (N_max read as the sum of the caps)
+        if errs[k] <= tol or sum(len(b) for b in Phi) >= N_max or all(len(b) >= cap for b in Phi):
             break
         chosen.append(k)  # the snapshot set Psi of step 2(d)
         grew = False

@@ -1301,7 +1301,7 @@ __device__ __noinline__ double dot_strided(const double* __restrict__ a, int sa,
   return (acc + a1) + (a2 + a3);
 }
 
-// r = b - A x with the block-sparse assembled A, in FP64, by the CTA
+// r = b - A x (r = A x when b is null) with the block-sparse assembled A, in FP64, by the CTA
 // (subdomain E to warp E mod kNW); x is staged in the shared work area xs [N].
 // p = floor(32 / N_E) lanes share a row: lane q N_E + i takes the columns
 // c = q (mod p) of row i and the partial sums meet by shuffles, so that the
@@ -1351,7 +1351,7 @@ __device__ void cresidual(const SimDev& S, const SolveMeta& mt, const double* x,
       const double v = __shfl_sync(0xffffffffu, acc, (lane + u * NE) & 31);
       if (q == 0) acc += v;
     }
-    if (q == 0) r[x0 + i] = b[x0 + i] - acc;
+    if (q == 0) r[x0 + i] = b ? b[x0 + i] - acc : acc;
   }
   __syncthreads();
 }
@@ -1370,6 +1370,20 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
   return r;
 }
 
+// sum over the CTA of v in a fixed order (bitwise reproducible); red: [kNW] doubles.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = red[0];
+#pragma unroll
+  for (int u = 1; u < kNW; ++u) r += red[u];
+  __syncthreads();
+  return r;
+}
+
 // x = (L L^T)^-1 b, then up to `iters` refinement steps x += (L L^T)^-1 (b - A x)
 // with the residual in FP64 (max norms throughout; ||dv_0|| := ||x_0||). The
 // refinement stops
@@ -1381,12 +1395,8 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
 //  - stalled: a correction that no longer halves above that level (the
 //    factor is too inexact for this matrix; the FP32 kernel then hands the
 //    simulation to the FP64 one).
-// Warm start (warm = true): x already holds the previous step's solution of
-// a nearby system, and every pass is a correction pass x += (L L^T)^-1 (b - A x);
-// the first correction is accepted only if it is itself below kRefineTol ||x||
-// (its size says nothing about the contraction yet).
-// Returns kRefOk, kRefStalled, kRefTimeout (a copy did not complete) or, warm
-// only, kRefNotConverged (the pass budget ran out before convergence).
+// Returns kRefOk, kRefStalled or kRefTimeout (a copy did not complete). The
+// warm-started mixed solve uses csolve_pcg instead.
 // Per-simulation solve bookkeeping (S.info, ints): [0] correction passes of
 // the last solve, [1] FP64 redos, [2] FP32 factorisations, [3] refactorings
 // forced by a stale factor that did not converge, [4] correction passes,
@@ -1399,17 +1409,15 @@ constexpr double kFloorTol = 1e-8;
 constexpr int kRefOk = 0, kRefStalled = 1, kRefTimeout = 2, kRefNotConverged = 3;
 
 template <typename T>
-__device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m,
-                             bool warm = false) {
+__device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
   double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
   double prev = 0.0;
-  int steps = 0, rc = warm ? kRefNotConverged : kRefOk;
-  // cold: pass 0 solves for x, pass it >= 1 for the correction dv of
-  // refinement step it; warm: every pass is a correction (one substitution
-  // call site keeps the kernel's code small)
+  int steps = 0, rc = kRefOk;
+  // pass 0 solves for x, pass it >= 1 for the correction dv of refinement
+  // step it (one substitution call site keeps the kernel's code small)
 #pragma unroll 1
   for (int it = 0; it <= iters; ++it) {
-    const bool corr = warm || it > 0;
+    const bool corr = it > 0;
     if (corr) cresidual(S, m.mt, S.x, S.b, S.rv, reinterpret_cast<double*>(m.yz));
     if (!csubstitute<T>(S, Lst, Linv, corr ? S.rv : S.b, corr ? S.dv : S.x, m)) return kRefTimeout;
     double mdv = 0.0, mx = 0.0;
@@ -1429,14 +1437,13 @@ __device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int i
       prev = mx;
       continue;
     }
-    steps = warm ? it + 1 : it;
-    const bool first = warm && it == 0;
-    const double pred = first ? mdv : mdv * fmin(1.0, mdv / prev);
+    steps = it;
+    const double pred = mdv * fmin(1.0, mdv / prev);
     if (!(pred > kRefineTol * mx)) {  // converged (also on 0/0)
       rc = kRefOk;
       break;
     }
-    if (!first && mdv > 0.5 * prev) {
+    if (mdv > 0.5 * prev) {
       rc = mdv > kFloorTol * mx ? kRefStalled : kRefOk;
       break;
     }
@@ -1444,7 +1451,81 @@ __device__ int csolve_refine(const SimDev& S, const T* Lst, const T* Linv, int i
   }
   if (threadIdx.x == 0 && S.info) {
     S.info[kInfoPasses] = steps;
-    S.info[kInfoPassSum] += steps + (warm ? 0 : 1);  // every substitution pass
+    S.info[kInfoPassSum] += steps + 1;  // every substitution pass
+  }
+  return rc;
+}
+
+// Warm-started preconditioned conjugate gradients in FP64 with the FP32
+// Cholesky factor L L^T (of this step or an earlier one) as the
+// preconditioner: from the guess x, r = b - A x; then per pass
+// z = (L L^T)^-1 r, rho = r.z, p = z + (rho / rho_prev) p (p = z first),
+// q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q. A changes between
+// steps only through the fitted mobility coefficients, so the spectrum of
+// (L L^T)^-1 A stays clustered near 1 and the iteration needs fewer passes
+// than plain refinement (x += (L L^T)^-1 (b - A x)), most of all with a
+// stale factor. Stops like csolve_refine (the correction alpha p in max norm,
+// predicted from the last two; the first accepted only if itself below
+// kRefineTol ||x||) after at most iters + 1 passes. Returns kRefOk,
+// kRefTimeout, kRefStalled (p.q or r.z not positive: the preconditioned
+// operator is not positive definite in this precision) or kRefNotConverged.
+// Work vectors: S.rv (r), S.dv (z), S.pv (p), S.qv (q).
+template <typename T>
+__device__ int csolve_pcg(const SimDev& S, const T* Lst, const T* Linv, int iters, CtaSmem<T>& m) {
+  double* red = reinterpret_cast<double*>(m.part);  // [kNW] doubles (part is free between passes)
+  double* xs = reinterpret_cast<double*>(m.yz);
+  cresidual(S, m.mt, S.x, S.b, S.rv, xs);
+  double rho = 0.0, prev = 0.0;
+  int steps = 0, rc = kRefNotConverged;
+#pragma unroll 1
+  for (int it = 0; it <= iters; ++it) {
+    if (!csubstitute<T>(S, Lst, Linv, S.rv, S.dv, m)) return kRefTimeout;
+    double acc = 0.0;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < S.N; i += kThreads) acc = fma(S.rv[i], S.dv[i], acc);
+    const double rn = cta_sum(acc, red);
+    if (!(rn > 0.0)) {  // r = 0: x is exact; otherwise not positive definite
+      rc = rn == 0.0 ? kRefOk : kRefStalled;
+      break;
+    }
+    const double beta = it == 0 ? 0.0 : rn / rho;
+    rho = rn;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < S.N; i += kThreads) S.pv[i] = it == 0 ? S.dv[i] : fma(beta, S.pv[i], S.dv[i]);
+    __syncthreads();
+    cresidual(S, m.mt, S.pv, nullptr, S.qv, xs);
+    acc = 0.0;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < S.N; i += kThreads) acc = fma(S.pv[i], S.qv[i], acc);
+    const double pq = cta_sum(acc, red);
+    steps = it + 1;
+    if (!(pq > 0.0) || !(pq < INFINITY)) {
+      rc = kRefStalled;
+      break;
+    }
+    const double al = rho / pq;
+    double mdv = 0.0, mx = 0.0;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < S.N; i += kThreads) {
+      const double d = al * S.pv[i];
+      const double xi = S.x[i] + d;
+      S.x[i] = xi;
+      S.rv[i] = fma(-al, S.qv[i], S.rv[i]);
+      mdv = fmax(mdv, fabs(d));
+      mx = fmax(mx, fabs(xi));
+    }
+    mdv = cta_max(mdv, red);
+    mx = cta_max(mx, red);
+    const double pred = it == 0 ? mdv : mdv * fmin(1.0, mdv / prev);
+    if (!(pred > kRefineTol * mx)) {
+      rc = kRefOk;
+      break;
+    }
+    prev = mdv;
+  }
+  if (threadIdx.x == 0 && S.info) {
+    S.info[kInfoPasses] = steps;
+    S.info[kInfoPassSum] += steps;
   }
   return rc;
 }
@@ -1453,13 +1534,14 @@ constexpr int kStRetry64 = 1;  // transient status: redo this simulation's solve
 constexpr int kStRetry32 = 2;  // transient status: refactor in FP32 now and solve again
 
 // The FP32 factor of an earlier step serves as the preconditioner of the
-// refinement (A changes only through the fitted mobility coefficients, so
-// the factor of a nearby step still contracts) for refactor_period steps; then
+// conjugate gradients (A changes only through the fitted mobility
+// coefficients, so the factor of a nearby step still clusters the spectrum
+// near 1) for refactor_period steps; then
 // the simulation refactors. Simulations loaded together therefore refactor on
 // the same steps, which keeps the refinement passes of a launch even (a
 // launch lasts as long as its slowest simulation). A step that needs more than
-// kRefactorPasses correction passes also refactors at the next step. The warm
-// refinement gets at most kStalePasses passes (or refine_iters + 1 if more);
+// kRefactorPasses passes also refactors at the next step. The warm solve
+// gets at most kStalePasses passes (or refine_iters + 1 if more);
 // a stale factor that has not converged by then, or stalls, is recomputed at
 // once (kStRetry32); a fresh one hands the solve to FP64.
 constexpr int kRefactorPasses = 10;
@@ -1521,8 +1603,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restri
   const bool fresh = S.info[kInfoAge] == 1;
   const int budget = max(iters, kStalePasses - 1);
   extrapolate_guess(S);
-  const int r = csolve_refine<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
-                                     budget, m, true);
+  const int r = csolve_pcg<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
+                                  budget, m);
   if (threadIdx.x == 0) {
     if (r == kRefOk) {
       S.info[kInfoSolves] += 1;

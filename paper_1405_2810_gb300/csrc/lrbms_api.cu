@@ -355,7 +355,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
                o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces), o_fwD = L.add(8 * (size_t)nb);
   const size_t o_x = L.add(8 * (size_t)N), o_xp = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N),
                o_y = L.add(16 * (size_t)N),
-               o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N);
+               o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N), o_pv = L.add(8 * (size_t)N),
+               o_qv = L.add(8 * (size_t)N);
   const size_t o_A = L.add(8 * (size_t)a_tot);
   const size_t o_L = L.add(8 * (size_t)loff[n_sub]), o_Li = L.add(8 * (size_t)ioff[n_sub]);
   const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
@@ -405,7 +406,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.sunl = dg ? (double*)P(o_unl) : nullptr;
   d.x = (double*)P(o_x); d.xp = (double*)P(o_xp); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
   d.refactor_period = ctx->refactor_period;
-  d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv);
+  d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv); d.pv = (double*)P(o_pv); d.qv = (double*)P(o_qv);
   d.A = (double*)P(o_A); d.L = (double*)P(o_L); d.Linv = (double*)P(o_Li);
   d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
   d.scal = (double*)P(o_scal); d.theta = (double*)P(o_theta);

@@ -86,7 +86,9 @@ struct SimDev {
   double* b;        // [N]
   double* y;        // [2N] substitution work (forward result, then backward result)
   double* rv;       // [N] refinement residual
-  double* dv;       // [N] refinement correction
+  double* dv;       // [N] refinement correction (conjugate gradients: preconditioned residual)
+  double* pv;       // [N] conjugate gradients: search direction (mixed solver)
+  double* qv;       // [N] conjugate gradients: A times the search direction
   double* A;        // [aoff[n_blocks]]
   double* L;        // [loff[n_sub]]
   double* Linv;     // [ioff[n_sub]]

@@ -38,6 +38,7 @@ struct FineDev {
   const double* s_D;
   const double* s0;
   uint8_t* prof_idx;
+  const double* prof;  // [M][n_cells] dense profiles (saturation-snapshot variant), or null
 };
 
 // One fine system to assemble: mobility gamma per cell given by
@@ -62,6 +63,12 @@ __device__ __forceinline__ double mob_total(const FineDev& f, double s) {
 
 __device__ __forceinline__ double job_gamma(const FineDev& f, const SysJob& J, int e) {
   if (J.mode == 0) return mob_total(f, f.s0[e]);
+  if (f.prof) {
+    if (J.mode == 2) return f.prof[(size_t)J.q * f.n_cells + e];
+    double g = 0.0;
+    for (int q = 0; q < f.M; ++q) g += J.mu[q] * f.prof[(size_t)q * f.n_cells + e];
+    return g;
+  }
   const int k = f.prof_idx[e];
   if (J.mode == 2) return (J.q + 1 >= k) ? f.lam1 : f.lam0;
   double g = 0.0;
@@ -319,6 +326,15 @@ __global__ void k_tof_sweep(const FineDev* __restrict__ fds, double* const* __re
 
 // Profile index (Algorithm 2, step 1(c)): first q in 2..M-1 with
 // tau <= (q-1) T/(M-2), else M; and a histogram of the indices.
+// Dense profiles of the saturation-snapshot variant (Section 6): the
+// saturations s_q [M][n_cells] are replaced in place by lambda(s_q).
+__global__ void k_sat_profiles(const FineDev* __restrict__ fds, int prob, double* __restrict__ P) {
+  const FineDev& f = fds[prob];
+  const size_t n = (size_t)f.M * f.n_cells;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    P[i] = mob_total(f, P[i]);
+}
+
 __global__ void k_profiles(FineDev* fds, double* const* __restrict__ taus, const double* T,
                            unsigned int* hist) {
   FineDev& f = fds[blockIdx.y];
@@ -1280,7 +1296,7 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
       return lrbms_internal_fail(ctx, LRBMS_E_ARG, "all problems of one build must share the grids");
     if (nx < 2 || ny < 2 || nx % Sx || ny % Sy)
       return lrbms_internal_fail(ctx, LRBMS_E_ARG, "grid must be at least 2x2 and match the subdomains");
-    if (O.M < 3 || O.M > kMaxM || O.n_snap < 0 || (O.n_snap && !O.mu) || !O.N_E || O.n_steps_T < 1 ||
+    if (O.M < 3 || O.M > kMaxM || O.n_snap < 0 || (O.n_snap && !O.mu) || !O.N_E || (O.n_steps_T < 1 && !O.prof_s) ||
         !(O.c_pen > 0))
       return lrbms_internal_fail(ctx, LRBMS_E_ARG, "bad build options");
   }
@@ -1316,10 +1332,22 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
     BCK(cudaMemcpyAsync(sD, P.s_D, 8 * (size_t)nb, cudaMemcpyDefault, st));
     f.perm = perm; f.poro = poro; f.s0 = s0; f.bc_type = bct; f.p_D = pD; f.v_N = vN; f.s_D = sD;
     f.prof_idx = pidx;
+    f.prof = nullptr;
+    if (opts[p].prof_s) {  // saturation snapshots: lambda(s_q) after the FineDev table is on the device
+      double* pr = B.get<double>((size_t)f.M * n_cells);
+      if (!pr) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the profiles");
+      BCK(cudaMemcpyAsync(pr, opts[p].prof_s, 8 * (size_t)f.M * n_cells, cudaMemcpyDefault, st));
+      f.prof = pr;
+    }
   }
   FineDev* d_fd = B.get<FineDev>(n_prob);
   if (!d_fd) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "device memory for the offline build");
   BCK(cudaMemcpyAsync(d_fd, fd.data(), sizeof(FineDev) * n_prob, cudaMemcpyHostToDevice, st));
+  for (int p = 0; p < n_prob; ++p)
+    if (fd[p].prof) {
+      k_sat_profiles<<<152, 256, 0, st>>>(d_fd, p, const_cast<double*>(fd[p].prof));
+      BCK(cudaGetLastError());
+    }
 
   auto run_systems = [&](std::vector<SysJob>& jobs) -> int {
     SysJob* dj = B.get<SysJob>(jobs.size());
@@ -1408,6 +1436,18 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
   for (int p = 0; p < n_prob; ++p) {
     const int M = opts[p].M;
     std::vector<double> G(M * M, 0.0);
+    if (fd[p].prof) {  // dense profiles: G = P P^T summed over the cells in order
+      std::vector<double> P((size_t)M * n_cells);
+      BCK(cudaMemcpy(P.data(), fd[p].prof, 8 * P.size(), cudaMemcpyDeviceToHost));
+      for (int a = 0; a < M; ++a)
+        for (int b = 0; b < M; ++b) {
+          double g = 0.0;
+          for (int e = 0; e < n_cells; ++e) g += P[(size_t)a * n_cells + e] * P[(size_t)b * n_cells + e];
+          G[a * M + b] = g;
+        }
+      sym_pinv(M, G, Gp[p]);
+      continue;
+    }
     for (int k = 1; k <= M; ++k) {
       const double n = hist[p * (kMaxM + 1) + k];
       if (n == 0) continue;
@@ -1627,8 +1667,8 @@ extern "C" int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_probl
       lrbms_offline off{};
       off.M = opts[p].M;
       off.N_E = dne;
-      off.prof_idx = fd[p].prof_idx;
-      off.prof = nullptr;
+      off.prof_idx = fd[p].prof ? nullptr : fd[p].prof_idx;
+      off.prof = fd[p].prof;
       off.Gpinv = dGp;
       off.Phi = uPhi;
       off.Dblk = ucomp;

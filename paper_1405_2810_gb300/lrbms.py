@@ -83,7 +83,8 @@ class BuildOpts(C.Structure):
     _fields_ = [("M", C.c_int), ("n_steps_T", C.c_int), ("N_E", C.c_void_p), ("n_snap", C.c_int),
                 ("mu", C.c_void_p), ("c_pen", C.c_double), ("allow_fewer", C.c_int), ("greedy", C.c_int),
                 ("greedy_tol", C.c_double), ("mu_bar", C.c_void_p), ("history", C.c_void_p),
-                ("max_history", C.c_int), ("n_history", C.c_void_p), ("pca_eps", C.c_double)]
+                ("max_history", C.c_int), ("n_history", C.c_void_p), ("pca_eps", C.c_double),
+                ("prof_s", C.c_void_p)]
 
 
 _lib = None
@@ -184,7 +185,7 @@ def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return
     """Build offline data on the GPU for each problem (dicts as for
     lrbms_offline_load; opts: dicts with M, n_steps_T, N_E, mu, c_pen and
     optionally allow_fewer, greedy, greedy_tol, mu_bar, history, n_history,
-    pca_eps) and
+    pca_eps, prof_s) and
     admit n_copies simulations per problem. rot: optional list (len
     n_prob*n_copies) of concatenated per-subdomain orthogonal matrices or
     None entries. Returns the simulation ids."""
@@ -201,10 +202,12 @@ def lrbms_offline_build(ctx, problems, opts, n_copies: int = 1, rot=None, return
         hist = o.get("history")  # a float64 NumPy array to fill, or None
         nh = o.get("n_history")  # a one-element int32 NumPy array, or None
         keep[id(mub)] = mub
+        ps = None if o.get("prof_s") is None else _as(o["prof_s"], np.float64)
+        keep[id(ps)] = ps
         ol.append(BuildOpts(o["M"], o["n_steps_T"], _ptr(ne), mu.shape[0], _ptr(mu), o["c_pen"],
                             int(o.get("allow_fewer", 0)), int(o.get("greedy", 0)), float(o.get("greedy_tol", 0.0)),
                             _ptr(mub), _ptr(hist), 0 if hist is None else len(hist), _ptr(nh),
-                            float(o.get("pca_eps", 0.0))))
+                            float(o.get("pca_eps", 0.0)), _ptr(ps)))
     oarr = (BuildOpts * n)(*ol)
     rp = None
     if rot is not None:
