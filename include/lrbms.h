@@ -94,26 +94,26 @@ typedef struct {
   int device;        /* CUDA device ordinal                                 */
   int solver;        /* reduced solve: LRBMS_SOLVE_FP64 (FP64 block Cholesky
                         every step, FP64 substitutions) or LRBMS_SOLVE_MIXED
-                        (FP32 block Cholesky and substitutions, iterative
-                        refinement with FP64 residuals and updates, warm-
-                        started from the previous steps' solutions; the FP32
-                        factor of an earlier step is reused for
-                        refactor_period steps, or until a step needs more
-                        than 10 correction passes; a reused factor that has
-                        not converged after 12 passes is recomputed at
-                        once; a solve whose fresh FP32 factorisation meets a
-                        non-positive pivot, or whose refinement stops
-                        contracting above 1e-8 of the solution, is redone
-                        in FP64)                                            */
+                        (FP32 block Cholesky and substitutions; conjugate
+                        gradients in FP64 preconditioned by the FP32
+                        factor, warm-started from the previous steps'
+                        solutions; the FP32 factor of an earlier step is
+                        reused for refactor_period steps, or until a step
+                        needs more than 10 passes; a reused factor that has
+                        not converged after 12 passes is recomputed at once
+                        and the solve repeated with FP64-residual
+                        refinement; a solve whose fresh FP32 factorisation
+                        meets a non-positive pivot, or whose iteration stops
+                        converging, is redone in FP64)                     */
   int refine_iters;  /* FP64: most refinement steps after the first solve;
-                        MIXED: most correction passes of a step minus one
-                        (at least 11). 0: default (1 for FP64, 6 for MIXED);
-                        at most 16. The refinement stops early once the next
+                        MIXED: most passes of a step minus one (at least
+                        11). 0: default (1 for FP64, 6 for MIXED); at most
+                        16. The iteration stops early once the next
                         correction, predicted from the last two, is below
-                        1e-12 of the solution, or once a correction no
-                        longer halves (max norms)                           */
+                        1e-12 of the solution (max norms); the FP64
+                        refinement also once a correction no longer halves */
   int refactor_period; /* MIXED: steps one FP32 factor serves before the
-                        simulation refactors (1: every step); 0: default 3.
+                        simulation refactors (1: every step); 0: default 6.
                         The first guess of each solve is the linear
                         extrapolation of the last two solutions            */
 } lrbms_config;
