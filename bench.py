@@ -245,7 +245,7 @@ class ClockSampler:
 def solve_flops(N_E, Sx: int) -> tuple:
     """Flops of the reduced solve per simulation, as implemented: the envelope
     block Cholesky (with the products by the diagonal inverses), one forward
-    and backward substitution pair, and one FP64 residual b - A x."""
+    and backward substitution pair, and one FP64 block mat-vec A x."""
     n = len(N_E)
     xoff = [0]
     for v in N_E:
@@ -614,15 +614,17 @@ def main():
     elem = 8 if a.precision == "fp64" else 4
     if names[dom] == "solve":
         # per simulation and step: FP32 factorisations x factor flops, substitution
-        # passes x (forward + backward) flops in the factor's type, and one FP64
-        # residual per correction pass (mixed; FP64: one residual per refinement)
+        # passes x (forward + backward) flops in the factor's type; mixed (conjugate
+        # gradients): the initial residual and one FP64 block mat-vec per pass, plus
+        # the pass's two dot products and three vector updates (10 N); FP64: one
+        # residual per refinement
         f_lo = f_hi = 0.0
         for k, sz in enumerate(sizes):
             fac, sub, res = solve_flops(list(sz), Sx)
             sl = slice(k * n_copies, (k + 1) * n_copies)  # ids are grouped by physical dataset
             if a.solver == "mixed":
                 f_lo += float(np.sum(factor_rate[sl] * fac + passes_per_solve[sl] * sub))
-                f_hi += float(np.sum(passes_per_solve[sl] * res))
+                f_hi += float(np.sum((passes_per_solve[sl] + 1) * res + passes_per_solve[sl] * 10.0 * float(sum(sz))))
             else:
                 f_hi += float(np.sum(fac + passes_per_solve[sl] * sub + (passes_per_solve[sl] - 1) * res))
         t_solve = phase_ms[dom] / 1000.0

@@ -226,7 +226,7 @@ def test_saturation_snapshot_profiles_match_oracle(L):
     step. The saturations are the oracle's fine states."""
     from oracle.offline import saturation_profiles
     prob, m, co, NE, mus = _setup()
-    n_steps = 8
+    n_steps = 48  # snapshots 7 steps apart: cond(P P^T) about 1e5 (8 steps in all: 4e9)
     P = saturation_profiles(m, prob.s0, n_steps, prob.M)
     states, s = [], prob.s0
     for n in range(n_steps + 1):
@@ -245,7 +245,7 @@ def test_saturation_snapshot_profiles_match_oracle(L):
         ref = online_step(m, off, s_q)
         th = L.lrbms_get_field(ctx, sid, L.FIELD_THETA)
         assert np.abs(th @ P - m.mobility(s_q)).max() <= 1e-10 * np.abs(P).max()  # exact fit
-        assert rel(th @ P, ref["theta"] @ P) < 1e-12
+        assert rel(th @ P, ref["theta"] @ P) < 1e-11
         assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_P), ref["p"].reshape(-1, 3).T.reshape(-1)) < 1e-7
         assert rel(L.lrbms_get_field(ctx, sid, L.FIELD_S), ref["s"]) < 1e-7
     L.lrbms_destroy(ctx)
