@@ -1301,57 +1301,53 @@ __device__ __noinline__ double dot_strided(const double* __restrict__ a, int sa,
   return (acc + a1) + (a2 + a3);
 }
 
-// r = b - A x (r = A x when b is null) with the block-sparse assembled A, in FP64, by the CTA
-// (subdomain E to warp E mod kNW); x is staged in the shared work area xs [N].
-// p = floor(32 / N_E) lanes share a row: lane q N_E + i takes the columns
-// c = q (mod p) of row i and the partial sums meet by shuffles, so that the
-// FP64 pipe sees p N_E of 32 lanes busy instead of N_E.
+// r = b - A x (r = A x when b is null) with the block-sparse assembled A, in
+// FP64, by the CTA; x is staged in the shared work area xs [N]. One thread
+// per row (rows g = threadIdx.x, + kThreads, ...; the row's subdomain by
+// binary search in xoff), so that every lane of a warp issues its FP64 FMAs
+// (rows of neighbouring subdomains share a warp): GB300's FP64 pipe bounds
+// this product. Row i of subdomain E sums, in this order, its diagonal block
+// (read down column i: the block is symmetric, and column i's elements are
+// consecutive across the threads of consecutive rows), the left and lower
+// couplings (stored [N_j][N_E]: column i, consecutive across rows) and the
+// right and upper ones (stored [N_E][N_j]: row i).
 __device__ void cresidual(const SimDev& S, const SolveMeta& mt, const double* x, const double* b, double* r,
                           double* xs) {
   const int Sx = S.Sx, Sy = S.Sy, nsub = S.n_sub;
-  const int lane = threadIdx.x & 31, w = vwarp();
   #pragma unroll 1
   for (int i = threadIdx.x; i < S.N; i += kThreads) xs[i] = x[i];
   __syncthreads();
   #pragma unroll 1
-  for (int E = w; E < nsub; E += kNW) {
-    const int NE = mt.NE[E], x0 = mt.xoff[E];
-    const int I = E % Sx, J = E / Sx;
-    const int p = 32 / NE;
-    const int q = lane / NE, i = lane - q * NE;
-    double acc = 0.0;
-    if (q < p) {
-      // columns c = q + p u of each block: element stride p times the column stride
-      const int d0 = (NE - q + p - 1) / p;
-      // diagonal block (symmetric: column i read coalesced)
-      acc = dot_strided(S.A + S.aoff[E] + i + (size_t)q * NE, p * NE, xs + x0 + q, p, d0, 0.0);
-      if (I > 0) {  // left neighbour: A_{E,E-1} = blk^T, blk [N_{E-1}][N_E]
-        const int j = E - 1, Nj = mt.NE[j];
-        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)] + i + (size_t)q * NE, p * NE,
-                          xs + mt.xoff[j] + q, p, (Nj - q + p - 1) / p, acc);
-      }
-      if (J > 0) {  // lower neighbour
-        const int j = E - Sx, Nj = mt.NE[j];
-        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + (J - 1) * Sx + I] + i + (size_t)q * NE, p * NE,
-                          xs + mt.xoff[j] + q, p, (Nj - q + p - 1) / p, acc);
-      }
-      if (I < Sx - 1) {  // right neighbour: A_{E,E+1} = blk [N_E][N_{E+1}]
-        const int j = E + 1, Nj = mt.NE[j];
-        acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + I] + (size_t)i * Nj + q, p, xs + mt.xoff[j] + q, p,
-                          (Nj - q + p - 1) / p, acc);
-      }
-      if (J < Sy - 1) {  // upper neighbour
-        const int j = E + Sx, Nj = mt.NE[j];
-        acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + J * Sx + I] + (size_t)i * Nj + q, p,
-                          xs + mt.xoff[j] + q, p, (Nj - q + p - 1) / p, acc);
-      }
-    }
+  for (int g = threadIdx.x; g < S.N; g += kThreads) {
+    int lo = 0, hi = nsub;  // xoff[lo] <= g < xoff[hi]
     #pragma unroll 1
-    for (int u = 1; u < p; ++u) {  // fixed order: q = 0, 1, ..., p-1
-      const double v = __shfl_sync(0xffffffffu, acc, (lane + u * NE) & 31);
-      if (q == 0) acc += v;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (mt.xoff[mid] <= g) lo = mid;
+      else hi = mid;
     }
-    if (q == 0) r[x0 + i] = b ? b[x0 + i] - acc : acc;
+    const int E = lo, NE = mt.NE[E], i = g - mt.xoff[E];
+    const int I = E % Sx, J = E / Sx;
+    double acc = dot_strided(S.A + S.aoff[E] + i, NE, xs + mt.xoff[E], 1, NE, 0.0);
+    if (I > 0) {
+      const int j = E - 1;
+      acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + (I - 1)] + i, NE, xs + mt.xoff[j], 1, mt.NE[j], acc);
+    }
+    if (J > 0) {
+      const int j = E - Sx;
+      acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + (J - 1) * Sx + I] + i, NE, xs + mt.xoff[j], 1, mt.NE[j],
+                        acc);
+    }
+    if (I < Sx - 1) {
+      const int j = E + 1, Nj = mt.NE[j];
+      acc = dot_strided(S.A + S.aoff[nsub + J * (Sx - 1) + I] + (size_t)i * Nj, 1, xs + mt.xoff[j], 1, Nj, acc);
+    }
+    if (J < Sy - 1) {
+      const int j = E + Sx, Nj = mt.NE[j];
+      acc = dot_strided(S.A + S.aoff[nsub + Sy * (Sx - 1) + J * Sx + I] + (size_t)i * Nj, 1, xs + mt.xoff[j], 1, Nj,
+                        acc);
+    }
+    r[g] = b ? b[g] - acc : acc;
   }
   __syncthreads();
 }
