@@ -782,15 +782,36 @@ __global__ void k_finalize(const SimDev* __restrict__ sims, const int* __restric
 }
 
 // Saturation exchange with caller memory (pinned host or device pointers).
+// The saturation of the next step read from caller memory (pinned host or
+// device, through unified addressing), tile by tile, together with what the
+// step's fit needs of it (lambda, f_w and the fit sums of Eq.
+// leastSquaresFit, as k_fit computes them), so that the step's k_fit skips.
 __global__ void k_sat_in(const SimDev* __restrict__ sims, const int* __restrict__ active,
                          const double* const* __restrict__ src) {
   const SimDev& S = sims[active[blockIdx.y]];
   const double* in = src[blockIdx.y];
-  if (!in) return;
+  const int tile = blockIdx.x;
+  if (!in || tile >= S.n_tiles) return;
   double* s = S.s + (size_t)(S.steps[0] & 1) * S.n_cells;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S.n_cells; e += gridDim.x * blockDim.x)
-    s[e] = in[e];
-  if (blockIdx.x == 0 && threadIdx.x == 0) S.fit_ready[0] = 0;  // the next step fits the new state
+  int e0, e1;
+  tile_range(S, tile, e0, e1);
+  if (S.status[0] != kStOk) {  // frozen: the state is still replaced, nothing is fitted
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) s[e] = in[e];
+    if (tile == 0 && threadIdx.x == 0) S.fit_ready[0] = 0;
+    return;
+  }
+  double acc[kMaxM];
+#pragma unroll
+  for (int q = 0; q < kMaxM; ++q) acc[q] = 0.0;
+  double* lam = S.lam + cur_half(S);
+  double* fw = S.fw + cur_half(S);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const double v = in[e];
+    s[e] = v;
+    fit_cell(S, v, e, lam, fw, acc);
+  }
+  fit_store(S, acc, tile);
+  if (tile == 0 && threadIdx.x == 0) S.fit_ready[0] = 1;  // every tile is done when the kernel ends
 }
 __global__ void k_sat_out(const SimDev* __restrict__ sims, const int* __restrict__ active,
                           double* const* __restrict__ dst) {
@@ -817,9 +838,9 @@ void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st) {
   k_to_float<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
 }
 
-void launch_sat_io(const SimDev* sims, const int* active, int n_active, const double* const* src,
+void launch_sat_io(const SimDev* sims, const int* active, int n_active, int max_tiles, const double* const* src,
                    double* const* dst, cudaStream_t st) {
-  if (src) k_sat_in<<<dim3(16, n_active), 256, 0, st>>>(sims, active, src);
+  if (src) k_sat_in<<<dim3(max_tiles, n_active), kCellThreads, 0, st>>>(sims, active, src);
   if (dst) k_sat_out<<<dim3(16, n_active), 256, 0, st>>>(sims, active, dst);
 }
 

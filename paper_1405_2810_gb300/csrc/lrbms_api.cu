@@ -677,14 +677,17 @@ int lrbms_step_io(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, const
     ptrs[ms + i] = s_out ? (const double*)s_out[i] : nullptr;
   }
   CK(cudaMemcpyAsync(ctx->d_io, ptrs.data(), sizeof(double*) * 2 * ms, cudaMemcpyHostToDevice, st));
+  int max_tiles = 1;
+  for (int i = 0; i < n_sims; ++i) max_tiles = std::max(max_tiles, ctx->slots[ids[i]].d.n_tiles);
   if (s_in) {
-    lrbms::launch_sat_io(ctx->d_sims, ctx->d_active, n_sims, ctx->d_io, nullptr, st);
+    lrbms::launch_sat_io(ctx->d_sims, ctx->d_active, n_sims, max_tiles, ctx->d_io, nullptr, st);
     ctx->launches += 1;
   }
   int rc = lrbms_step(ctx, n_sims, ids, n_steps, nullptr);
   if (rc) return rc;
   if (s_out) {
-    lrbms::launch_sat_io(ctx->d_sims, ctx->d_active, n_sims, nullptr, (double* const*)(ctx->d_io + ms), st);
+    lrbms::launch_sat_io(ctx->d_sims, ctx->d_active, n_sims, max_tiles, nullptr, (double* const*)(ctx->d_io + ms),
+                         st);
     ctx->launches += 1;
   }
   CK(cudaGetLastError());

@@ -189,7 +189,9 @@ void launch_transport_dg(const SimDev* sims, const int* active, int n_active, in
 void launch_finalize(const SimDev* sims, const int* active, int n_active, cudaStream_t st,
                      int* status_out = nullptr);
 void launch_to_float(const double* src, float* dst, size_t n, cudaStream_t st);
-void launch_sat_io(const SimDev* sims, const int* active, int n_active, const double* const* src,
+// Saturations in (src: also lambda, f_w and the fit sums of the new state)
+// and out, per active simulation; max_tiles: the largest n_tiles among them.
+void launch_sat_io(const SimDev* sims, const int* active, int n_active, int max_tiles, const double* const* src,
                    double* const* dst, cudaStream_t st);
 
 }  // namespace lrbms
