@@ -974,65 +974,46 @@ __device__ __forceinline__ void wring_release(WRing<T>& r) {
   else r.tpos = r.epos[r.b0 + (int)(r.consumed % (unsigned)kEnt)];
 }
 
-// The warp's own chunks, in consumption order. Iteration k owns, for the
-// leader: (a) the previous (forward) / next (backward) row's chunk at row k,
-// (b) the diagonal inverse of row k; for warp w > 0: the c-items i = w-1,
-// w-1+(kNW-1), ... (forward: rows k' = k+1+i at block k-1; backward: row k+1
-// at block j = jlo_{k+1}+i).
-struct SCursor {
-  int dir, k, sub;
-};
-
-__device__ __forceinline__ int n_citems(const SolveMeta& mt, int Sx, int nsub, int dir, int k) {
-  (void)mt;
-  if (dir > 0) return k >= 1 ? max(0, min(k - 1 + Sx, nsub - 1) - k) : 0;
-  return k <= nsub - 2 ? k - jlo_of(k + 1, Sx) : 0;
+// The chunks of the substitutions, per warp in consumption order. Block row
+// k (forward k = 0, 1, ..., then backward k = nsub-1, ..., 0) gives
+//  - the leader: the coupling block to the previous row (forward: panel k at
+//    block k-1) or to the next row (backward: panel k+1 at block k), then the
+//    diagonal inverse of row k;
+//  - warp w >= 1: its share of the C_k = xoff[k] - xoff[jlo(k+1)] columns of
+//    panel k+1 before block k (blocks jlo(k+1)..k-1, adjacent in the
+//    transposed panel), columns [C_k (w-1)/(kNW-1), C_k w/(kNW-1)), copied in
+//    pieces of at most pc columns, so that one copy usually carries all of a
+//    warp's blocks of the row. The forward pass uses them for row k+1's sum
+//    over those blocks, the backward pass for their update by z_{k+1}.
+// Each warp keeps kPartWords elements at the start of its FIFO region for
+// the forward partial sums (two rows of 32).
+constexpr int kPartWords = 64;
+__host__ __device__ inline int fifo_cap(int panel_words) {
+  return ((int)((round4((size_t)panel_words) + (size_t)kRing * kSlot) / kNW) & ~3) - kPartWords;
 }
-
-constexpr int kChNone = 0, kChPanel = 1, kChInverse = 2;
-__device__ int scursor_item(const SolveMeta& mt, int Sx, int nsub, int w, const SCursor& c, long long* off,
-                            int* cnt) {
-  const int k = c.k;
-  if (w == 0) {
-    const bool has_a = c.dir > 0 ? k >= 1 : k <= nsub - 2;
-    const int ia = has_a ? 0 : -1;
-    if (c.sub == ia) {
-      if (c.dir > 0) {  // panel k at block k-1: [g][c]
-        *off = mt.loff[k] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(k, Sx)]) * mt.NE[k];
-        *cnt = mt.NE[k - 1] * mt.NE[k];
-      } else {  // panel k+1 at block k
-        *off = mt.loff[k + 1] + (long long)(mt.xoff[k] - mt.xoff[jlo_of(k + 1, Sx)]) * mt.NE[k + 1];
-        *cnt = mt.NE[k] * mt.NE[k + 1];
-      }
-      return kChPanel;
-    }
-    if (c.sub == ia + 1) {
-      const int Nk = mt.NE[k];
-      *off = mt.ioff[k] + (c.dir > 0 ? ((Nk * Nk + 3) & ~3) : 0);
-      *cnt = Nk * Nk;
-      return kChInverse;
-    }
-    return kChNone;
+// Most columns of a piece for a row of n2 elements: half the FIFO, at least one column.
+__host__ __device__ inline int piece_cols(int panel_words, int n2) {
+  const int c = (fifo_cap(panel_words) / 2 - 4) / n2;
+  return c > 1 ? c : 1;
+}
+__device__ __forceinline__ void warp_share(const SolveMeta& mt, int Sx, int nsub, int w, int k, int* c0, int* c1) {
+  if (w == 0 || k + 1 >= nsub) {
+    *c0 = *c1 = 0;
+    return;
   }
-  const int i = (w - 1) + c.sub * (kNW - 1);
-  if (i >= n_citems(mt, Sx, nsub, c.dir, k)) return kChNone;
-  if (c.dir > 0) {
-    const int kk = k + 1 + i;
-    *off = mt.loff[kk] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(kk, Sx)]) * mt.NE[kk];
-    *cnt = mt.NE[k - 1] * mt.NE[kk];
-  } else {
-    const int jl1 = jlo_of(k + 1, Sx), j = jl1 + i;
-    *off = mt.loff[k + 1] + (long long)(mt.xoff[j] - mt.xoff[jl1]) * mt.NE[k + 1];
-    *cnt = mt.NE[j] * mt.NE[k + 1];
-  }
-  return kChPanel;
+  const int C = mt.xoff[k] - mt.xoff[jlo_of(k + 1, Sx)];
+  *c0 = (int)((long long)C * (w - 1) / (kNW - 1));
+  *c1 = (int)((long long)C * w / (kNW - 1));
 }
 
 // Chunk descriptor of the copy schedule: element offset (bits 0-39) into the
 // panels, or into the diagonal inverses if bit 63 is set; element count in
-// bits 40-50.
+// bits 40-55.
 constexpr unsigned long long kDescOffMask = (1ull << 40) - 1;
 constexpr unsigned long long kDescInverse = 1ull << 63;
+__device__ __forceinline__ unsigned long long sdesc(long long off, int cnt, bool inv) {
+  return (unsigned long long)off | ((unsigned long long)cnt << 40) | (inv ? kDescInverse : 0ull);
+}
 
 // The copy schedule of a simulation, by one thread: the word layout is that
 // of sched_words (list starts relative to the buffer, then the lists); the
@@ -1048,19 +1029,26 @@ __device__ void build_sched(const SimDev& S, unsigned long long* out) {
     out[w] = n;
     #pragma unroll 1
     for (int dir = 1; dir >= -1; dir -= 2) {
-      SCursor c{dir, dir > 0 ? 0 : nsub - 1, 0};
       #pragma unroll 1
-      while (dir > 0 ? c.k < nsub : c.k >= 0) {
-        long long off;
-        int cnt;
-        const int kind = scursor_item(mt, Sx, nsub, w, c, &off, &cnt);
-        if (kind == kChNone) {
-          c.k += dir;
-          c.sub = 0;
+      for (int k = dir > 0 ? 0 : nsub - 1; dir > 0 ? k < nsub : k >= 0; k += dir) {
+        const int Nk = mt.NE[k];
+        if (w == 0) {
+          if (dir > 0 && k >= 1)  // panel k at block k-1: [g][c]
+            out[n++] = sdesc(mt.loff[k] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(k, Sx)]) * Nk,
+                             mt.NE[k - 1] * Nk, false);
+          if (dir < 0 && k <= nsub - 2)  // panel k+1 at block k
+            out[n++] = sdesc(mt.loff[k + 1] + (long long)(mt.xoff[k] - mt.xoff[jlo_of(k + 1, Sx)]) * mt.NE[k + 1],
+                             Nk * mt.NE[k + 1], false);
+          out[n++] = sdesc(mt.ioff[k] + (dir > 0 ? ((Nk * Nk + 3) & ~3) : 0), Nk * Nk, true);
           continue;
         }
-        out[n++] = (unsigned long long)off | ((unsigned long long)cnt << 40) | (kind == kChInverse ? kDescInverse : 0ull);
-        ++c.sub;
+        int c0, c1;
+        warp_share(mt, Sx, nsub, w, k, &c0, &c1);
+        if (c1 <= c0) continue;
+        const int N2 = mt.NE[k + 1], pc = piece_cols(S.panel_words, N2);
+        #pragma unroll 1
+        for (int c = c0; c < c1; c += pc)
+          out[n++] = sdesc(mt.loff[k + 1] + (long long)c * N2, (c1 - c < pc ? c1 - c : pc) * N2, false);
       }
     }
   }
@@ -1106,7 +1094,7 @@ __device__ __forceinline__ void srefill(WRing<T>& r, SFeed& f, const T* LT, cons
     }
     const unsigned long long dsc = __shfl_sync(0xffffffffu, f.cur, f.next - f.base);
     const T* src = (dsc & kDescInverse) ? Linv : LT;
-    if (!wring_try_issue<T>(r, src, (long long)(dsc & kDescOffMask), (int)((dsc >> 40) & 0x7ff), lane,
+    if (!wring_try_issue<T>(r, src, (long long)(dsc & kDescOffMask), (int)((dsc >> 40) & 0xffff), lane,
                             f.next == f.withhold))
       return;
     ++f.next;
@@ -1173,9 +1161,12 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   T* y = m.yz;
   T* z = y + N;
   T* tv = m.tv;
-  const int area = (int)(round4((size_t)S.panel_words) + (size_t)kRing * kSlot);
-  const int cap = (area / kNW) & ~3;
-  WRing<T> rg{m.R + (size_t)w * cap, cap, w * kEnt, m.full, m.dl, m.epos, 0, 0, 0u, 0u, m.ph, m.used, m.fpar, true};
+  // warp w's region of the panel and ring area: kPartWords partial-sum
+  // elements (forward pass, two rows of 32), then its FIFO of chunks
+  const int region = fifo_cap(S.panel_words) + kPartWords;
+  T* part = m.R + (size_t)w * region;
+  WRing<T> rg{part + kPartWords, fifo_cap(S.panel_words), w * kEnt, m.full, m.dl, m.epos, 0, 0, 0u, 0u, m.ph,
+              m.used, m.fpar, true};
   #pragma unroll 1
   for (int i = threadIdx.x; i < N; i += kThreads) {
     y[i] = (T)in[i];
@@ -1188,17 +1179,21 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
   if (w == 0 && S.inject && S.inject[0] != 0) fd.withhold = fd.n - 1;
   srefill<T>(rg, fd, LT, Linv, lane);
   __syncthreads();
-  // forward
+  // forward, y_k = L_kk^-1 (in_k - sum_{j<k} L_kj y_j): at step k the leader
+  // finishes row k with the partial sums the other warps formed for it at
+  // step k-1 and the block L_{k,k-1}; meanwhile the other warps form row
+  // k+1's sums over blocks jlo(k+1)..k-1 (y of those blocks is known)
   #pragma unroll 1
   for (int k = 0; k < nsub; ++k) {
     const int Nk = mt.NE[k], xk = mt.xoff[k];
     if (w == 0) {
       T t = (lane < Nk) ? y[xk + lane] : T(0);
-      if (k >= 1) {  // t_k -= L_{k,k-1} y_{k-1}
+      if (k >= 1) {
+        const int h = (k & 1) * 32 + lane;
+        if (lane < Nk) t -= (m.R[(size_t)region + h] + m.R[2 * (size_t)region + h]) + m.R[3 * (size_t)region + h];
         const int Nj = mt.NE[k - 1];
         const T* P = wring_wait<T>(rg);  // [g][c]
-        const T* yj = y + mt.xoff[k - 1];
-        if (lane < Nk) t -= dot_col<T>(P + lane, Nk, yj, Nj);
+        if (lane < Nk) t -= dot_col<T>(P + lane, Nk, y + mt.xoff[k - 1], Nj);
         wring_release<T>(rg);
         srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
       }
@@ -1208,25 +1203,30 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       // y_k[c] = sum_{t <= c} Linv[c][t] tv[t] (the stored inverse holds its zeros)
       const T yk = lane < Nk ? dot_col<T>(LiT + lane, Nk, tv, Nk) : T(0);
       wring_release<T>(rg);
-        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+      srefill<T>(rg, fd, LT, Linv, lane);
       if (lane < Nk) y[xk + lane] = yk;
-    } else if (k >= 1) {  // t_k' -= L_{k',k-1} y_{k-1} for the warp's rows k'
-      const int Nj = mt.NE[k - 1];
-      const T* yj = y + mt.xoff[k - 1];
-      const int nc = n_citems(mt, Sx, nsub, 1, k);
+    } else if (k + 1 < nsub) {
+      int c0, c1;
+      warp_share(mt, Sx, nsub, w, k, &c0, &c1);
+      const int N2 = mt.NE[k + 1], pc = piece_cols(S.panel_words, N2);
+      const T* yb = y + mt.xoff[jlo_of(k + 1, Sx)];
+      T acc = T(0);
       #pragma unroll 1
-      for (int i = w - 1; i < nc; i += kNW - 1) {
-        const int kk = k + 1 + i, N2 = mt.NE[kk];
-        const T* P = wring_wait<T>(rg);  // [g][c]
-        if (lane < N2) y[mt.xoff[kk] + lane] -= dot_col<T>(P + lane, N2, yj, Nj);
+      for (int c = c0; c < c1; c += pc) {
+        const T* P = wring_wait<T>(rg);  // columns c.. of panel k+1, [c][g]
+        if (lane < N2) acc += dot_col<T>(P + lane, N2, yb + c, min(pc, c1 - c));
         wring_release<T>(rg);
-        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);
       }
+      if (lane < N2) part[((k + 1) & 1) * 32 + lane] = acc;  // zero for an empty share
     }
     srefill<T>(rg, fd, LT, Linv, lane);
     __syncthreads();
   }
-  // backward (the feed runs on into the backward chunks)
+  // backward, z_k = L_kk^-T (y_k - sum_{k'>k} L_k'k^T z_k'): at step k, with
+  // z_{k+1} known, the leader applies L_{k+1,k}^T z_{k+1} to row k and
+  // finishes it, the other warps apply L_{k+1,j}^T z_{k+1} to their columns of
+  // blocks jlo(k+1)..k-1 (the feed runs on into the backward chunks)
   srefill<T>(rg, fd, LT, Linv, lane);
   #pragma unroll 1
   for (int k = nsub - 1; k >= 0; --k) {
@@ -1238,7 +1238,7 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
         const T* zn = z + mt.xoff[k + 1];
         if (lane < Nk) z[xk + lane] += dot_row<T>(P + lane * N2, zn, N2, (N2 & 1) ? 0 : lane % N2);
         wring_release<T>(rg);
-        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);
       }
       const T* Li = wring_wait<T>(rg);
       if (lane < Nk) tv[lane] = y[xk + lane] - z[xk + lane];
@@ -1246,20 +1246,22 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
       // z_k[c] = sum_{r >= c} Linv[r][c] tv[r] (zeros stored above the diagonal)
       const T zc = lane < Nk ? dot_col<T>(Li + lane, Nk, tv, Nk) : T(0);
       wring_release<T>(rg);
-        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+      srefill<T>(rg, fd, LT, Linv, lane);
       if (lane < Nk) z[xk + lane] = zc;
-    } else if (k <= nsub - 2) {  // p_j += L_{k+1,j}^T z_{k+1} for the warp's j < k
-      const int N2 = mt.NE[k + 1];
+    } else if (k + 1 < nsub) {
+      int c0, c1;
+      warp_share(mt, Sx, nsub, w, k, &c0, &c1);
+      const int N2 = mt.NE[k + 1], pc = piece_cols(S.panel_words, N2);
       const T* zn = z + mt.xoff[k + 1];
-      const int jl1 = jlo_of(k + 1, Sx);
-      const int nc = n_citems(mt, Sx, nsub, -1, k);
+      T* zb = z + mt.xoff[jlo_of(k + 1, Sx)];
       #pragma unroll 1
-      for (int i = w - 1; i < nc; i += kNW - 1) {
-        const int j = jl1 + i, Nj = mt.NE[j];
-        const T* P = wring_wait<T>(rg);  // [g][c]: g in block j, c in block k+1
-        if (lane < Nj) z[mt.xoff[j] + lane] += dot_row<T>(P + lane * N2, zn, N2, (N2 & 1) ? 0 : lane % N2);
+      for (int c = c0; c < c1; c += pc) {
+        const int nc = min(pc, c1 - c);
+        const T* P = wring_wait<T>(rg);  // columns c.. of panel k+1, [c][g]
+        #pragma unroll 1
+        for (int u = lane; u < nc; u += 32) zb[c + u] += dot_row<T>(P + u * N2, zn, N2, (N2 & 1) ? 0 : u % N2);
         wring_release<T>(rg);
-        srefill<T>(rg, fd, LT, Linv, lane);  // the next own chunk is issued before it is awaited
+        srefill<T>(rg, fd, LT, Linv, lane);
       }
     }
     srefill<T>(rg, fd, LT, Linv, lane);

@@ -109,10 +109,15 @@ __host__ __device__ inline int jlo_of(int k, int Sx) { return k - Sx > 0 ? k - S
 
 constexpr int kSolveWarps = 4;  // warps of the CTA that solves one reduced system
 // 64-bit words of the substitution copy schedule: kSolveWarps + 1 list starts,
-// then the warps' lists, together at most n_sub (2 Sx + 3) chunk descriptors
-// (a block row holds at most Sx + 1 forward and Sx + 2 backward chunks).
+// then the warps' lists, together at most n_sub (4 Sx + 16) chunk descriptors.
+// Per block row and direction: the leader's two chunks, and the other warps'
+// C columns of a panel row of n2 <= 32 elements in pieces of pc columns, at
+// most C / pc + 3 pieces. A FIFO holds at least panel_words / 4 + 965
+// elements and pc n2 >= FIFO / 2 - 36, while C <= 32 Sx and C n2 <=
+// panel_words: C / pc < min(8, 2.2 Sx), so at most 2 (5 + min(8, 2.2 Sx))
+// chunks per block row.
 inline size_t sched_words(int n_sub, int Sx) {
-  return kSolveWarps + 1 + (size_t)n_sub * (2 * (size_t)Sx + 3);
+  return kSolveWarps + 1 + (size_t)n_sub * (4 * (size_t)Sx + 16);
 }
 
 // Launchers (all enqueue on `st`; `active` lists slot indices, device array).

@@ -1,65 +1,103 @@
-"""Size bound of the substitution copy schedule (host logic, no GPU).
+"""Size bound and coverage of the substitution copy schedule (host logic, no GPU).
 
 The library builds, once per simulation, the per-warp list of chunks that the
-pipelined substitutions copy (forward, then backward). The buffer holding it
-is sized by a closed-form bound: kSolveWarps + 1 list starts plus n_sub (2 Sx
-+ 3) descriptors. This test enumerates the chunk lists the same way (block
-rows in order; the leader takes the coupling block to the previous/next row
-and the diagonal inverse, the other warps take the coupling blocks of the
-rows within the envelope, dealt in turn) for many subdomain layouts and
-checks the bound, and that every chunk of the envelope is copied exactly once
-per direction."""
+pipelined substitutions copy (forward, then backward). Per block row k the
+leader takes the coupling block to the previous (forward) or next (backward)
+row and the diagonal inverse; the other warps split the columns of panel k+1
+before its block k into three contiguous shares, each copied in pieces of at
+most pc columns, pc = max(1, (FIFO / 2 - 4) // n2) with the per-warp FIFO
+((panel_words rounded up to 4 + 4 * 1032) // 4 rounded down to 4, minus 64
+partial-sum elements). The buffer holding the lists is sized by a closed-form
+bound: kSolveWarps + 1 list starts plus n_sub (4 Sx + 16) descriptors. This
+test enumerates the lists that way for many layouts and basis sizes (panel
+words taken at their smallest, which gives the most pieces), checks the
+bound, that every piece fits half a FIFO, and that every block of the
+envelope is copied exactly once per direction."""
+import numpy as np
 import pytest
 
-NW = 4  # warps per CTA of the reduced solve
+NW = 4       # warps per CTA of the reduced solve
+RING = 4     # slots of the factorisation ring
+SLOT = 32 * 32 + 8
+PART = 64    # partial-sum elements at the start of each warp's region
 
 
 def jlo(k, Sx):
     return max(0, k - Sx)
 
 
-def n_citems(nsub, Sx, direction, k):
-    if direction > 0:
-        return max(0, min(k - 1 + Sx, nsub - 1) - k) if k >= 1 else 0
-    return k - jlo(k + 1, Sx) if k <= nsub - 2 else 0
+def fifo_cap(panel_words):
+    area = ((panel_words + 3) & ~3) + RING * SLOT
+    return ((area // NW) & ~3) - PART
 
 
-def warp_lists(nsub, Sx):
+def piece_cols(panel_words, n2):
+    return max(1, (fifo_cap(panel_words) // 2 - 4) // n2)
+
+
+def warp_lists(NE, Sx):
+    nsub = len(NE)
+    xoff = np.concatenate([[0], np.cumsum(NE)])
+    pw = max(int(NE[k]) * int(xoff[k + 1] - xoff[jlo(k, Sx)]) for k in range(nsub))
     lists = [[] for _ in range(NW)]
     for direction in (1, -1):
         rows = range(nsub) if direction > 0 else range(nsub - 1, -1, -1)
         for k in rows:
-            # leader: coupling block to the previous (forward) / next (backward) row, then L_kk^-1
-            if direction > 0 and k >= 1:  # row k at block k-1
-                lists[0].append(("panel", direction, k, k - 1))
-            if direction < 0 and k <= nsub - 2:  # row k+1 at block k
-                lists[0].append(("panel", direction, k + 1, k))
-            lists[0].append(("inverse", direction, k))
-            for i in range(n_citems(nsub, Sx, direction, k)):
-                w = 1 + i % (NW - 1)
-                if direction > 0:  # row k+1+i at block k-1
-                    lists[w].append(("panel", direction, k + 1 + i, k - 1))
-                else:  # row k+1 at block jlo(k+1)+i
-                    lists[w].append(("panel", direction, k + 1, jlo(k + 1, Sx) + i))
-    return lists
+            if direction > 0 and k >= 1:
+                lists[0].append(("panel", direction, k, [k - 1], NE[k - 1] * NE[k]))
+            if direction < 0 and k <= nsub - 2:
+                lists[0].append(("panel", direction, k + 1, [k], NE[k] * NE[k + 1]))
+            lists[0].append(("inverse", direction, k, None, NE[k] ** 2))
+            if k + 1 >= nsub:
+                continue
+            base = xoff[jlo(k + 1, Sx)]
+            C = int(xoff[k] - base)
+            n2 = int(NE[k + 1])
+            pc = piece_cols(pw, n2)
+            for w in range(1, NW):
+                c0, c1 = C * (w - 1) // (NW - 1), C * w // (NW - 1)
+                for c in range(c0, c1, pc):
+                    ce = min(c + pc, c1)
+                    cols = (base + c, base + ce)  # global columns covered
+                    lists[w].append(("piece", direction, k + 1, cols, (ce - c) * n2))
+    return lists, xoff, pw
 
 
 def sched_words(n_sub, Sx):
-    return NW + 1 + n_sub * (2 * Sx + 3)
+    return NW + 1 + n_sub * (4 * Sx + 16)
 
 
-@pytest.mark.parametrize("Sx,Sy", [(1, 1), (1, 7), (2, 1), (2, 2), (3, 5), (4, 4), (8, 8), (16, 16),
-                                   (32, 2), (5, 40), (64, 3), (6, 22)])
-def test_schedule_fits_its_bound_and_covers_the_envelope(Sx, Sy):
+LAYOUTS = [(1, 1), (1, 7), (2, 1), (2, 2), (3, 5), (4, 4), (8, 8), (16, 16), (32, 2), (5, 40), (64, 3), (6, 22),
+           (32, 32)]
+
+
+@pytest.mark.parametrize("Sx,Sy", LAYOUTS)
+@pytest.mark.parametrize("sizes", ["small", "uniform", "large"])
+def test_schedule_fits_its_bound_and_covers_the_envelope(Sx, Sy, sizes):
     nsub = Sx * Sy
-    lists = warp_lists(nsub, Sx)
+    rng = np.random.default_rng(Sx * 1000 + Sy)
+    NE = {"small": np.full(nsub, 5), "uniform": rng.integers(5, 31, nsub), "large": np.full(nsub, 32)}[sizes]
+    lists, xoff, pw = warp_lists(NE, Sx)
     total = sum(len(l) for l in lists)
     assert NW + 1 + total <= sched_words(nsub, Sx)
-    # every off-diagonal block (r, j) of the envelope, jlo(r) <= j < r, is copied once per
-    # direction: forward as (row r at block j), backward as (row r at block j) too
+    half = fifo_cap(pw) // 2
+    assert all(c[4] + 3 <= half or c[0] != "piece" for l in lists for c in l)  # two pieces in flight
+    assert all(c[4] + 3 <= fifo_cap(pw) for l in lists for c in l)
     for direction in (1, -1):
-        got = sorted((c[2], c[3]) for l in lists for c in l if c[0] == "panel" and c[1] == direction)
-        want = sorted((r, j) for r in range(nsub) for j in range(jlo(r, Sx), r))
-        assert got == want
+        # columns of each panel row r covered: leader blocks and the other warps' pieces
+        cover = {r: np.zeros(int(xoff[r] - xoff[jlo(r, Sx)]), dtype=int) for r in range(nsub)}
+        for l in lists:
+            for c in l:
+                if c[1] != direction or c[0] == "inverse":
+                    continue
+                r = c[2]
+                b = xoff[jlo(r, Sx)]
+                if c[0] == "panel":
+                    j = c[3][0]
+                    cover[r][xoff[j] - b: xoff[j + 1] - b] += 1
+                else:
+                    cover[r][c[3][0] - b: c[3][1] - b] += 1
+        for r in range(nsub):
+            assert np.all(cover[r] == 1), (direction, r)
         inv = sorted(c[2] for c in lists[0] if c[0] == "inverse" and c[1] == direction)
         assert inv == list(range(nsub))
