@@ -114,8 +114,8 @@ typedef struct {
                         refinement also once a correction no longer halves */
   int refactor_period; /* MIXED: steps one FP32 factor serves before the
                         simulation refactors (1: every step); 0: default 6.
-                        The first guess of each solve is the linear
-                        extrapolation of the last two solutions            */
+                        The first guess of each solve is the quadratic
+                        extrapolation of the last three solutions          */
 } lrbms_config;
 
 /* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with

