@@ -110,10 +110,11 @@ typedef struct {
                         11). 0: default (1 for FP64, 6 for MIXED); at most
                         16. The iteration stops early once the next
                         correction, predicted from the last two, is below
-                        1e-12 of the solution (max norms); the FP64
-                        refinement also once a correction no longer halves */
+                        2.5e-13 (conjugate gradients) or 1e-12 (refinement)
+                        of the solution (max norms); the refinement also
+                        once a correction no longer halves                 */
   int refactor_period; /* MIXED: steps one FP32 factor serves before the
-                        simulation refactors (1: every step); 0: default 6.
+                        simulation refactors (1: every step); 0: default 8.
                         The first guess of each solve is the quadratic
                         extrapolation of the last three solutions          */
 } lrbms_config;

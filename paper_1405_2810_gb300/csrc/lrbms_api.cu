@@ -92,7 +92,7 @@ struct lrbms_ctx {
   int precision = LRBMS_FP64;
   int solver = LRBMS_SOLVE_FP64;
   int refine_iters = 1;
-  int refactor_period = 6;
+  int refactor_period = 8;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t admit_stream = nullptr;  // admission copies and kernels (overlap the steps)
@@ -165,7 +165,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   ctx->precision = cfg->precision;
   ctx->solver = cfg->solver;
   ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 6 : 1);
-  ctx->refactor_period = cfg->refactor_period > 0 ? cfg->refactor_period : 6;  // measured best at 512 sims
+  ctx->refactor_period = cfg->refactor_period > 0 ? cfg->refactor_period : 8;  // measured best at 512 sims
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete ctx;
