@@ -471,8 +471,10 @@ __device__ __forceinline__ void factor_issue(Ring<T>& r, FactorSeq& q, const Sol
 // loop runs over every t > c; the entries above the diagonal it also
 // touches are never read). Inverse Y = L^-1 row by row, lane = column:
 // Y[i][j] = (delta_ij - sum_{t < i} L[i][t] Y[t][j]) / L[i][i], over a
-// zero-filled Y. Writes L to the transposed panel rows LTd ([c][r], zero
-// above the diagonal), L^-1 to Li [N][N] and its transpose after it.
+// zero-filled Y. Writes L^-1 to Li [N][N] and its transpose after it, and
+// the transpose also to the panel's diagonal slot LTd (L itself is never
+// read again: products use the inverse), where the forward substitution
+// fetches it in the same copy as the block to its left.
 // Returns true (in every lane) on a non-positive or non-finite pivot.
 template <typename T>
 __device__ __noinline__ bool diag_block_warp(const T* Rd, int ld, int N, T* W, T* LTd, T* Li) {
@@ -543,10 +545,10 @@ __device__ __noinline__ bool diag_block_warp(const T* Rd, int ld, int N, T* W, T
   if (lane < N) {
 #pragma unroll 1
     for (int c = 0; c < N; ++c) {
-      LTd[(size_t)c * N + lane] = (c <= lane) ? D[lane * ldd + c] : T(0);
       const T y = Y[c * N + lane];  // row c of L^-1 (zero right of the diagonal)
       Li[c * N + lane] = y;
       LiT[lane * N + c] = y;
+      LTd[lane * N + c] = y;  // the panel's diagonal slot holds L^-1 in LiT's layout (see fwd_pair)
     }
   }
   return __any_sync(0xffffffffu, bad);
@@ -894,13 +896,13 @@ __device__ int cfactor_mma(const SimDev& S, float* LT, float* Linv, CtaSmem<floa
 
 // ---------------------------------------------------------------- substitutions
 // Forward and backward substitution, pipelined over the block rows with one
-// CTA barrier per row. Forward, iteration k: the leader applies the
-// contribution of row k-1 to row k and y_k = L_kk^-1 t_k (the critical path);
-// the other warps apply the contributions of row k-1 to rows k+1 ..
-// k-1+Sx (t_k' -= L_{k'k-1} y_{k-1}). Backward, iteration k (descending): the
-// leader applies the contribution of row k+1 to row k and z_k = L_kk^-T (y_k
-// - p_k); the other warps apply the contributions of row k+1 to rows j <
-// k (p_j += L_{k+1 j}^T z_{k+1}). Every warp streams its own chunks through
+// CTA barrier per row. Forward, step k: the leader finishes row k (the other
+// warps' partial sums for it, the block L_{k,k-1}, then y_k = L_kk^-1 t_k:
+// the critical path) while the other warps form row k+1's sums over blocks
+// jlo(k+1)..k-1. Backward, step k (descending): the leader applies the
+// contribution of row k+1 to row k and z_k = L_kk^-T (y_k - p_k); the other
+// warps apply the contributions of row k+1 to their columns of rows j < k
+// (p_j += L_{k+1 j}^T z_{k+1}). Every warp streams its own chunks through
 // its own region of shared memory (a FIFO of variable-size bulk copies with
 // kEnt full barriers), so no warp waits for another to release a slot.
 constexpr int kEnt = kMaxSlots / kNW;  // chunks in flight per warp
@@ -996,6 +998,13 @@ __host__ __device__ inline int piece_cols(int panel_words, int n2) {
   const int c = (fifo_cap(panel_words) / 2 - 4) / n2;
   return c > 1 ? c : 1;
 }
+// The leader's forward chunk of row k: the coupling block L_{k,k-1} and the
+// panel's diagonal slot (L_kk^-1, transposed) are adjacent in panel k, so one
+// copy carries both when they fit half a FIFO (always for k = 0, the slot
+// alone); otherwise the inverse comes from the inverse array.
+__host__ __device__ inline bool fwd_pair(int panel_words, int nprev, int nk) {
+  return (nprev + nk) * nk + 3 <= fifo_cap(panel_words) / 2;
+}
 __device__ __forceinline__ void warp_share(const SolveMeta& mt, int Sx, int nsub, int w, int k, int* c0, int* c1) {
   if (w == 0 || k + 1 >= nsub) {
     *c0 = *c1 = 0;
@@ -1033,9 +1042,14 @@ __device__ void build_sched(const SimDev& S, unsigned long long* out) {
       for (int k = dir > 0 ? 0 : nsub - 1; dir > 0 ? k < nsub : k >= 0; k += dir) {
         const int Nk = mt.NE[k];
         if (w == 0) {
+          const int Np = k >= 1 ? mt.NE[k - 1] : 0;
+          if (dir > 0 && fwd_pair(S.panel_words, Np, Nk)) {  // panel k at block k-1 and the diagonal slot
+            out[n++] = sdesc(mt.loff[k] + (long long)(mt.xoff[k] - Np - mt.xoff[jlo_of(k, Sx)]) * Nk, (Np + Nk) * Nk,
+                             false);
+            continue;
+          }
           if (dir > 0 && k >= 1)  // panel k at block k-1: [g][c]
-            out[n++] = sdesc(mt.loff[k] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(k, Sx)]) * Nk,
-                             mt.NE[k - 1] * Nk, false);
+            out[n++] = sdesc(mt.loff[k] + (long long)(mt.xoff[k - 1] - mt.xoff[jlo_of(k, Sx)]) * Nk, Np * Nk, false);
           if (dir < 0 && k <= nsub - 2)  // panel k+1 at block k
             out[n++] = sdesc(mt.loff[k + 1] + (long long)(mt.xoff[k] - mt.xoff[jlo_of(k + 1, Sx)]) * mt.NE[k + 1],
                              Nk * mt.NE[k + 1], false);
@@ -1198,17 +1212,21 @@ __device__ bool csubstitute(const SimDev& S, const T* LT, const T* Linv, const d
     const int Nk = mt.NE[k], xk = mt.xoff[k];
     if (w == 0) {
       T t = (lane < Nk) ? y[xk + lane] : T(0);
+      const int Nj = k >= 1 ? mt.NE[k - 1] : 0;
+      const bool pair = fwd_pair(S.panel_words, Nj, Nk);
+      const T* P = (k >= 1 || pair) ? swait<T>(rg, fd, LT, Linv, lane) : nullptr;  // [g][c] (and the slot)
       if (k >= 1) {
         const int h = (k & 1) * 32 + lane;
         if (lane < Nk) t -= (m.R[(size_t)region + h] + m.R[2 * (size_t)region + h]) + m.R[3 * (size_t)region + h];
-        const int Nj = mt.NE[k - 1];
-        const T* P = swait<T>(rg, fd, LT, Linv, lane);  // [g][c]
         if (lane < Nk) t -= dot_col<T>(P + lane, Nk, y + mt.xoff[k - 1], Nj);
-        wring_release<T>(rg);
       }
       if (lane < Nk) tv[lane] = t;
       __syncwarp();
-      const T* LiT = swait<T>(rg, fd, LT, Linv, lane);
+      const T* LiT = pair ? P + Nj * Nk : nullptr;
+      if (!pair) {
+        if (k >= 1) wring_release<T>(rg);
+        LiT = swait<T>(rg, fd, LT, Linv, lane);
+      }
       // y_k[c] = sum_{t <= c} Linv[c][t] tv[t] (the stored inverse holds its zeros)
       const T yk = lane < Nk ? dot_col<T>(LiT + lane, Nk, tv, Nk) : T(0);
       wring_release<T>(rg);
