@@ -73,6 +73,9 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-steps", type=int, default=300, help="online steps per request")
+    ap.add_argument("--serve-align", type=int, default=0,
+                    help="admit only every this many ticks (0: the refactor period, 8, with the mixed solver; "
+                         "1 with FP64)")
     return ap.parse_args()
 
 
@@ -352,8 +355,9 @@ def run_serving(a):
     free, _tot = torch.cuda.mem_get_info()
     prec = L.LRBMS_FP64 if a.precision == "fp64" else L.LRBMS_MIXED
     solver = L.LRBMS_SOLVE_MIXED if a.solver == "mixed" else L.LRBMS_SOLVE_FP64
+    period = a.refactor_period if a.refactor_period > 0 else 8  # FP32 refactor period of the mixed solver
     ctx = L.lrbms_create(precision=prec, max_slots=2048, hbm_budget=int(min(free * 0.45, 96 << 30)),
-                         stream=stream.cuda_stream, solver=solver)
+                         stream=stream.cuda_stream, solver=solver, refactor_period=period)
     t0 = time.perf_counter()
     pool = []  # (sim id, nx, ny, shape)
     for i, (n, S) in enumerate(SERVE_SHAPES):
@@ -367,7 +371,8 @@ def run_serving(a):
     kinds = rng.integers(0, len(pool), size=a.serve_requests)
     arrivals = [(float(t), {"nx": pool[k][1], "ny": pool[k][2]}, {"src": pool[k][0], "kind": int(k)},
                  a.serve_steps) for t, k in zip(times, kinds)]
-    srv = Server(L, ctx, admit=lambda c, r: L.lrbms_clone(c, r.offline["src"], None))
+    align = a.serve_align if a.serve_align > 0 else (period if a.solver == "mixed" else 1)
+    srv = Server(L, ctx, admit=lambda c, r: L.lrbms_clone(c, r.offline["src"], None), align=align)
     t1 = time.perf_counter()
     done = srv.run_timed(arrivals)
     wall = time.perf_counter() - t1
@@ -390,7 +395,8 @@ def run_serving(a):
         "dtype": "f64+f32" if a.solver == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"Poisson arrivals at {a.serve_rate:g}/s, {a.serve_requests} requests of "
                                f"{a.serve_steps} steps, grids/subdomains " + ", ".join(p[3] for p in pool),
-                   "precision": a.precision, "solver": a.solver, "pool_build_s": t_pool},
+                   "precision": a.precision, "solver": a.solver, "admission_align_ticks": align,
+                   "pool_build_s": t_pool},
     }))
     L.lrbms_destroy(ctx)
 

@@ -9,6 +9,14 @@ simulation that has taken its steps is read out and released, which frees
 its memory for the queue. All arithmetic runs in the library's kernels; this
 module only schedules. Because the kernels reduce in a fixed order per
 simulation, each result is the same as the simulation run alone.
+
+With the mixed solver a simulation recomputes its FP32 factor every
+refactor_period steps, counted from its first step, and a launch lasts as
+long as its slowest simulation: the factor of the largest systems is several
+times their solve. Simulations that started on different ticks would put
+some factor into every tick. Server(align=refactor_period) therefore admits
+only on ticks whose next tick is a refactor tick of the residents, so that
+all of them factor together; a request waits at most align - 1 ticks more.
 """
 from __future__ import annotations
 
@@ -43,12 +51,18 @@ class Server:
     lrbms_release, LrbmsError, LRBMS_E_BUDGET). admit: optional callable
     (ctx, request) -> sim_id replacing lrbms_offline_load (for instance a
     lrbms_clone of a resident simulation); it raises LrbmsError with
-    LRBMS_E_BUDGET when the request does not fit yet."""
+    LRBMS_E_BUDGET when the request does not fit yet. align: admissions
+    happen only on ticks t with (t + 1 - t0) % align == 0, t0 the first tick
+    of the residents present since the server was last empty (1: any tick)."""
 
-    def __init__(self, backend, ctx, admit=None):
+    def __init__(self, backend, ctx, admit=None, align: int = 1):
+        if int(align) < 1:
+            raise ValueError("align must be >= 1")
         self.L = backend
         self.ctx = ctx
         self.admit = admit
+        self.align = int(align)
+        self.anchor = 0  # first tick of the current residents
         self.clock = None  # run_timed: seconds since its start
         self.queue: deque[Request] = deque()
         self.active: list[Request] = []
@@ -65,6 +79,10 @@ class Server:
         return r.rid
 
     def _admit(self):
+        if not self.active:
+            self.anchor = self.tick + 1  # no residents: the next tick starts a new phase
+        elif (self.tick + 1 - self.anchor) % self.align != 0:
+            return
         while self.queue:
             r = self.queue[0]
             t0 = time.perf_counter()

@@ -92,3 +92,30 @@ def test_admit_hook_and_timed_arrivals():
     assert all(r.arrival_s <= r.admitted_s <= r.finished_s for r in done)
     assert done[3].arrival_s == 0.05 and done[3].admitted_s >= 0.05
     assert max(len(c) for c in lib.calls) <= 3 and not lib.live
+
+
+def test_aligned_admission_keeps_residents_in_phase():
+    """With align=k every simulation takes its first step on a tick that is a
+    multiple of k after the first tick of the residents, so their step counts
+    agree modulo k (the mixed solver's refactor ticks coincide); an empty
+    server starts a new phase at once."""
+    lib = FakeLib(capacity=100)
+    srv = Server(lib, ctx=None, align=4)
+    prob = {"nx": 1, "ny": 1}
+    arrivals = [(0, prob, None, 10), (1, prob, None, 10), (2, prob, None, 3), (5, prob, None, 6),
+                (9, prob, None, 2), (30, prob, None, 5), (31, prob, None, 4)]
+    done = srv.run(arrivals)
+    assert [r.rid for r in done] == list(range(len(arrivals)))
+    assert all(r.result["steps"] == r.n_steps for r in done)
+    # residents of the first phase start on ticks 1 + 4 j (request 0 is admitted on tick 0)
+    starts = [r.admitted_tick + 1 for r in done]
+    assert starts[0] == 1
+    assert all((s - starts[0]) % 4 == 0 for s in starts[:5])
+    assert all(r.admitted_tick >= r.arrival_tick for r in done)
+    assert all(r.admitted_tick - r.arrival_tick < 4 for r in done[1:5])
+    # the server emptied before request 5 arrived: it starts a new phase at once
+    assert done[5].admitted_tick == done[5].arrival_tick
+    assert (starts[6] - starts[5]) % 4 == 0
+    assert not lib.live
+    with pytest.raises(ValueError):
+        Server(lib, ctx=None, align=0)
