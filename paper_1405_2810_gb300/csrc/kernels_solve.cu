@@ -727,22 +727,37 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// One warp: C[r][c] (set: =, else -=) sum_{t < K} A[r][t] B(t, c) for the
-// 16-row tiles [m0, m1) of r < M and all c < N (N, K <= 32); A row-major
-// (lda), B(t, c) at B[t * ldbk + c * ldbn], C row-major (ldc). With `set`, C
-// may alias A (a tile's rows are read for all t before they are written).
-__device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ldc, int M, int N, int K,
-                                       const float* B, int ldbk, int ldbn, int m0, int m1, bool set) {
+// One warp: C[r][c] (set: =, else -=) sum_{t < K} A[r][t] B(t, c) for TM
+// consecutive 16-row tiles from mt0 (rows r < M) and all c < N (N, K <= 32);
+// A row-major (lda), B(t, c) at B[t * ldbk + c * ldbn], C row-major (ldc).
+// B's fragments are loaded and split once per k-step and serve every tile.
+// Every tile's rows are read for all t before any is written, so with `set`
+// C may alias A. Each accumulator takes its terms in the same order for any
+// TM (k-steps ascending; per k-step a_lo b_hi, a_hi b_lo, a_hi b_hi).
+template <int TM>
+__device__ __forceinline__ void mma_tiles(const float* A, int lda, float* C, int ldc, int M, int N, int K,
+                                          const float* B, int ldbk, int ldbn, int mt0, bool set) {
   const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-#pragma unroll 1
-  for (int mt = m0; mt < m1 && mt * 16 < M; ++mt) {
-    float acc[4][4];
+  float acc[TM][4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    const int r0 = mt * 16 + g, r1 = r0 + 8;
+  for (int m = 0; m < TM; ++m)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[m][i][0] = acc[m][i][1] = acc[m][i][2] = acc[m][i][3] = 0.f;
 #pragma unroll 1
-    for (int kt = 0; kt * 8 < K; ++kt) {
-      const int k0 = kt * 8 + tq, k1 = k0 + 4;
+  for (int kt = 0; kt * 8 < K; ++kt) {
+    const int k0 = kt * 8 + tq, k1 = k0 + 4;
+    uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int n = nt * 8 + g;
+      const float b0 = (nt * 8 < N && k0 < K && n < N) ? B[k0 * ldbk + n * ldbn] : 0.f;
+      const float b1 = (nt * 8 < N && k1 < K && n < N) ? B[k1 * ldbk + n * ldbn] : 0.f;
+      split_tf32(b0, bh[nt][0], bl[nt][0]);
+      split_tf32(b1, bh[nt][1], bl[nt][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < TM; ++m) {
+      const int r0 = (mt0 + m) * 16 + g, r1 = r0 + 8;
       float av[4];
       av[0] = (r0 < M && k0 < K) ? A[r0 * lda + k0] : 0.f;
       av[1] = (r1 < M && k0 < K) ? A[r1 * lda + k0] : 0.f;
@@ -751,39 +766,45 @@ __device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ld
       uint32_t ah[4], al[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) split_tf32(av[i], ah[i], al[i]);
-      uint32_t bh[4][2], bl[4][2];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int n = nt * 8 + g;
-        const float b0 = (nt * 8 < N && k0 < K && n < N) ? B[k0 * ldbk + n * ldbn] : 0.f;
-        const float b1 = (nt * 8 < N && k1 < K && n < N) ? B[k1 * ldbk + n * ldbn] : 0.f;
-        split_tf32(b0, bh[nt][0], bl[nt][0]);
-        split_tf32(b1, bh[nt][1], bl[nt][1]);
-      }
       // term by term over the independent accumulators (small terms first)
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt)
-        if (nt * 8 < N) mma_tf32(acc[nt], al, bh[nt]);
+        if (nt * 8 < N) mma_tf32(acc[m][nt], al, bh[nt]);
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt)
-        if (nt * 8 < N) mma_tf32(acc[nt], ah, bl[nt]);
+        if (nt * 8 < N) mma_tf32(acc[m][nt], ah, bl[nt]);
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt)
-        if (nt * 8 < N) mma_tf32(acc[nt], ah, bh[nt]);
+        if (nt * 8 < N) mma_tf32(acc[m][nt], ah, bh[nt]);
     }
-    __syncwarp();
+  }
+  __syncwarp();
+#pragma unroll
+  for (int m = 0; m < TM; ++m) {
+    const int r0 = (mt0 + m) * 16 + g, r1 = r0 + 8;
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       if (nt * 8 < N) {
         const int c0 = nt * 8 + 2 * tq, c1 = c0 + 1;
-        if (r0 < M && c0 < N) C[r0 * ldc + c0] = set ? acc[nt][0] : C[r0 * ldc + c0] - acc[nt][0];
-        if (r0 < M && c1 < N) C[r0 * ldc + c1] = set ? acc[nt][1] : C[r0 * ldc + c1] - acc[nt][1];
-        if (r1 < M && c0 < N) C[r1 * ldc + c0] = set ? acc[nt][2] : C[r1 * ldc + c0] - acc[nt][2];
-        if (r1 < M && c1 < N) C[r1 * ldc + c1] = set ? acc[nt][3] : C[r1 * ldc + c1] - acc[nt][3];
+        if (r0 < M && c0 < N) C[r0 * ldc + c0] = set ? acc[m][nt][0] : C[r0 * ldc + c0] - acc[m][nt][0];
+        if (r0 < M && c1 < N) C[r0 * ldc + c1] = set ? acc[m][nt][1] : C[r0 * ldc + c1] - acc[m][nt][1];
+        if (r1 < M && c0 < N) C[r1 * ldc + c0] = set ? acc[m][nt][2] : C[r1 * ldc + c0] - acc[m][nt][2];
+        if (r1 < M && c1 < N) C[r1 * ldc + c1] = set ? acc[m][nt][3] : C[r1 * ldc + c1] - acc[m][nt][3];
       }
     }
   }
   __syncwarp();
+}
+
+// One warp: the 16-row tiles [m0, m1) of C (set: =, else -=) A B, rows
+// r < M (M <= 32), as mma_tiles; two tiles share B's fragments.
+__device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ldc, int M, int N, int K,
+                                       const float* B, int ldbk, int ldbn, int m0, int m1, bool set) {
+  const int me = min(m1, (M + 15) >> 4);
+  if (me - m0 >= 2)
+    mma_tiles<2>(A, lda, C, ldc, M, N, K, B, ldbk, ldbn, m0, set);
+  else if (me - m0 == 1)
+    mma_tiles<1>(A, lda, C, ldc, M, N, K, B, ldbk, ldbn, m0, set);
 }
 
 // FP32 envelope block Cholesky with the block products on the tensor cores,
