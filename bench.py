@@ -55,6 +55,8 @@ def parse_args():
                     help="reduced solve: FP64 Cholesky, or FP32 Cholesky with FP64 refinement")
     ap.add_argument("--refactor-period", type=int, default=0,
                     help="mixed solver: steps one FP32 factor serves (0: the library default)")
+    ap.add_argument("--refactor-stages", type=int, default=1,
+                    help="mixed solver: steps over which each next FP32 factor is built (default 1: in one step)")
     ap.add_argument("--horizon", type=int, default=300, help="steps per simulation (warm-up + timed)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-workers", type=int, default=0,
@@ -356,8 +358,10 @@ def run_serving(a):
     prec = L.LRBMS_FP64 if a.precision == "fp64" else L.LRBMS_MIXED
     solver = L.LRBMS_SOLVE_MIXED if a.solver == "mixed" else L.LRBMS_SOLVE_FP64
     period = a.refactor_period if a.refactor_period > 0 else 8  # FP32 refactor period of the mixed solver
+    stages = max(a.refactor_stages, 1)
     ctx = L.lrbms_create(precision=prec, max_slots=2048, hbm_budget=int(min(free * 0.45, 96 << 30)),
-                         stream=stream.cuda_stream, solver=solver, refactor_period=period)
+                         stream=stream.cuda_stream, solver=solver, refactor_period=period,
+                         refactor_stages=stages if a.solver == "mixed" else 0)
     t0 = time.perf_counter()
     pool = []  # (sim id, nx, ny, shape)
     for i, (n, S) in enumerate(SERVE_SHAPES):
@@ -396,6 +400,7 @@ def run_serving(a):
         "config": {"workload": f"Poisson arrivals at {a.serve_rate:g}/s, {a.serve_requests} requests of "
                                f"{a.serve_steps} steps, grids/subdomains " + ", ".join(p[3] for p in pool),
                    "precision": a.precision, "solver": a.solver, "admission_align_ticks": align,
+                   "refactor_stages": stages if a.solver == "mixed" else None,
                    "pool_build_s": t_pool},
     }))
     L.lrbms_destroy(ctx)
@@ -487,7 +492,7 @@ def main():
     solver = L.LRBMS_SOLVE_MIXED if a.solver == "mixed" else L.LRBMS_SOLVE_FP64
     ctx = L.lrbms_create(precision=prec, max_slots=a.n_sims + 8, hbm_budget=budget,
                          stream=stream.cuda_stream, device=local, solver=solver,
-                         refactor_period=a.refactor_period)
+                         refactor_period=a.refactor_period, refactor_stages=max(a.refactor_stages, 1))
 
     # ---- offline data on the GPU (not timed)
     t0 = time.perf_counter()
@@ -672,6 +677,7 @@ def main():
             "config": {"workload": workload_name(a), "n_sims": a.n_sims, "physical_datasets": a.n_prob,
                        "grid": f"{a.n}x{a.n}", "subdomains": f"{a.S}x{a.S}", "M": 8,
                        "basis_sizes_mean_N": N_mean, "precision": a.precision, "solver": a.solver,
+                       "refactor_stages": max(a.refactor_stages, 1),
                        "l2": f"inputs larger than L2: {used / 2**30:.1f} GiB resident",
                        "p50_step_ms": p50, "p99_step_ms": p99, "sims_ok": n_ok,
                        "offline_build_s": t_build, "parallelism": f"replicas x{world}",

@@ -117,6 +117,19 @@ typedef struct {
                         simulation refactors (1: every step); 0: default 8.
                         The first guess of each solve is the quadratic
                         extrapolation of the last three solutions          */
+  int refactor_stages; /* MIXED: steps over which each next FP32 factor is
+                        built, 1..refactor_period (0: default 1, the whole
+                        factorisation in one step). With R > 1 the next
+                        factor is computed in the idle one of two FP32
+                        buffers during the last R steps of the current
+                        factor's period, about n_sub / R block rows per
+                        step from that step's matrix, and serves from the
+                        solve of its last stage on. No step then carries a
+                        whole factorisation (lower tail latency); the
+                        factor is up to R - 1 steps older (more passes).
+                        A first factor, and one forced by a slow or failed
+                        solve, is still computed in one step. Larger than
+                        refactor_period: LRBMS_E_ARG                     */
 } lrbms_config;
 
 /* The model problem of Section 2 (Eqs. mainPressure..mainInitialData) with

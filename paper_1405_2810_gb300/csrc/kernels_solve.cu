@@ -21,25 +21,32 @@ namespace lrbms {
 
 namespace {
 
-// theta = G^+ (sum over tiles of the fit partials), by warp 0; w[0] = 1.
-__device__ void compute_weights(const SimDev& S, double* w, double* rsh, bool store) {
-  const int M = S.M;
-  if (threadIdx.x < 32) {
-    const int q = threadIdx.x;
-    if (q < M) {
-      double r = 0.0;
-      for (int t = 0; t < S.n_tiles; ++t) r += S.fit_part[(size_t)t * kMaxM + q];
-      rsh[q] = r;
-    }
-    __syncwarp();
-    if (q < M) {
-      double th = 0.0;
-      for (int j = 0; j < M; ++j) th = fma(S.Gpinv[q * M + j], rsh[j], th);
-      w[1 + q] = th;
-      if (store) S.theta[q] = th;
-    }
-    if (q == 0) w[0] = 1.0;
+// Eq. leastSquaresFit: theta = G^+ r, r_q the sum over tiles (in tile order)
+// of the fit partials; one warp per simulation, once per step, before the
+// assembly's CTAs read it.
+__global__ void k_theta(const SimDev* __restrict__ sims, const int* __restrict__ active) {
+  const SimDev& S = sims[active[blockIdx.x]];
+  if (S.status[0] != kStOk) return;
+  __shared__ double rsh[kMaxM];
+  const int M = S.M, q = threadIdx.x;
+  if (q < M) {
+    double r = 0.0;
+    for (int t = 0; t < S.n_tiles; ++t) r += S.fit_part[(size_t)t * kMaxM + q];
+    rsh[q] = r;
   }
+  __syncwarp();
+  if (q < M) {
+    double th = 0.0;
+    for (int j = 0; j < M; ++j) th = fma(S.Gpinv[q * M + j], rsh[j], th);
+    S.theta[q] = th;
+  }
+}
+
+// Eq. reducedSystem: A = c + sum_q theta_q b_q and rhs = e + sum_q theta_q d_q,
+// the components stored as Q = M + 1 consecutive arrays per block (weight 1,
+// then theta). One CTA per block of A or per subdomain's rhs.
+__device__ __forceinline__ void load_weights(const SimDev& S, double* w) {
+  if (threadIdx.x <= S.M) w[threadIdx.x] = threadIdx.x == 0 ? 1.0 : S.theta[threadIdx.x - 1];
   __syncthreads();
 }
 
@@ -48,8 +55,7 @@ __global__ void k_assemble(const SimDev* __restrict__ sims, const int* __restric
   const int bidx = blockIdx.x;
   if (bidx >= S.n_blocks + S.n_sub || S.status[0] != kStOk) return;
   __shared__ double w[kMaxM + 1];
-  __shared__ double rsh[kMaxM];
-  compute_weights(S, w, rsh, bidx == 0);
+  load_weights(S, w);
   const int Q = S.M + 1;
   if (bidx < S.n_blocks) {
     const long long o = S.aoff[bidx];
@@ -78,8 +84,7 @@ __global__ void k_assemble32(const SimDev* __restrict__ sims, const int* __restr
   const int bidx = blockIdx.x;
   if (bidx >= S.n_blocks + S.n_sub || S.status[0] != kStOk) return;
   __shared__ double w[kMaxM + 1];
-  __shared__ double rsh[kMaxM];
-  compute_weights(S, w, rsh, bidx == 0);
+  load_weights(S, w);
   float wf[kMaxM + 1];
   const int Q = S.M + 1;
 #pragma unroll
@@ -324,6 +329,8 @@ __device__ CtaSmem<T> cta_carve_and_load(const SimDev& S, unsigned char* b) {
     }
     m.flag[0] = 0;
     m.flag[1] = 0;
+    m.flag[2] = 0;  // block rows of cfactor_mma: all
+    m.flag[3] = ns;
     fence_mbar_init();
   }
   __syncthreads();
@@ -815,16 +822,20 @@ __device__ __noinline__ void mma_block(const float* A, int lda, float* C, int ld
 // update into block j+1; R_kk -= X_j X_j^T. Every warp waits for every chunk of the ring before it
 // releases it (whether it used it or not), so no warp releases a slot ahead
 // of the chunk's user. The diagonal block is factored by the leader warp as in
-// cfactor. Same results contract as cfactor.
+// cfactor. Same results contract as cfactor. Only block rows [m.flag[2],
+// m.flag[3]) are computed (cta_carve_and_load sets all rows); the rows
+// before m.flag[2] must already be in LT and Linv. The range is read from
+// shared memory, so that it takes no register through the row loop.
 __device__ int cfactor_mma(const SimDev& S, float* LT, float* Linv, CtaSmem<float>& m) {
   using T = float;
   const SolveMeta& mt = m.mt;
-  const int nsub = S.n_sub, Sx = S.Sx;
+  const int Sx = S.Sx;
+  const volatile int* rows = m.flag + 2;
   const int lane = threadIdx.x & 31, w = vwarp();
   T* R = m.R;
   Ring<T> rg{m.ring, m.full, m.empty, m.dl, kRing, 0u, 0u, m.ph, m.eph, m.used, m.fpar, true};
 #pragma unroll 1
-  for (int k = 0; k < nsub; ++k) {
+  for (int k = rows[0]; k < rows[1]; ++k) {
     const int jl = jlo_of(k, Sx);
     const int base = mt.xoff[jl];
     const int Nk = mt.NE[k];
@@ -1442,9 +1453,11 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
 // the last solve, [1] FP64 redos, [2] FP32 factorisations, [3] refactorings
 // forced by a stale factor that did not converge, [4] correction passes,
 // [5] reduced solves (all since load), [6] the FP32 factor's state: 0 none,
-// a >= 1 computed a - 1 steps ago, [7] refactor at the next step.
+// a >= 1 computed a - 1 steps ago, [7] refactor at the next step, [8] the
+// FP32 buffer holding the current factor (0 or 1), [9] 1 if the current
+// factor was built in stages.
 constexpr int kInfoPasses = 0, kInfoRedo64 = 1, kInfoFactors = 2, kInfoStaleRetry = 3, kInfoPassSum = 4,
-              kInfoSolves = 5, kInfoAge = 6, kInfoRefactor = 7;
+              kInfoSolves = 5, kInfoAge = 6, kInfoRefactor = 7, kInfoBuf = 8, kInfoStaged = 9;
 constexpr double kRefineTol = 1e-12;
 // The conjugate gradients stop tighter: their error is not the rounding noise
 // of a direct solve but a systematic remainder, which a 50-step trajectory of
@@ -1593,9 +1606,53 @@ constexpr int kStRetry32 = 2;  // transient status: refactor in FP32 now and sol
 constexpr int kRefactorPasses = 10;
 constexpr int kStalePasses = 12;
 
-__device__ __forceinline__ bool wants_factor(const SimDev& S) {
-  const int age = S.info[kInfoAge];
-  return age == 0 || age > S.refactor_period || S.info[kInfoRefactor] != 0;
+// Staged refactorisation (refactor_stages R > 1): the next factor is built
+// in the idle FP32 buffer over the last R steps of the current one's period,
+// a contiguous range of about n_sub / R block rows per step, each row from
+// that step's matrix (the lower triangular result with a positive diagonal
+// is still a symmetric positive definite preconditioner). The build's last
+// stage runs when the current factor expires (age refactor_period + 1) and
+// the solve of that step already uses the new factor. So no step pays a whole
+// factorisation; the price is a factor whose early rows are up to R - 1 steps
+// older. A fresh factor (age 0, or a refactorisation forced by a slow or
+// failed solve) is still computed whole, in the current buffer.
+struct FactorPlan {
+  int k0, k1;  // block rows to compute (k1 <= k0: none)
+  int buf;     // FP32 buffer written
+  bool whole, last_stage;
+};
+
+__device__ __forceinline__ FactorPlan factor_plan(const SimDev& S, const volatile int* info) {
+  const int age = info[kInfoAge], P = S.refactor_period, R = S.refactor_stages;
+  const int cur = info[kInfoBuf] & 1;
+  FactorPlan p{0, 0, cur, false, false};
+  if (age == 0 || info[kInfoRefactor] != 0 || (R <= 1 && age > P)) {
+    p.k1 = S.n_sub;
+    p.whole = true;
+    return p;
+  }
+  if (R <= 1) return p;
+  const int st = age - (P - R + 2);  // stage of the build in progress
+  if (st < 0) return p;
+  if (st >= R) {  // past the period without a completed build: whole, now
+    p.k1 = S.n_sub;
+    p.whole = true;
+    return p;
+  }
+  p.k0 = (int)((long long)S.n_sub * st / R);
+  p.k1 = (int)((long long)S.n_sub * (st + 1) / R);
+  p.buf = cur ^ 1;
+  p.last_stage = st == R - 1;
+  return p;
+}
+
+// The two FP32 factor buffers of the mixed solver share the FP64 factor's
+// storage (8 bytes per element): buffer 1 starts after buffer 0's elements.
+__device__ __forceinline__ float* fac32_lt(const SimDev& S, const SolveMeta& mt, int buf) {
+  return reinterpret_cast<float*>(S.L) + (buf ? mt.loff[S.n_sub] : 0);
+}
+__device__ __forceinline__ float* fac32_inv(const SimDev& S, const SolveMeta& mt, int buf) {
+  return reinterpret_cast<float*>(S.Linv) + (buf ? mt.ioff[S.n_sub] : 0);
 }
 
 // Initial guess of the warm solve: the quadratic extrapolation
@@ -1625,19 +1682,46 @@ __global__ void __launch_bounds__(kThreads, 4) k_factor32(const SimDev* __restri
   const int a = blockIdx.x;
   if (a >= n_active) return;
   const SimDev& S = sims[active[a]];
-  if (S.status[0] != kStOk || !wants_factor(S)) return;
+  if (S.status[0] != kStOk) return;
+  int buf;
+  {
+    const FactorPlan p = factor_plan(S, S.info);
+    if (p.k1 <= p.k0 && !p.last_stage) return;
+    buf = p.buf;
+  }
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
-  const int f = cfactor_mma(S, reinterpret_cast<float*>(S.L), reinterpret_cast<float*>(S.Linv), m);
   if (threadIdx.x == 0) {
-    if (f == kFacOk) {
+    const FactorPlan p = factor_plan(S, S.info);
+    m.flag[2] = p.k0;  // an empty range (a last stage of no rows) computes nothing
+    m.flag[3] = p.k1;
+  }
+  __syncthreads();
+  const int f = cfactor_mma(S, fac32_lt(S, m.mt, buf), fac32_inv(S, m.mt, buf), m);
+  if (threadIdx.x == 0) {
+    // S.info is unchanged until here: the plan is read again (volatile: not
+    // kept in registers through the factorisation).
+    const FactorPlan p = factor_plan(S, S.info);
+    if (p.whole) {
+      if (f == kFacOk) {
+        S.info[kInfoFactors] += 1;
+        S.info[kInfoAge] = 1;
+        S.info[kInfoRefactor] = 0;
+        S.info[kInfoStaged] = 0;
+      } else {
+        S.info[kInfoAge] = 0;
+        S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
+      }
+    } else if (f == kFacTimeout) {
+      S.status[0] = kStTimeout;
+    } else if (f == kFacPivot) {
+      S.info[kInfoRefactor] = 1;  // abandon the build: a whole factorisation at the next step
+    } else if (p.last_stage) {  // the build is complete: it serves from this step's solve on
+      S.info[kInfoBuf] = p.buf;
       S.info[kInfoFactors] += 1;
       S.info[kInfoAge] = 1;
-      S.info[kInfoRefactor] = 0;
-    } else {
-      S.info[kInfoAge] = 0;
-      S.status[0] = f == kFacPivot ? kStRetry64 : kStTimeout;
+      S.info[kInfoStaged] = 1;
     }
   }
 }
@@ -1652,11 +1736,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_refine32(const SimDev* __restri
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
-  const bool fresh = S.info[kInfoAge] == 1;
+  const bool fresh = S.info[kInfoAge] == 1 && S.info[kInfoStaged] == 0;  // a staged build counts as stale
   const int budget = max(iters, kStalePasses - 1);
   extrapolate_guess(S);
-  const int r = csolve_pcg<float>(S, reinterpret_cast<const float*>(S.L), reinterpret_cast<const float*>(S.Linv),
-                                  budget, m);
+  const int cur = S.info[kInfoBuf] & 1;
+  const int r = csolve_pcg<float>(S, fac32_lt(S, m.mt, cur), fac32_inv(S, m.mt, cur), budget, m);
   if (threadIdx.x == 0) {
     if (r == kRefOk) {
       S.info[kInfoSolves] += 1;
@@ -1686,8 +1770,9 @@ __global__ void __launch_bounds__(kThreads) k_retry32(const SimDev* __restrict__
   extern __shared__ double sm[];
   unsigned char* b = reinterpret_cast<unsigned char*>(sm);
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
-  float* Lf = reinterpret_cast<float*>(S.L);
-  float* Lif = reinterpret_cast<float*>(S.Linv);
+  const int cur = S.info[kInfoBuf] & 1;
+  float* Lf = fac32_lt(S, m.mt, cur);
+  float* Lif = fac32_inv(S, m.mt, cur);
   const int f = cfactor_mma(S, Lf, Lif, m);
   if (f != kFacOk) {
     if (threadIdx.x == 0) {
@@ -1701,6 +1786,7 @@ __global__ void __launch_bounds__(kThreads) k_retry32(const SimDev* __restrict__
     S.info[kInfoFactors] += 1;
     S.info[kInfoAge] = 2;  // computed this step, and served it
     S.info[kInfoRefactor] = 0;
+    S.info[kInfoStaged] = 0;
     if (r == kRefTimeout) S.status[0] = kStTimeout;
     else if (r != kRefOk) S.status[0] = kStRetry64;
     else S.info[kInfoSolves] += 1;
@@ -1826,6 +1912,7 @@ __global__ void __launch_bounds__(kThreads) k_csolve_static(SimDev S, int mode, 
 // entry of A and b the same way, so the choice does not change the result.
 void launch_assemble(const SimDev* sims, const int* active, int n_active, int max_blocks,
                      int mixed, cudaStream_t st, int threads) {
+  k_theta<<<n_active, 32, 0, st>>>(sims, active);
   if (mixed)
     k_assemble32<<<dim3(max_blocks, n_active), threads, 0, st>>>(sims, active);
   else

@@ -93,6 +93,7 @@ struct lrbms_ctx {
   int solver = LRBMS_SOLVE_FP64;
   int refine_iters = 1;
   int refactor_period = 8;
+  int refactor_stages = 1;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t admit_stream = nullptr;  // admission copies and kernels (overlap the steps)
@@ -156,7 +157,8 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   if (!out || !cfg) return LRBMS_E_ARG;
   *out = nullptr;
   if (cfg->max_slots < 1 || cfg->hbm_budget == 0 || cfg->refine_iters < 0 || cfg->refine_iters > 16 ||
-      cfg->refactor_period < 0 || cfg->refactor_period > 1000 ||
+      cfg->refactor_period < 0 || cfg->refactor_period > 1000 || cfg->refactor_stages < 0 ||
+      cfg->refactor_stages > (cfg->refactor_period > 0 ? cfg->refactor_period : 8) ||
       (cfg->precision != LRBMS_FP64 && cfg->precision != LRBMS_MIXED) ||
       (cfg->solver != LRBMS_SOLVE_FP64 && cfg->solver != LRBMS_SOLVE_MIXED))
     return LRBMS_E_ARG;
@@ -166,6 +168,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   ctx->solver = cfg->solver;
   ctx->refine_iters = cfg->refine_iters > 0 ? cfg->refine_iters : (cfg->solver == LRBMS_SOLVE_MIXED ? 6 : 1);
   ctx->refactor_period = cfg->refactor_period > 0 ? cfg->refactor_period : 8;  // measured best at 512 sims
+  ctx->refactor_stages = cfg->refactor_stages > 0 ? cfg->refactor_stages : 1;
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     delete ctx;
@@ -363,7 +366,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   const size_t o_fitp = L.add(8 * (size_t)n_tiles * lrbms::kMaxM);
   const size_t o_cflp = L.add(8 * (size_t)n_tiles), o_massp = L.add(8 * (size_t)n_tiles);
   const size_t o_scal = L.add(8 * 4), o_theta = L.add(8 * lrbms::kMaxM);
-  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 8), o_fitr = L.add(4),
+  const size_t o_status = L.add(4), o_steps = L.add(4), o_info = L.add(4 * 12), o_fitr = L.add(4),
                o_inj = L.add(4);
   const size_t o_sched = L.add(8 * lrbms::sched_words(n_sub, Sx));
   (void)d_tot;
@@ -407,6 +410,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   d.sunl = dg ? (double*)P(o_unl) : nullptr;
   d.x = (double*)P(o_x); d.xp = (double*)P(o_xp); d.xpp = (double*)P(o_xpp); d.b = (double*)P(o_b); d.y = (double*)P(o_y);
   d.refactor_period = ctx->refactor_period;
+  d.refactor_stages = ctx->refactor_stages;
   d.rv = (double*)P(o_rv); d.dv = (double*)P(o_dv); d.pv = (double*)P(o_pv); d.qv = (double*)P(o_qv);
   d.A = (double*)P(o_A); d.L = (double*)P(o_L); d.Linv = (double*)P(o_Li);
   d.fit_part = (double*)P(o_fitp); d.cfl_part = (double*)P(o_cflp); d.mass_part = (double*)P(o_massp);
@@ -450,7 +454,7 @@ int lrbms_offline_load(lrbms_ctx* ctx, const lrbms_problem* pr, const lrbms_offl
   CK(cudaMemsetAsync(P(o_theta), 0, 8 * lrbms::kMaxM, st));
   CK(cudaMemsetAsync(P(o_status), 0, 4, st));
   CK(cudaMemsetAsync(P(o_steps), 0, 4, st));
-  CK(cudaMemsetAsync(P(o_info), 0, 4 * 8, st));
+  CK(cudaMemsetAsync(P(o_info), 0, 4 * 12, st));
   CK(cudaMemsetAsync(P(o_fitr), 0, 4, st));
   CK(cudaMemsetAsync(P(o_inj), 0, 4, st));
   if (dg) CK(cudaMemsetAsync(P(o_slope), 0, 32 * (size_t)n_cells, st));  // s0 piecewise constant
@@ -517,7 +521,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     ctx->last_active = act;
   }
   const int mixed = ctx->precision == LRBMS_MIXED;
-  const int per_step = 6 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1)  // mixed solve: factor (where
+  const int per_step = 7 + (ctx->solver == LRBMS_SOLVE_MIXED ? 4 : 1)  // mixed solve: factor (where
                        + (any_dg ? 2 : 0);                             // needed), refine, retry, FP64 redo
   CK(lrbms::prepare_chol_solve(ctx->solver, sh));  // kernel attributes, outside any capture
   CK(lrbms::prepare_flux_cfl(flux_smem));
@@ -536,7 +540,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    auto best_of = [&](const std::vector<int>& sizes, auto&& launch) -> int {
+    auto best_of = [&](const std::vector<int>& sizes, int kernels, auto&& launch) -> int {
       int best = sizes[0];
       float best_ms = 1e30f;
       for (int t : sizes) {
@@ -548,15 +552,15 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        ctx->launches += 3;
+        ctx->launches += 3 * kernels;
         if (ms < best_ms) best_ms = ms, best = t;
       }
       return best;
     };
-    const int ta = best_of({64, 128, 256, 512}, [&](int t) {
+    const int ta = best_of({64, 128, 256, 512}, 2, [&](int t) {  // theta, then the assembly
       lrbms::launch_assemble(ctx->d_sims, ctx->d_active, n_sims, max_blocks, mixed, st, t);
     });
-    const int tr = best_of({128, 256, 512, 1024}, [&](int t) {
+    const int tr = best_of({128, 256, 512, 1024}, 1, [&](int t) {
       lrbms::launch_reconstruct(ctx->d_sims, ctx->d_active, n_sims, max_sub, mixed, st, t);
     });
     cudaEventDestroy(e0);

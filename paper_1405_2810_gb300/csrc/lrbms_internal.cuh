@@ -34,6 +34,7 @@ struct SimDev {
   int n_blocks;     // n_sub + n_cf assembled blocks
   int relperm, swapped, prof_mode, dt_mode;
   int refactor_period;  // steps one FP32 factor serves (mixed solver)
+  int refactor_stages;  // steps over which the next FP32 factor is built (1: all at once)
   int vel_mode;         // mobility of the velocity: 0 lambda(s^n), 1 fitted (needs theta of the step)
   int transport;        // 0: P0 finite volume upwind; 1: P1 DG with the slope limiter
   double hx, hy, vol, c_pen, Lf, inv_eta_w, inv_eta_o, cfl, dt_fixed, dt_max;

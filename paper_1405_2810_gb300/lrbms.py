@@ -58,7 +58,7 @@ class LrbmsError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_slots", C.c_int), ("hbm_budget", C.c_size_t),
                 ("stream", C.c_void_p), ("device", C.c_int), ("solver", C.c_int),
-                ("refine_iters", C.c_int), ("refactor_period", C.c_int)]
+                ("refine_iters", C.c_int), ("refactor_period", C.c_int), ("refactor_stages", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -155,8 +155,9 @@ def _as(a, dtype):
 
 # ------------------------------------------------------------------ C-ABI names
 def lrbms_create(precision=LRBMS_FP64, max_slots=64, hbm_budget=8 << 30, stream=None, device=0,
-                 solver=LRBMS_SOLVE_FP64, refine_iters=0, refactor_period=0):
-    cfg = Config(precision, max_slots, hbm_budget, stream, device, solver, refine_iters, refactor_period)
+                 solver=LRBMS_SOLVE_FP64, refine_iters=0, refactor_period=0, refactor_stages=0):
+    cfg = Config(precision, max_slots, hbm_budget, stream, device, solver, refine_iters, refactor_period,
+                 refactor_stages)
     h = C.c_void_p()
     _check(None, library().lrbms_create(C.byref(h), C.byref(cfg)))
     return h

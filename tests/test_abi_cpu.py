@@ -45,3 +45,18 @@ def test_create_rejects_bad_config():
     with pytest.raises(lrbms.LrbmsError) as ei:
         lrbms.lrbms_create(max_slots=0)
     assert ei.value.code == lrbms.LRBMS_E_ARG
+    for kw in (dict(refactor_stages=-1), dict(refactor_period=4, refactor_stages=5),
+               dict(refactor_stages=9)):  # more stages than steps in the (default 8) period
+        with pytest.raises(lrbms.LrbmsError) as ei:
+            lrbms.lrbms_create(solver=lrbms.LRBMS_SOLVE_MIXED, **kw)
+        assert ei.value.code == lrbms.LRBMS_E_ARG
+
+
+def test_config_struct_matches_header():
+    """The binding's lrbms_config fields are the header's, in the header's order."""
+    from paper_1405_2810_gb300 import lrbms
+    src = open(os.path.join(ROOT, "include", "lrbms.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*?)\} lrbms_config;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = [re.findall(r"(\w+)\s*$", decl.strip())[0] for decl in body.split(";") if decl.strip()]
+    assert names == [f[0] for f in lrbms.Config._fields_]
