@@ -350,7 +350,13 @@ int lrbms_offline_build(lrbms_ctx* ctx, int n_prob, const lrbms_problem* probs,
  * results are unchanged up to round-off; the stored bytes differ. The copy
  * starts from src's current saturation, at time 0. It runs on the admission
  * stream; if src was in the last stepped batch the call first waits for the
- * context stream. */
+ * context stream. Warm admission (mixed solver, rot == NULL, src never
+ * stepped): the copy has src's matrix, so it starts with src's FP32 factor.
+ * The first such call computes that factor once for src (fit, theta,
+ * assembly and factorisation of src alone, as its own first step would);
+ * later calls only copy it. The results are bitwise those of a cold start;
+ * only the first step's factorisation is saved. lrbms_set_saturation on src
+ * drops the precomputed factor. */
 int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_id);
 
 /* Like lrbms_step, with the saturation exchanged with caller memory: before

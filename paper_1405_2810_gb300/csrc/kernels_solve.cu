@@ -1947,6 +1947,14 @@ cudaError_t prepare_chol_solve(int mode, const SolveShape& sh) {
 
 // One CTA of kNW warps per simulation; the CTAs spread over the SMs, as many
 // per SM as their shared memory allows (attributes from prepare_chol_solve).
+cudaError_t launch_factor32(const SimDev* sims, const int* active, int n_active, const SolveShape& sh,
+                            cudaStream_t st) {
+  if (n_active <= 0) return cudaSuccess;
+  const size_t s32 = warp_smem_bytes(sh.n_sub, sh.panel_words, sh.N, sizeof(float));
+  k_factor32<<<n_active, kThreads, s32, st>>>(sims, active, n_active);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
                               const SolveShape& sh, cudaStream_t st) {
   if (n_active <= 0) return cudaSuccess;

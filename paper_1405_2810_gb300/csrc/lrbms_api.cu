@@ -81,6 +81,7 @@ class Arena {
 
 struct Slot {
   bool used = false;
+  bool prefactored = false;  // at rest, holding the FP32 factor of its current matrix
   size_t off = 0, bytes = 0;
   SimDev d{};
 };
@@ -103,7 +104,7 @@ struct lrbms_ctx {
   Arena arena;
   std::vector<Slot> slots;
   SimDev* d_sims = nullptr;
-  int* d_active = nullptr;
+  int* d_active = nullptr;    // [max_slots + 1]: the step's list, then the admission stream's one entry
   std::vector<int> last_active;
   const double** d_io = nullptr;  // [2 * max_slots] saturation exchange pointers
   std::string err;
@@ -185,7 +186,7 @@ int lrbms_create(lrbms_ctx** out, const lrbms_config* cfg) {
   }
   if (ctx->arena.init(cfg->hbm_budget) != cudaSuccess ||
       cudaMalloc(&ctx->d_sims, sizeof(SimDev) * cfg->max_slots) != cudaSuccess ||
-      cudaMalloc(&ctx->d_active, sizeof(int) * cfg->max_slots) != cudaSuccess ||
+      cudaMalloc(&ctx->d_active, sizeof(int) * (cfg->max_slots + 1)) != cudaSuccess ||
       cudaMalloc(&ctx->d_io, sizeof(double*) * 2 * cfg->max_slots) != cudaSuccess ||
       cudaMalloc(&ctx->d_status, sizeof(int) * cfg->max_slots) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(int) * cfg->max_slots) != cudaSuccess ||
@@ -237,6 +238,57 @@ int lrbms_internal_sim(lrbms_ctx* ctx, int id, SimDev* out) {
   return LRBMS_OK;
 }
 int lrbms_internal_fail(lrbms_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+
+// Warm admission (mixed solver). A resting simulation that has not stepped
+// gets the FP32 factor of its current matrix once, on the admission stream:
+// the fit, theta, the assembly and a whole factorisation of that one
+// simulation, exactly as its own first step would compute them (that step
+// then finds a factor of age 1 and reuses it). The factor and the solver
+// state are copied into dst, a new simulation with the same basis and state
+// (so the same matrix), whose first step then reuses them too: the results
+// are bitwise those of a cold start, without the first step's whole
+// factorisation. If the factorisation fails, src is restored and nothing
+// is copied (both factor at their first step).
+int lrbms_internal_share_factor(lrbms_ctx* ctx, int src, int dst) {
+  if (ctx->solver != LRBMS_SOLVE_MIXED || !valid_sim(ctx, src) || !valid_sim(ctx, dst) || src == dst)
+    return LRBMS_OK;
+  Slot& ss = ctx->slots[src];
+  const SimDev& d = ss.d;
+  const SimDev& t = ctx->slots[dst].d;
+  if (t.n_sub != d.n_sub || t.N != d.N || t.panel_words != d.panel_words) return LRBMS_OK;
+  cudaStream_t st = ctx->admit_stream;
+  int* act = ctx->d_active + ctx->slots.size();
+  if (!ss.prefactored) {
+    CK(cudaMemcpyAsync(act, &src, sizeof(int), cudaMemcpyHostToDevice, st));
+    lrbms::launch_fit(ctx->d_sims, act, 1, d.n_tiles, st);
+    lrbms::launch_assemble(ctx->d_sims, act, 1, d.n_blocks + d.n_sub, ctx->precision == LRBMS_MIXED, st, 128);
+    const lrbms::SolveShape sh{d.n_sub, d.panel_words, d.max_w, d.N};
+    CK(lrbms::prepare_chol_solve(ctx->solver, sh));
+    CK(lrbms::launch_factor32(ctx->d_sims, act, 1, sh, st));
+    ctx->launches += 4;
+    int status = -1, age = -1;
+    CK(cudaMemcpyAsync(&status, d.status, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&age, d.info + 6, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (status != LRBMS_OK || age != 1) {  // undo: src factors at its own first step
+      CK(cudaMemsetAsync(d.status, 0, 4, st));
+      CK(cudaMemsetAsync(d.info, 0, 4 * 12, st));
+      CK(cudaStreamSynchronize(st));
+      return LRBMS_OK;
+    }
+    ss.prefactored = true;
+  }
+  long long ends[2] = {0, 0};  // loff[n_sub], ioff[n_sub]
+  CK(cudaMemcpyAsync(&ends[0], d.loff + d.n_sub, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ends[1], d.ioff + d.n_sub, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpyAsync(t.L, d.L, 8 * (size_t)ends[0], cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(t.Linv, d.Linv, 8 * (size_t)ends[1], cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(t.info, d.info, 4 * 12, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->slots[dst].prefactored = true;
+  return LRBMS_OK;
+}
 SimDev* lrbms_internal_dsims(lrbms_ctx* ctx) { return ctx->d_sims; }
 void lrbms_internal_count(lrbms_ctx* ctx, long long n) { ctx->launches += n; }
 
@@ -504,6 +556,7 @@ int lrbms_step(lrbms_ctx* ctx, int n_sims, const int* ids, int n_steps, int* sta
   lrbms::SolveShape sh{0, 0, 0, 0};
   for (int id : act) {
     if (!valid_sim(ctx, id)) return fail(ctx, LRBMS_E_STATE, "unknown simulation id");
+    ctx->slots[id].prefactored = false;  // it leaves the state its factor was computed for
     const SimDev& d = ctx->slots[id].d;
     sh.n_sub = std::max(sh.n_sub, d.n_sub);
     sh.panel_words = std::max(sh.panel_words, d.panel_words);
@@ -855,6 +908,10 @@ int lrbms_set_saturation(lrbms_ctx* ctx, int id, const double* s) {
   CK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(d.s + (size_t)(steps & 1) * d.n_cells, s, 8 * (size_t)d.n_cells, cudaMemcpyDefault));
   CK(cudaMemset(d.fit_ready, 0, 4));  // the next step fits the new saturation
+  if (ctx->slots[id].prefactored) {   // the factor of the old state no longer matches
+    CK(cudaMemset(d.info, 0, 4 * 12));
+    ctx->slots[id].prefactored = false;
+  }
   if (d.sslope) CK(cudaMemset(d.sslope + (size_t)(steps & 1) * 2 * d.n_cells, 0, 16 * (size_t)d.n_cells));
   return LRBMS_OK;
 }

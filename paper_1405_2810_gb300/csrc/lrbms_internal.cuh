@@ -170,6 +170,9 @@ __host__ __device__ inline void solve_offsets(int n_sub, int Sx, const int* NE, 
 // factorisation meets a non-positive pivot). Both refine with FP64 residuals.
 cudaError_t launch_chol_solve(const SimDev* sims, const int* active, int n_active, int mode, int iters,
                               const SolveShape& sh, cudaStream_t st);
+// The mixed solver's FP32 factorisation step alone (k_factor32), after prepare_chol_solve.
+cudaError_t launch_factor32(const SimDev* sims, const int* active, int n_active, const SolveShape& sh,
+                            cudaStream_t st);
 // Shared-memory attributes of the solve kernels for a launch shape; call
 // before launch_chol_solve (and outside a stream capture).
 cudaError_t prepare_chol_solve(int mode, const SolveShape& sh);

@@ -1027,6 +1027,7 @@ extern "C" lrbms::SimDev* lrbms_internal_dsims(lrbms_ctx* ctx);
 extern "C" cudaStream_t lrbms_internal_admit_stream(lrbms_ctx* ctx);
 extern "C" bool lrbms_internal_in_last_batch(lrbms_ctx* ctx, int id);
 extern "C" void lrbms_internal_count(lrbms_ctx* ctx, long long n);
+extern "C" int lrbms_internal_share_factor(lrbms_ctx* ctx, int src, int dst);
 
 #define BCK(call)                                                              \
   do {                                                                         \
@@ -1758,7 +1759,12 @@ extern "C" int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_
   off.Phi = uPhi; off.Dblk = ucomp; off.Fblk = n_cf ? ucomp + (size_t)Q * aoff[n_sub] : nullptr;
   off.rhs = urhs; off.c_pen = d.c_pen; off.Lf = d.Lf;
   BCK(cudaStreamSynchronize(st));
-  return lrbms_offline_load(ctx, &pr, &off, sim_id);
+  const int rc = lrbms_offline_load(ctx, &pr, &off, sim_id);
+  if (rc != LRBMS_OK) return rc;
+  // Same basis and state as a source that has not stepped: the same matrix,
+  // so the new simulation can start with the source's FP32 factor.
+  if (!rot && steps == 0) return lrbms_internal_share_factor(ctx, src, *sim_id);
+  return LRBMS_OK;
 }
 
 // Algorithm 1 (the high-dimensional IMPES scheme) on resident simulations:

@@ -150,3 +150,36 @@ def test_staged_refactorisation(L, label):
         assert rel(s_gpu, s_ref) < TOL and close_elementwise(s_gpu, s_ref, TOL) <= TOL
         vol = prob.poro * m.grid.vol
         assert abs((np.sum(vol * s_gpu) - np.sum(vol * prob.s0)) + mg) <= 1e-13 * abs(mg)
+
+
+@pytest.mark.parametrize("stages", [1, 4])
+def test_warm_admission_is_bitwise_a_cold_start(L, stages):
+    """Unrotated clones of a resting simulation start with its FP32 factor
+    (computed once for the source): the source, two clones and a cold load
+    of the same data give bitwise the same states, solutions and solver
+    counters over LATE steps; a source whose saturation was set afresh drops
+    the precomputed factor and again matches a cold load."""
+    c = shape_case("bench-8x8")
+    prob, m, co, off = c
+    ctx = L.lrbms_create(hbm_budget=2 << 30, max_slots=8, solver=1, refactor_period=4, refactor_stages=stages)
+    src = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+    warm = [L.lrbms_clone(ctx, src, None), L.lrbms_clone(ctx, src, None)]
+    cold = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+    info0 = [L.lrbms_get_field(ctx, i, L.FIELD_SOLVE_INFO, dtype=np.int32) for i in (src, *warm, cold)]
+    assert [int(v[2]) for v in info0] == [1, 1, 1, 0]  # factors held before any step
+    other = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+    moved = L.lrbms_clone(ctx, other, None)
+    s_late = shape_states("bench-8x8", LATE)[LATE]
+    L.lrbms_set_saturation(ctx, other, s_late)  # drops other's factor
+    cold_late = L.lrbms_offline_load(ctx, abi_problem(prob, m), abi_offline(co, off))
+    L.lrbms_set_saturation(ctx, cold_late, s_late)
+    ids = [src, *warm, cold, other, cold_late, moved]
+    assert list(L.lrbms_step(ctx, ids, LATE)) == [0] * len(ids)
+    fields = {i: (L.lrbms_get_field(ctx, i, L.FIELD_S), L.lrbms_get_field(ctx, i, L.FIELD_X),
+                  L.lrbms_get_field(ctx, i, L.FIELD_SOLVE_INFO, dtype=np.int32)) for i in ids}
+    for i in (src, *warm, moved):
+        for a, b in zip(fields[i], fields[cold]):
+            assert np.array_equal(a, b), i
+    for a, b in zip(fields[other], fields[cold_late]):
+        assert np.array_equal(a, b)
+    L.lrbms_destroy(ctx)
