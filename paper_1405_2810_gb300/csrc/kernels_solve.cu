@@ -1694,7 +1694,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_factor32(const SimDev* __restri
   CtaSmem<float> m = cta_carve_and_load<float>(S, b);
   if (threadIdx.x == 0) {
     const FactorPlan p = factor_plan(S, S.info);
-    m.flag[2] = p.k0;  // an empty range (a last stage of no rows) computes nothing
+    m.flag[2] = p.k0;  // block rows of this step (an empty range computes nothing)
     m.flag[3] = p.k1;
   }
   __syncthreads();
