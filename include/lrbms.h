@@ -452,6 +452,17 @@ int lrbms_tuned_threads(lrbms_ctx* ctx, int n_sims, const int* sim_ids, int* ass
  * fires once. */
 int lrbms_test_withhold_copy(lrbms_ctx* ctx, int sim_id);
 
+/* Test hook (host only, no device work; the paper has no counterpart): the
+ * mixed solver's factorisation plan for one step of a simulation with n_sub
+ * block rows, the given refactor period and stages (1 <= stages <= period)
+ * and solver state info[12] (the kernels' internal counters: [6] factor age,
+ * [7] forced refactorisation, [8] current FP32 buffer). out[5] receives the
+ * block rows [out[0], out[1]) that the step's factor kernel computes, the
+ * buffer it writes (out[2]), whether it is a whole factorisation (out[3])
+ * and whether it completes a staged build (out[4]). LRBMS_E_ARG on invalid
+ * sizes. */
+int lrbms_test_factor_plan(int n_sub, int refactor_period, int refactor_stages, const int* info, int* out);
+
 /* Wait for all enqueued work. */
 int lrbms_sync(lrbms_ctx* ctx);
 

@@ -1622,7 +1622,7 @@ struct FactorPlan {
   bool whole, last_stage;
 };
 
-__device__ __forceinline__ FactorPlan factor_plan(const SimDev& S, const volatile int* info) {
+__host__ __device__ __forceinline__ FactorPlan factor_plan(const SimDev& S, const volatile int* info) {
   const int age = info[kInfoAge], P = S.refactor_period, R = S.refactor_stages;
   const int cur = info[kInfoBuf] & 1;
   FactorPlan p{0, 0, cur, false, false};
@@ -1979,6 +1979,23 @@ constexpr int kMaxDevices = 64;
 constexpr int kNoAllocMaxSub = 4096;
 unsigned char* g_noalloc_dev[kMaxDevices] = {nullptr};
 }  // namespace
+
+extern "C" int lrbms_test_factor_plan(int n_sub, int refactor_period, int refactor_stages, const int* info,
+                                      int* out) {
+  if (n_sub < 1 || refactor_period < 1 || refactor_stages < 1 || refactor_stages > refactor_period || !info || !out)
+    return LRBMS_E_ARG;
+  lrbms::SimDev S{};
+  S.n_sub = n_sub;
+  S.refactor_period = refactor_period;
+  S.refactor_stages = refactor_stages;
+  const lrbms::FactorPlan p = lrbms::factor_plan(S, info);
+  out[0] = p.k0;
+  out[1] = p.k1;
+  out[2] = p.buf;
+  out[3] = p.whole ? 1 : 0;
+  out[4] = p.last_stage ? 1 : 0;
+  return LRBMS_OK;
+}
 
 extern "C" int lrbms_solve_noalloc(int Sx, int Sy, const int* N_E, const double* A, const double* rhs,
                                    double* x, int solver, int refine_iters, void* stream) {

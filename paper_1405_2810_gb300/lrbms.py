@@ -45,8 +45,8 @@ EXPORTED = ["lrbms_create", "lrbms_destroy", "lrbms_offline_load", "lrbms_offlin
             "lrbms_release", "lrbms_clone", "lrbms_step", "lrbms_step_io", "lrbms_profile_start", "lrbms_profile_read",
             "lrbms_run", "lrbms_get_state", "lrbms_set_saturation", "lrbms_get_field",
             "lrbms_field_bytes", "lrbms_sync", "lrbms_memory", "lrbms_launch_count", "lrbms_solve_noalloc",
-            "lrbms_fine_step", "lrbms_step_status", "lrbms_test_withhold_copy", "lrbms_tuned_threads",
-            "lrbms_last_error", "lrbms_set_slopes"]
+            "lrbms_fine_step", "lrbms_step_status", "lrbms_test_withhold_copy", "lrbms_test_factor_plan",
+            "lrbms_tuned_threads", "lrbms_last_error", "lrbms_set_slopes"]
 
 
 class LrbmsError(RuntimeError):
@@ -113,6 +113,7 @@ def library() -> C.CDLL:
         lib.lrbms_fine_step.argtypes = [vp, i, vp, i, vp]
         lib.lrbms_step_status.argtypes = [vp, i, vp]
         lib.lrbms_test_withhold_copy.argtypes = [vp, i]
+        lib.lrbms_test_factor_plan.argtypes = [i, i, i, vp, vp]
         lib.lrbms_tuned_threads.argtypes = [vp, i, vp, C.POINTER(i), C.POINTER(i)]
         lib.lrbms_run.argtypes = [vp, i, i, vp, vp, vp]
         lib.lrbms_get_state.argtypes = [vp, i, vp, dp, dp]
@@ -343,6 +344,16 @@ def lrbms_test_withhold_copy(ctx, sim_id: int):
     """Test hook: the next reduced solve of sim_id withholds one bulk copy, so
     its bounded wait runs out and the simulation stops with LRBMS_E_TIMEOUT."""
     _check(ctx, library().lrbms_test_withhold_copy(ctx, sim_id))
+
+
+def lrbms_test_factor_plan(n_sub: int, refactor_period: int, refactor_stages: int, info) -> tuple:
+    """Test hook (host only): the factor kernel's plan for one step, as
+    (k0, k1, buffer, whole, last_stage), from the solver state info[12]."""
+    inf = np.ascontiguousarray(info, dtype=np.int32)
+    assert inf.size == 12
+    out = np.zeros(5, dtype=np.int32)
+    _check(None, library().lrbms_test_factor_plan(n_sub, refactor_period, refactor_stages, _ptr(inf), _ptr(out)))
+    return int(out[0]), int(out[1]), int(out[2]), bool(out[3]), bool(out[4])
 
 
 def lrbms_set_slopes(ctx, sim_id: int, slopes):
