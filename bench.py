@@ -390,6 +390,7 @@ def run_serving(a):
         "metric": "LRBMS serving: per-tick step latency under Poisson arrivals of mixed grids",
         "value": p99, "unit": "ms (p99 step latency)", "higher_is_better": False,
         "p50_step_ms": p50, "p99_step_ms": p99, "ticks": len(srv.tick_ms),
+        "step_ms_percentiles": {str(q): float(np.percentile(srv.tick_ms, q)) for q in (90, 95, 100)},
         "throughput_sim_steps_per_s": steps / wall,
         "request_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "admission_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
