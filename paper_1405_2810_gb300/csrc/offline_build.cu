@@ -1714,18 +1714,24 @@ extern "C" int lrbms_clone(lrbms_ctx* ctx, int src, const double* rot, int* sim_
   std::vector<long long> qoff(n_sub + 1, 0);
   for (int E = 0; E < n_sub; ++E) qoff[E + 1] = qoff[E] + (long long)NE[E] * NE[E];
   const long long phi_tot = phioff[n_sub - 1] + (long long)NE[n_sub - 1] * 3 * cells;
-  DevBuf B;
-  double* rPhi = B.get<double>((size_t)phi_tot);
-  double* rcomp = B.get<double>((size_t)Q * aoff[d.n_blocks]);
-  double* rrhs = B.get<double>((size_t)Q * xoff[n_sub]);
-  double* dQ = B.get<double>((size_t)qoff[n_sub]);
-  double* s0 = B.get<double>((size_t)d.n_cells);
-  if (!rPhi || !rcomp || !rrhs || !dQ || !s0) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "clone buffers");
   int steps = 0;
   BCK(cudaMemcpy(&steps, d.steps, 4, cudaMemcpyDeviceToHost));
-  BCK(cudaMemcpyAsync(s0, d.s + (size_t)(steps & 1) * d.n_cells, 8 * (size_t)d.n_cells, cudaMemcpyDeviceToDevice, st));
+  // An unrotated copy is loaded straight from the source's arrays and its
+  // current saturation (the source is at rest): no scratch buffers, whose
+  // cudaMalloc and cudaFree would wait for the steps in flight on the other
+  // streams.
+  const double* s0 = d.s + (size_t)(steps & 1) * d.n_cells;
   const double *uPhi = d.Phi, *ucomp = d.comp, *urhs = d.rhs;
+  DevBuf B;
   if (rot) {
+    double* rPhi = B.get<double>((size_t)phi_tot);
+    double* rcomp = B.get<double>((size_t)Q * aoff[d.n_blocks]);
+    double* rrhs = B.get<double>((size_t)Q * xoff[n_sub]);
+    double* dQ = B.get<double>((size_t)qoff[n_sub]);
+    double* s0buf = B.get<double>((size_t)d.n_cells);
+    if (!rPhi || !rcomp || !rrhs || !dQ || !s0buf) return lrbms_internal_fail(ctx, LRBMS_E_BUDGET, "clone buffers");
+    BCK(cudaMemcpyAsync(s0buf, s0, 8 * (size_t)d.n_cells, cudaMemcpyDeviceToDevice, st));
+    s0 = s0buf;
     BCK(cudaMemcpyAsync(dQ, rot, 8 * (size_t)qoff[n_sub], cudaMemcpyDefault, st));
     std::vector<RotJob> rj;
     for (int E = 0; E < n_sub; ++E) {
