@@ -384,6 +384,7 @@ def run_serving(a):
     p50, p99 = srv.latency_ms()
     lat = np.array([r.finished_s - r.arrival_s for r in done])
     wait = np.array([r.admitted_s - r.arrival_s for r in done])
+    start_wait = np.array([r.started_s - r.arrival_s for r in done])
     adm = np.array([r.admit_ms for r in done])
     steps = sum(r.steps_done for r in done)
     print(json.dumps({
@@ -394,6 +395,7 @@ def run_serving(a):
         "throughput_sim_steps_per_s": steps / wall,
         "request_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "admission_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "start_wait_s": {"p50": float(np.percentile(start_wait, 50)), "p99": float(np.percentile(start_wait, 99))},
         "admission_ms": {"p50": float(np.percentile(adm, 50)), "p99": float(np.percentile(adm, 99))},
         "active_sims": {"mean": float(np.mean(srv.tick_n)), "max": int(max(srv.tick_n))},
         "requests": len(done), "requests_ok": ok, "sim_steps": steps, "wall_s": wall,

@@ -14,9 +14,12 @@ With the mixed solver a simulation recomputes its FP32 factor every
 refactor_period steps, counted from its first step, and a launch lasts as
 long as its slowest simulation: the factor of the largest systems is several
 times their solve. Simulations that started on different ticks would put
-some factor into every tick. Server(align=refactor_period) therefore admits
-only on ticks whose next tick is a refactor tick of the residents, so that
-all of them factor together; a request waits at most align - 1 ticks more.
+some factor into every tick. Server(align=refactor_period) therefore starts
+new simulations only on ticks that are refactor ticks of the residents, so
+that all of them factor together; a request waits at most align - 1 ticks
+more. It is admitted (loaded or cloned) as soon as it fits, and waits,
+resident, for its start tick: the admissions of a cohort are spread over
+the ticks before it starts instead of all landing in one tick.
 """
 from __future__ import annotations
 
@@ -35,9 +38,11 @@ class Request:
     sim_id: int = -1
     steps_done: int = 0
     admitted_tick: int = -1
+    start_tick: int = -1     # tick of its first step
     finished_tick: int = -1
     arrival_s: float = 0.0   # wall-clock times (run_timed), seconds from its start
     admitted_s: float = -1.0
+    started_s: float = -1.0  # when it joined the stepped list (its first step is the next tick)
     finished_s: float = -1.0
     admit_ms: float = 0.0    # host time of the admitting call
     result: dict = field(default_factory=dict)
@@ -51,9 +56,10 @@ class Server:
     lrbms_release, LrbmsError, LRBMS_E_BUDGET). admit: optional callable
     (ctx, request) -> sim_id replacing lrbms_offline_load (for instance a
     lrbms_clone of a resident simulation); it raises LrbmsError with
-    LRBMS_E_BUDGET when the request does not fit yet. align: admissions
-    happen only on ticks t with (t + 1 - t0) % align == 0, t0 the first tick
-    of the residents present since the server was last empty (1: any tick)."""
+    LRBMS_E_BUDGET when the request does not fit yet. align: admitted
+    requests start (take their first step) only on ticks t with
+    (t - t0) % align == 0, t0 the first tick of the residents present since
+    the server was last empty (1: on the tick after their admission)."""
 
     def __init__(self, backend, ctx, admit=None, align: int = 1):
         if int(align) < 1:
@@ -66,6 +72,7 @@ class Server:
         self.clock = None  # run_timed: seconds since its start
         self.queue: deque[Request] = deque()
         self.active: list[Request] = []
+        self.ready: list[Request] = []  # admitted, waiting for their start tick
         self.done: list[Request] = []
         self.tick_ms: list[float] = []
         self.tick_n: list[int] = []  # simulations stepped per tick
@@ -81,8 +88,17 @@ class Server:
     def _admit(self):
         if not self.active:
             self.anchor = self.tick + 1  # no residents: the next tick starts a new phase
-        elif (self.tick + 1 - self.anchor) % self.align != 0:
-            return
+        starting = (self.tick + 1 - self.anchor) % self.align == 0
+        self._load_queued()
+        if starting:  # the admitted requests take their first step in the next tick
+            for r in self.ready:
+                r.start_tick = self.tick + 1
+                if self.clock is not None:
+                    r.started_s = self.clock()
+            self.active.extend(self.ready)
+            self.ready = []
+
+    def _load_queued(self):
         while self.queue:
             r = self.queue[0]
             t0 = time.perf_counter()
@@ -100,14 +116,15 @@ class Server:
             if self.clock is not None:
                 r.admitted_s = self.clock()
             self.queue.popleft()
-            self.active.append(r)
+            self.ready.append(r)
 
     def step(self):
         """One tick: enqueue one step of every active simulation, admit the
         queued requests while it runs on the device (their copies and set-up
         kernels go to the library's admission stream), then wait for the
         step's statuses (one copy for the batch) and retire the finished
-        simulations. Requests admitted in a tick join the next one."""
+        simulations. Admitted requests join at the next start tick (with
+        align 1, the next tick)."""
         ids = [r.sim_id for r in self.active]
         t0 = time.perf_counter()
         if ids:
@@ -143,7 +160,7 @@ class Server:
         every request has finished."""
         pending = sorted(arrivals, key=lambda a: a[0])
         i = 0
-        while (i < len(pending) or self.queue or self.active) and self.tick < max_ticks:
+        while (i < len(pending) or self.queue or self.active or self.ready) and self.tick < max_ticks:
             while i < len(pending) and pending[i][0] <= self.tick:
                 _, p, o, n = pending[i]
                 self.submit(p, o, n)
@@ -160,7 +177,7 @@ class Server:
         t0 = time.perf_counter()
         self.clock = lambda: time.perf_counter() - t0
         i = 0
-        while i < len(pending) or self.queue or self.active:
+        while i < len(pending) or self.queue or self.active or self.ready:
             now = self.clock()
             if now > max_seconds:
                 break
@@ -169,7 +186,7 @@ class Server:
                 self.submit(p, o, n)
                 self.queue[-1].arrival_s = at
                 i += 1
-            if not self.queue and not self.active:
+            if not self.queue and not self.active and not self.ready:
                 time.sleep(max(0.0, pending[i][0] - now))
                 continue
             self.step()

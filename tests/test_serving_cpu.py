@@ -97,8 +97,9 @@ def test_admit_hook_and_timed_arrivals():
 def test_aligned_admission_keeps_residents_in_phase():
     """With align=k every simulation takes its first step on a tick that is a
     multiple of k after the first tick of the residents, so their step counts
-    agree modulo k (the mixed solver's refactor ticks coincide); an empty
-    server starts a new phase at once."""
+    agree modulo k (the mixed solver's refactor ticks coincide). Requests are
+    admitted (loaded) as soon as they arrive and wait, resident, for their
+    start tick; an empty server starts a new phase at once."""
     lib = FakeLib(capacity=100)
     srv = Server(lib, ctx=None, align=4)
     prob = {"nx": 1, "ny": 1}
@@ -107,15 +108,32 @@ def test_aligned_admission_keeps_residents_in_phase():
     done = srv.run(arrivals)
     assert [r.rid for r in done] == list(range(len(arrivals)))
     assert all(r.result["steps"] == r.n_steps for r in done)
-    # residents of the first phase start on ticks 1 + 4 j (request 0 is admitted on tick 0)
-    starts = [r.admitted_tick + 1 for r in done]
-    assert starts[0] == 1
+    assert all(r.admitted_tick == r.arrival_tick for r in done)  # loaded on arrival
+    starts = [r.start_tick for r in done]
+    assert starts[0] == 1  # request 0 is admitted on tick 0, which steps nothing
     assert all((s - starts[0]) % 4 == 0 for s in starts[:5])
-    assert all(r.admitted_tick >= r.arrival_tick for r in done)
-    assert all(r.admitted_tick - r.arrival_tick < 4 for r in done[1:5])
+    assert all(0 < s - r.arrival_tick <= 4 for s, r in zip(starts, done))
     # the server emptied before request 5 arrived: it starts a new phase at once
-    assert done[5].admitted_tick == done[5].arrival_tick
+    assert starts[5] == done[5].arrival_tick + 1
     assert (starts[6] - starts[5]) % 4 == 0
+    # every step call lists only started simulations, each with its steps counted from its start
+    assert all(r.finished_tick - r.start_tick + 1 == r.n_steps for r in done)
     assert not lib.live
     with pytest.raises(ValueError):
         Server(lib, ctx=None, align=0)
+
+
+def test_aligned_admission_waits_for_budget_in_order():
+    """A request that does not fit stays queued (arrival order kept) and is
+    loaded once a retirement frees memory; it still starts on a start tick."""
+    lib = FakeLib(capacity=2)
+    srv = Server(lib, ctx=None, align=3)
+    prob = {"nx": 1, "ny": 1}
+    done = srv.run([(0, prob, None, 4), (0, prob, None, 7), (1, prob, None, 2), (2, prob, None, 2)])
+    assert [r.rid for r in done] == [0, 1, 2, 3]
+    assert all(r.result["steps"] == r.n_steps for r in done)
+    assert max(len(c) for c in lib.calls) <= 2
+    assert done[2].admitted_tick >= done[0].finished_tick  # waited for request 0's memory
+    starts = [r.start_tick for r in done]
+    assert all((s - starts[0]) % 3 == 0 for s in starts if s <= done[1].finished_tick)
+    assert not lib.live
